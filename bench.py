@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of the IC-D2S hot path on GB300.
+
+A step is one whole outer iteration of Algorithm 2 on the device (Tabu
+search, control parameters, subQUBO selection, the emulated Ising machine,
+write-back, mutation, best update) over one synthetic solution set.  The
+metric is spin-flip attempts of the emulated Ising machine per second of
+step time (sweeps x subQUBO size x subQUBOs per step / step time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--workload NAME]
+
+The default workload is the Beasley-shaped instance (n = 2500, 10 % density,
+int8 entries in [-100, 100]) with 128 replicas, subQUBOs of 64, 1024 sweeps,
+alpha = 5n, c = 16 and a 1 % mutation rate.  Inputs are resident in HBM when
+the timed region starts; L2 is flushed (256 MiB write) before every timed
+step, outside the step's events.  `--impl reference` times the CPU oracle
+(single thread, as it stands) on a bounded sample of the same workload.
+Under torchrun every rank solves its own instance (independent problems,
+weak scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2502_13947_gb300.instances import make_qubo, random_solutions  # noqa: E402
+
+WORKLOADS = {
+    "beasley-like-n2500-d0.1-m64-z128": dict(
+        n=2500, density=0.1, qseed=1, z=128, K=1, m_min=64, m_max=64, m_init=64, sweeps=1024, alpha=12500, c=16,
+        T_max=1500.0, T_min=1.0, mut_mode=1, mut_rate=0.01),
+}
+DEFAULT_WORKLOAD = "beasley-like-n2500-d0.1-m64-z128"
+METRIC = "spin-flip attempts/s"
+UNIT = "attempts/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def attempts_per_step(w):
+    # subQUBO sizes are drawn per (replica, group); the mean is exact for m_min == m_max
+    return w["z"] * w["K"] * w["sweeps"] * (w["m_min"] + w["m_max"]) // 2
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def ncu_traffic(kernel_file, kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source is unchanged since the capture (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            tab = json.load(f)
+        ent = tab.get(kernel)
+        if not ent:
+            return None
+        src = os.path.join(ROOT, "paper_2502_13947_gb300", "csrc", kernel_file)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        return ent["dram_bytes_per_launch"] if ent.get("source_sha256") == h else None
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------------------- clocks
+CLOCK_Q = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+           "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+           "clocks_event_reasons.sw_power_cap")
+
+
+def start_clocks():
+    try:
+        return subprocess.Popen(["nvidia-smi", "--query-gpu=" + CLOCK_Q, "--format=csv,noheader,nounits", "-lms", "100"],
+                                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return None
+
+
+def stop_clocks(proc, uuid):
+    if proc is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        out, _ = proc.communicate()
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9 or (uuid and f[0] != uuid):
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax.append(float(f[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle arm
+def oracle_sample(w, z_sample, seed=9):
+    """One oracle step on z_sample replicas of the workload; returns (seconds, attempts)."""
+    from oracle import oracle as O
+    O.build()
+    Q = make_qubo(w["n"], w["density"], w["qseed"])
+    prm = O.Params(z=z_sample, K=w["K"], m_min=w["m_min"], m_max=w["m_max"], m_init=w["m_init"], alpha=w["alpha"],
+                   c=w["c"], sweeps=w["sweeps"], T_max=w["T_max"], T_min=w["T_min"], w1=65536, w2=65536, w3=32768,
+                   mut_mode=w["mut_mode"], mut_rate=w["mut_rate"], patience=0, max_iters=1)
+    S0 = random_solutions(w["n"], z_sample, 42)
+    t0 = time.perf_counter()
+    O.step(Q, prm, seed, 0, S0)
+    dt = time.perf_counter() - t0
+    return dt, z_sample * w["K"] * w["sweeps"] * (w["m_min"] + w["m_max"]) // 2
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    per_replica = 0.15  # seconds of oracle time per replica-step on one core (measured order of magnitude)
+    z_s = int(max(1, min(w["z"], 120.0 / max(1, args.steps + args.warmup) / per_replica)))
+    for _ in range(args.warmup):
+        oracle_sample(w, z_s)
+    times, att = [], 0
+    for _ in range(args.steps):
+        dt, att = oracle_sample(w, z_s)
+        times.append(dt)
+    tot = sum(times)
+    value = att * len(times) / tot
+    sample = "one outer iteration of the workload on %d of its %d replicas per step (single-threaded C oracle)" % (
+        z_s, w["z"])
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": dict(workload=args.workload, **{k: w[k] for k in ("n", "density", "z", "K", "m_min", "m_max",
+                                                                          "sweeps", "alpha", "c", "mut_rate")},
+                           replicas_per_sample_step=z_s, l2="n/a (CPU)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args, w):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2502_13947_gb300 import build as B
+    from paper_2502_13947_gb300 import icd2s as I
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    if not B.up_to_date():
+        if rank == 0:
+            B.build()
+        if world > 1:
+            dist.barrier()
+    dev_uuid = None
+    try:
+        dev_uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+
+    n, z = w["n"], w["z"]
+    Q = make_qubo(n, w["density"], w["qseed"] + 1000 * rank)   # every rank: its own instance
+    p = I.icd2s_default_params(n, z=z, K=w["K"], m_min=w["m_min"], m_max=w["m_max"], m_init=w["m_init"],
+                               sweeps=w["sweeps"], alpha=w["alpha"], c=w["c"], T_max=w["T_max"], T_min=w["T_min"],
+                               mut_mode=w["mut_mode"], mut_rate=w["mut_rate"], patience=0, max_iters=1 << 30)
+    q = I.icd2s_qubo_create(Q)
+    st = I.icd2s_state_create(q, z, 7 + rank)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        I.icd2s_initial_pass(st, p, sp)
+        I.icd2s_best_update(st, sp)
+    torch.cuda.synchronize()
+    I.icd2s_set_timing(st, True)
+    t = 0
+    for _ in range(args.warmup):
+        I.icd2s_step(st, p, t, sp)
+        t += 1
+    torch.cuda.synchronize()
+
+    phase_tot = dict.fromkeys(I.PHASES, 0.0)
+    step_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = start_clocks() if rank == 0 else None
+    time.sleep(0.25 if clocks else 0)
+    launches0 = I.icd2s_kernel_launches()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()                       # L2 flush, outside the step's events
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            I.icd2s_step(st, p, t, sp)
+            e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        for k, v in I.icd2s_get_phase_ms(st).items():
+            phase_tot[k] += v
+        t += 1
+    launches = I.icd2s_kernel_launches() - launches0
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = stop_clocks(clocks, dev_uuid) if rank == 0 else None
+    total_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    att = attempts_per_step(w)
+    value = world * att * args.steps / (total_ms / 1000.0)
+
+    # end to end through the host-buffer entry point (pinned host memory, copies inside the timed region)
+    e2e_steps = max(1, min(args.steps, 10))
+    x_in = torch.empty((z, n), dtype=torch.uint8, pin_memory=True).numpy()
+    x_out = torch.empty((z, n), dtype=torch.uint8, pin_memory=True).numpy()
+    E_out = torch.empty(z, dtype=torch.int64, pin_memory=True).numpy()
+    x_in[:] = random_solutions(n, z, 5 + rank)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e2e_s = 0.0
+    for _ in range(e2e_steps):
+        t0 = time.perf_counter()
+        I.icd2s_step_host(st, p, t, x_in, x_out, E_out, sp)
+        e2e_s += time.perf_counter() - t0
+        x_in[:] = x_out
+        t += 1
+    if world > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = world * att * e2e_steps / e2e_s
+
+    I.icd2s_state_destroy(st)
+    I.icd2s_qubo_destroy(q)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = measured_peaks()
+    K = args.steps
+    phase_avg = {k: v / K for k, v in phase_tot.items()}
+    ld = (n + 127) // 128 * 128
+    # Tabu (Algorithm 1): one row of Q (n bytes) per iteration per replica, plus
+    # the replica state read and written once (g, C, T int32; x bytes)
+    tabu_bytes = z * w["alpha"] * n + z * ld * (4 + 4 + 4 + 4 + 1 + 1)
+    tabu_s = phase_avg["tabu"] / 1000.0
+    tabu_gbs = tabu_bytes / tabu_s / 1e9
+    roofline = {"kernel": "k_tabu", "bound": "hbm", "achieved": tabu_gbs, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": tabu_gbs / peaks["hbm_gbs"],
+                "traffic": ncu_traffic("kernels_tabu.cu", "k_tabu"),
+                "algorithmic_bytes_per_launch": tabu_bytes, "launch_ms": phase_avg["tabu"],
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src}
+    anneal_rate = att / (phase_avg["anneal"] / 1000.0)
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        dt, a = oracle_sample(w, z)
+        cpu = {"value": a / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one whole outer iteration of the workload (all %d replicas), single-threaded C oracle, "
+                         "%.1f s" % (z, dt)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "density": w["density"], "z": z, "K": w["K"],
+                   "m_min": w["m_min"], "m_max": w["m_max"], "sweeps": w["sweeps"], "alpha": w["alpha"],
+                   "c": w["c"], "mutation_rate": w["mut_rate"], "T_max": w["T_max"], "T_min": w["T_min"],
+                   "attempts_per_step": att, "parallelism": "independent instance per GPU" if world > 1 else "1 GPU",
+                   "l2": "flushed before every timed step (256 MiB write outside the step events)"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": z * n, "d2h_bytes_per_step": z * n + 8 * z,
+                "steps": e2e_steps, "api": "icd2s_step_host"},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "phase_ms": phase_avg,
+        "anneal_kernel_attempts_per_s": anneal_rate,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,238 @@
+/*
+ * icd2s.h -- C ABI of the GB300 (sm_103a) IC-D2S hot path.
+ *
+ * IC-D2S (Abdollahi, Kamal, Pedram, ASP-DAC'25) minimises the QUBO objective
+ * f(x) = x^T Q x over binary x for a symmetric integer Q (Eq. 1).  This
+ * library runs the data-parallel part of its loop (Algorithm 2) on one GPU:
+ * Tabu search (Algorithm 1), the control parameters (Eq. 6-8, Algorithm 3),
+ * subQUBO selection and the emulated Ising machine (Eq. 4, Algorithm 4),
+ * the write-back of accepted flips into exact int32 gain vectors, and the
+ * mutation operator with its cosine rate schedule (Eq. 5).
+ *
+ * Conventions, for every entry point:
+ *  - Return value: ICD2S_OK (0) or a negative ICD2S_ERR_* code; the message of
+ *    the last failure on the calling thread is returned by icd2s_last_error().
+ *  - Host pointers are read (or written) during the call only; the caller
+ *    keeps ownership.
+ *  - Device pointers ("_dev") are borrowed for the duration of the work the
+ *    call enqueues on `stream`; they must stay valid until that work is done.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  Calls that return host data synchronise that stream.
+ *  - Handles are not thread-safe: one thread at a time per handle.
+ *  - All energies are exact int64; gains are exact int32 (|g| <= 200 n + 100).
+ *  - Limits: 1 <= n <= 16384, entries of Q are int8, 1 <= replicas <= 4096,
+ *    subQUBO size 1..256.  Violations return ICD2S_ERR_RANGE / ICD2S_ERR_ARG.
+ *  - Random numbers are Philox4x32-10 (Salmon et al., SC'11) keyed by the
+ *    64-bit seed; every draw is a pure function of (seed, counter), so
+ *    results do not depend on launch geometry or scheduling.
+ */
+#ifndef ICD2S_H
+#define ICD2S_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ICD2S_OK 0
+#define ICD2S_ERR_ARG (-1)        /* bad argument (null pointer, size mismatch, ...) */
+#define ICD2S_ERR_ASYMMETRIC (-2) /* Q is not symmetric */
+#define ICD2S_ERR_RANGE (-3)      /* a size is beyond the supported limits */
+#define ICD2S_ERR_OOM (-4)        /* device allocation failed */
+#define ICD2S_ERR_CUDA (-5)       /* a CUDA call failed; see icd2s_last_error() */
+#define ICD2S_ERR_TIMEOUT (-6)    /* a bounded device-side wait gave up */
+#define ICD2S_ERR_INVARIANT (-7)  /* tracked gains/energies differ from a recompute */
+#define ICD2S_ERR_STATE (-8)      /* call made in the wrong order (e.g. mutate before select) */
+
+typedef struct icd2s_qubo icd2s_qubo;   /* device copy of Q and its per-instance data */
+typedef struct icd2s_state icd2s_state; /* z solutions (replicas) with gains and energies */
+
+/* Solver parameters (Algorithm 2; defaults from Table 1 via icd2s_default_params). */
+typedef struct icd2s_params {
+    int32_t z;          /* solutions (replicas) in S */
+    int32_t K;          /* subQUBOs per solution per Ising-machine call (multi-IM fabric) */
+    int32_t m_min;      /* subQUBO size range; m_min == m_max for the plain method */
+    int32_t m_max;
+    int32_t m_init;     /* block size of Call_IM_Solution_Set (0: m_max) */
+    int32_t alpha;      /* Tabu iterations per call (Algorithm 1) */
+    int32_t c;          /* Tabu tenure increment, 1 <= c <= n */
+    int32_t sweeps;     /* anneal sweeps per subQUBO */
+    double T_max;       /* cosine temperature schedule of the emulated Ising machine */
+    double T_min;
+    int64_t w1, w2, w3; /* aggregation weights, Q16 fixed point (65536 = 1.0), |w| <= 2^24 */
+    int32_t mut_mode;   /* 0: rate r_t of Eq. 5; 1: constant rate mut_rate */
+    double mut_rate;
+    int32_t patience;   /* stop after this many iterations without a new best (<= 0: off) */
+    int32_t max_iters;  /* hard cap on outer iterations */
+    int32_t reserved[8];
+} icd2s_params;
+
+/* Per-call anneal parameters (the emulated Ising machine). */
+typedef struct icd2s_anneal_params {
+    int32_t sweeps;
+    double T_max, T_min;
+    uint32_t iter;      /* iteration number mixed into the Philox counter */
+    int32_t per_replica;/* subQUBOs per replica: subQUBO s belongs to replica s / per_replica */
+} icd2s_anneal_params;
+
+/* Per-call selection parameters (control parameters + top-A choice). */
+typedef struct icd2s_select_params {
+    int64_t w1, w2, w3; /* Q16 weights of Algorithm 3 */
+    int32_t K;          /* groups (subQUBOs) per replica */
+    int32_t m_min, m_max;
+    uint32_t iter;      /* iteration number (drives uneven sizes) */
+} icd2s_select_params;
+
+typedef struct icd2s_mutate_params {
+    int32_t mut_mode;   /* 0: Eq. 5 rate at iteration `iter`; 1: constant mut_rate */
+    double mut_rate;
+    uint32_t iter;
+} icd2s_mutate_params;
+
+typedef struct icd2s_stats {
+    int32_t iters;           /* outer iterations run */
+    int64_t best_E;          /* best energy found */
+    int64_t init_best_E;     /* best energy after Call_IM_Solution_Set */
+    int64_t anneal_attempts; /* single-flip attempts made by the emulated Ising machine */
+    int64_t tabu_moves;      /* Tabu iterations summed over solutions */
+    double device_ms;        /* device time of the loop (CUDA events) */
+} icd2s_stats;
+
+/* Message of the last failure on this thread ("" if none).  Never NULL. */
+const char* icd2s_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int32_t icd2s_version(void);
+
+/* Table 1 defaults for a problem of size n: z = 4, c = n / 150 clamped to
+ * [2, n], alpha = 5 n, w = (1, 1, 0.5), IM size 50 (Section 4.1), K = 1,
+ * 256 sweeps, T_max = 100, T_min = 1, Eq. 5 mutation rate, patience 30. */
+int icd2s_default_params(int32_t n, icd2s_params* out);
+
+/* --- Problem ---------------------------------------------------------------
+ * Copies the row-major n x n int8 matrix Q_host (Eq. 1) to the device.
+ * Q must be symmetric (ICD2S_ERR_ASYMMETRIC otherwise).  Also computes the
+ * diagonal and the normalised weight effect eta_j = sum_i |Q_ij| (Eq. 6). */
+int icd2s_qubo_create(const int8_t* Q_host, int32_t n, icd2s_qubo** out);
+int icd2s_qubo_destroy(icd2s_qubo* q);
+int icd2s_qubo_size(const icd2s_qubo* q, int32_t* n_out);
+
+/* Eq. 1 for `count` binary rows x_dev[count][n] (dense, row stride n, values
+ * 0/1) into E_dev[count] (int64).  Enqueued on `stream`. */
+int icd2s_energy(icd2s_qubo* q, const uint8_t* x_dev, int32_t count, int64_t* E_dev, void* stream);
+
+/* --- Solutions -------------------------------------------------------------
+ * z = `replicas` random solutions (Generate_Initial_Solution_Set, Algorithm 2)
+ * drawn from Philox with `seed`; their gains and energies are computed. */
+int icd2s_state_create(icd2s_qubo* q, int32_t replicas, uint64_t seed, icd2s_state** out);
+int icd2s_state_destroy(icd2s_state* st);
+
+/* Replaces the solutions with x[replicas][n] (0/1; on the host when
+ * x_is_device == 0, else on the device) and recomputes gains and energies. */
+int icd2s_state_load(icd2s_state* st, const uint8_t* x, int32_t x_is_device, void* stream);
+
+/* Copies the solutions, gains and energies to host arrays x[replicas][n],
+ * g[replicas][n], E[replicas]; any pointer may be NULL.  Synchronises. */
+int icd2s_get_state(icd2s_state* st, uint8_t* x, int32_t* g, int64_t* E);
+
+/* Best solution seen by icd2s_best_update / icd2s_step (host copies). */
+int icd2s_get_best(icd2s_state* st, uint8_t* x_best, int64_t* E_best);
+
+/* --- The steps of one outer iteration (Algorithm 2) ------------------------ */
+
+/* Algorithm 1 on every solution: alpha iterations of the non-tabu argmin move
+ * with tenure c; each solution is replaced by the best one it visited.
+ * Toggle counts T and final tabu memory C are kept for the control
+ * parameters and can be read with icd2s_get_tabu. */
+int icd2s_tabu(icd2s_state* st, int32_t alpha, int32_t c, void* stream);
+int icd2s_get_tabu(icd2s_state* st, int32_t* T, int32_t* C);
+
+/* Control parameters and selection: gamma (Eq. 8) over the replicas, Delta
+ * (Eq. 7) from the last Tabu toggle counts, A = w1 eta + w2 gamma - w3 Delta
+ * (Algorithm 3, Q16), then per replica the K groups of the highest-A
+ * variables (ranked by A desc, index asc), each listed in ascending index
+ * order.  Writes idx_dev[sum of sizes] and off_dev[replicas * K + 1]
+ * (group s = (p, k) is idx_dev[off_dev[s] .. off_dev[s+1])); both buffers
+ * must hold replicas * K * m_max + 1 entries.  The selection and A are kept
+ * for icd2s_mutate. */
+int icd2s_select_subqubos(icd2s_state* st, const icd2s_select_params* sp, int32_t* idx_dev,
+                          int32_t* off_dev, void* stream);
+
+/* Copies A[replicas][n], gamma[n] and Delta[replicas][n] (Q16) of the last
+ * selection to the host; any pointer may be NULL.  Synchronises. */
+int icd2s_get_control(icd2s_state* st, int32_t* A, int32_t* gamma, int32_t* delta);
+
+/* The emulated Ising machine (Eq. 4, Algorithm 4): for each of `count`
+ * subQUBOs (indices idx_dev[off_dev[s] .. off_dev[s+1]), ascending, disjoint
+ * within a replica), stage Q[S,S] and the boundary-biased diagonal, then run
+ * `sweeps` single-flip Metropolis sweeps on the cosine temperature schedule.
+ * All subQUBOs read the solutions as they were before the call.  Writes the
+ * flip mask flips_dev[replicas][n] (1 = flipped; cleared by the call) and the
+ * subQUBO energy changes dE_dev[count] (may be NULL).  Solutions are not
+ * modified; apply the mask with icd2s_apply_flips_update_gains. */
+int icd2s_anneal_subqubos_batch(icd2s_state* st, const int32_t* idx_dev, const int32_t* off_dev,
+                                int32_t count, const icd2s_anneal_params* ap, uint8_t* flips_dev,
+                                int64_t* dE_dev, void* stream);
+
+/* Flips every variable marked in flips_dev[replicas][n] and updates the
+ * int32 gains g_i = (1 - 2 x_i)(Q_ii + 2 sum_{j != i} Q_ij x_j) and int64
+ * energies exactly (streams the rows of Q of the flipped variables). */
+int icd2s_apply_flips_update_gains(icd2s_state* st, const uint8_t* flips_dev, void* stream);
+
+/* Mutation: per replica, the floor((n - |S'|) r) variables outside the last
+ * selection S' with the highest A flip with probability given by A
+ * normalised over the replica (min-max), then gains and energies are
+ * updated.  r is Eq. 5 at mp->iter or a constant.  flips_dev[replicas][n]
+ * receives the mutation mask when not NULL. */
+int icd2s_mutate(icd2s_state* st, const icd2s_mutate_params* mp, uint8_t* flips_dev, void* stream);
+
+/* Folds the current solutions into the best one (strictly lower energy,
+ * lowest replica on ties). */
+int icd2s_best_update(icd2s_state* st, void* stream);
+
+/* Call_IM_Solution_Set (Algorithm 2): for each replica, floor(n / m_init)
+ * disjoint blocks of m_init consecutive variables are annealed and written
+ * back one after the other (each sees the previous ones' result). */
+int icd2s_initial_pass(icd2s_state* st, const icd2s_params* p, void* stream);
+
+/* One whole outer iteration t of Algorithm 2 on the device: Tabu, control
+ * parameters, selection, Ising machine, write-back, mutation, best update.
+ * Enqueued on `stream`; no host synchronisation. */
+int icd2s_step(icd2s_state* st, const icd2s_params* p, int32_t t, void* stream);
+
+/* icd2s_step with host buffers: loads x_in[replicas][n] (if not NULL) into
+ * the state, runs iteration t, and copies the solutions to x_out (if not
+ * NULL) and energies to E_out[replicas] (if not NULL).  Synchronises. */
+int icd2s_step_host(icd2s_state* st, const icd2s_params* p, int32_t t, const uint8_t* x_in,
+                    uint8_t* x_out, int64_t* E_out, void* stream);
+
+/* The whole method (Algorithm 2) from a fresh random set: returns the best
+ * solution x_out[n] and its energy.  trace (optional, max_iters * (3 z + 1)
+ * int64): per iteration the energies of all solutions after the Tabu
+ * search, after the Ising-machine step and after the mutation, then the best
+ * energy.  S_out (optional, z * n): the final solutions. */
+int icd2s_run(icd2s_qubo* q, const icd2s_params* p, uint64_t seed, uint8_t* x_out, int64_t* E_out,
+              icd2s_stats* stats, int64_t* trace, uint8_t* S_out);
+
+/* Per-phase device timing of icd2s_step.  When enabled, each step records
+ * CUDA events on its stream around its phases; icd2s_get_phase_ms waits for
+ * the last step and writes ICD2S_PHASES durations in milliseconds:
+ * [0] Tabu search, [1] control parameters + selection, [2] Ising machine
+ * (anneal), [3] write-back of the anneal flips, [4] mutation decision,
+ * [5] write-back of the mutation flips, [6] the last best-solution update. */
+#define ICD2S_PHASES 7
+int icd2s_set_timing(icd2s_state* st, int32_t enable);
+int icd2s_get_phase_ms(icd2s_state* st, double* ms);
+
+/* Number of kernel launches the library has made in this process. */
+int icd2s_kernel_launches(uint64_t* count);
+
+/* Host copies of the library's tables, for checking: BETA[sweeps] (Q24
+ * inverse temperatures of the cosine schedule) and NLOG[4096] (Q24 -ln). */
+int icd2s_tables(int32_t sweeps, double T_max, double T_min, uint32_t* beta, uint32_t* nlog);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ICD2S_H */

@@ -486,28 +486,27 @@ static void orc_best_update(const uint8_t* S, const int64_t* E, int32_t z, int32
         }
 }
 
-/* Runs Algorithm 2.  Outputs: best_x[n], S_out[z][n] (final solutions),
- * trace[max_iters][3 z + 1] (int64, optional): per iteration the energies of
- * all solutions after the Tabu search, after the IM step, after the mutation,
- * then the best energy; init_E[z] (optional): energies after
- * Call_IM_Solution_Set. */
-int32_t orc_run(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t seed,
-                uint8_t* best_x, uint8_t* S_out, int64_t* trace, int64_t* init_E,
-                orc_result* res)
+/* One outer iteration t of Algorithm 2 on the solution set S[z][n], in
+ * place: Tabu search (Algorithm 1), Deviation_Extraction (Eq. 8),
+ * Control_Parameters_Aggregation (Algorithm 3), Call_IM_Partial_Solution_Set
+ * (Algorithm 4) and the mutation with rate r_t (Eq. 5) or a constant rate.
+ * E[z] receives the energies after the iteration; trace3[3 z] (optional) the
+ * energies after the Tabu search, the Ising-machine step and the mutation;
+ * the best solution is folded in after each of the three phases.  T_out and
+ * A_out (optional, z * n) receive the toggle counts and A.  Returns 1 if the
+ * best energy improved. */
+int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t seed, int32_t t,
+                 const int32_t* eta_hat, uint8_t* S, int64_t* E, int64_t* trace3, int64_t* best_E,
+                 uint8_t* best_x, int32_t* T_out, int32_t* A_out)
 {
     const int32_t z = prm->z, K = prm->K;
-    uint8_t* S = (uint8_t*)malloc((size_t)z * n);
-    int64_t* E = (int64_t*)malloc(sizeof(int64_t) * (size_t)z);
     int32_t* T = (int32_t*)malloc(sizeof(int32_t) * (size_t)z * n);
     int32_t* C = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
     int32_t* A = (int32_t*)malloc(sizeof(int32_t) * (size_t)z * n);
     int32_t* gam = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
     int32_t* del = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
-    int64_t* eta = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
-    int32_t* eta_hat = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
-    int32_t mmax = prm->m_max > prm->m_init ? prm->m_max : prm->m_init;
-    int32_t* Qs = (int32_t*)malloc(sizeof(int32_t) * (size_t)mmax * mmax);
-    uint8_t* xs = (uint8_t*)malloc((size_t)mmax);
+    int32_t* Qs = (int32_t*)malloc(sizeof(int32_t) * (size_t)prm->m_max * prm->m_max);
+    uint8_t* xs = (uint8_t*)malloc((size_t)prm->m_max);
     int32_t* sizes = (int32_t*)malloc(sizeof(int32_t) * (size_t)K);
     int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)K * prm->m_max);
     uint8_t* S_pre = (uint8_t*)malloc((size_t)n);
@@ -515,103 +514,130 @@ int32_t orc_run(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t seed
     int32_t* msel = (int32_t*)malloc(sizeof(int32_t) * (size_t)z);
     uint32_t* beta = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(prm->sweeps > 0 ? prm->sweeps : 1));
     uint32_t nlog[4096];
-    int64_t best_E = INT64_MAX;
     int improved = 0;
-
     orc_beta_table(prm->sweeps, prm->T_max, prm->T_min, beta);
     orc_nlog_table(nlog);
 
-    /* Generate_Initial_Solution_Set */
-    orc_init_solutions(n, z, seed, S);
-
-    /* Call_IM_Solution_Set -- floor(n / m) disjoint blocks per
-     * solution, each solved with the bias of the current values of the
-     * others and written back before the next block (Gauss-Seidel). */
+    /* Tabu search on every solution (Algorithm 1) */
+    for (int32_t p = 0; p < z; ++p)
+        E[p] = orc_tabu(Q, n, S + (int64_t)p * n, prm->alpha, prm->c, T + (int64_t)p * n, C);
+    orc_best_update(S, E, z, n, best_E, best_x, &improved);
+    if (trace3) memcpy(trace3, E, sizeof(int64_t) * (size_t)z);
+    /* Deviation_Extraction (Eq. 8), Control_Parameters_Aggregation (Algorithm 3) */
+    orc_gamma(S, z, n, gam);
+    for (int32_t p = 0; p < z; ++p) {
+        orc_delta(T + (int64_t)p * n, n, del);
+        orc_aggregate(eta_hat, gam, del, n, prm->w1, prm->w2, prm->w3, A + (int64_t)p * n);
+    }
+    /* Call_IM_Partial_Solution_Set (Algorithm 4) */
     for (int32_t p = 0; p < z; ++p) {
         uint8_t* x = S + (int64_t)p * n;
-        for (int32_t l = 0; l < n / prm->m_init; ++l) {
-            int32_t m = prm->m_init;
+        const int32_t* Ap = A + (int64_t)p * n;
+        orc_subqubo_sizes(K, prm->m_min, prm->m_max, seed, (uint32_t)p, (uint32_t)t, sizes);
+        orc_select(Ap, n, sizes, K, idx);
+        memcpy(S_pre, x, (size_t)n);
+        memset(in_sel + (int64_t)p * n, 0, (size_t)n);
+        int32_t off = 0;
+        msel[p] = 0;
+        for (int32_t k = 0; k < K; ++k) {
+            int32_t m = sizes[k];
+            /* every subQUBO of this call is built from the state before
+             * the call (Jacobi merge, reading S16) */
+            orc_subqubo(Q, n, S_pre, idx + off, m, Qs, NULL);
+            for (int32_t a = 0; a < m; ++a) xs[a] = S_pre[idx[off + a]];
+            orc_anneal(Qs, m, xs, prm->sweeps, beta, nlog, seed, (uint32_t)(p * K + k), (uint32_t)t, NULL);
+            for (int32_t a = 0; a < m; ++a) {
+                x[idx[off + a]] = xs[a];
+                in_sel[(int64_t)p * n + idx[off + a]] = 1;
+            }
+            off += m;
+            msel[p] += m;
+        }
+        E[p] = orc_energy(Q, n, x);
+    }
+    orc_best_update(S, E, z, n, best_E, best_x, &improved);
+    if (trace3) memcpy(trace3 + z, E, sizeof(int64_t) * (size_t)z);
+    /* Mutation with the MRAnnealer rate (Eq. 5) */
+    double r = prm->mut_mode == 0 ? orc_mutation_rate(t) : prm->mut_rate;
+    for (int32_t p = 0; p < z; ++p) {
+        uint8_t* x = S + (int64_t)p * n;
+        int32_t L = (int32_t)floor((double)(n - msel[p]) * r);
+        orc_mutate(A + (int64_t)p * n, n, in_sel + (int64_t)p * n, L, seed, (uint32_t)p, (uint32_t)t, x);
+        E[p] = orc_energy(Q, n, x);
+    }
+    orc_best_update(S, E, z, n, best_E, best_x, &improved);
+    if (trace3) memcpy(trace3 + 2 * z, E, sizeof(int64_t) * (size_t)z);
+    if (T_out) memcpy(T_out, T, sizeof(int32_t) * (size_t)z * n);
+    if (A_out) memcpy(A_out, A, sizeof(int32_t) * (size_t)z * n);
+    free(T); free(C); free(A); free(gam); free(del); free(Qs); free(xs); free(sizes); free(idx);
+    free(S_pre); free(in_sel); free(msel); free(beta);
+    return improved;
+}
+
+/* Call_IM_Solution_Set (Algorithm 2): floor(n / m) disjoint blocks of m
+ * consecutive variables per solution, each solved with the bias of the
+ * current values of the others and written back before the next block
+ * (Gauss-Seidel).  E[z] receives the energies. */
+void orc_initial_pass(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t seed, uint8_t* S, int64_t* E)
+{
+    const int32_t m = prm->m_init;
+    int32_t* Qs = (int32_t*)malloc(sizeof(int32_t) * (size_t)m * m);
+    uint8_t* xs = (uint8_t*)malloc((size_t)m);
+    int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)m);
+    uint32_t* beta = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(prm->sweeps > 0 ? prm->sweeps : 1));
+    uint32_t nlog[4096];
+    orc_beta_table(prm->sweeps, prm->T_max, prm->T_min, beta);
+    orc_nlog_table(nlog);
+    for (int32_t p = 0; p < prm->z; ++p) {
+        uint8_t* x = S + (int64_t)p * n;
+        for (int32_t l = 0; l < n / m; ++l) {
             for (int32_t a = 0; a < m; ++a) idx[a] = l * m + a;
             orc_subqubo(Q, n, x, idx, m, Qs, NULL);
             for (int32_t a = 0; a < m; ++a) xs[a] = x[idx[a]];
-            orc_anneal(Qs, m, xs, prm->sweeps, beta, nlog, seed, (uint32_t)p,
-                       0x80000000u | (uint32_t)l, NULL);
+            orc_anneal(Qs, m, xs, prm->sweeps, beta, nlog, seed, (uint32_t)p, 0x80000000u | (uint32_t)l, NULL);
             for (int32_t a = 0; a < m; ++a) x[idx[a]] = xs[a];
         }
         E[p] = orc_energy(Q, n, x);
     }
+    free(Qs); free(xs); free(idx); free(beta);
+}
+
+/* Runs Algorithm 2 from Generate_Initial_Solution_Set.  Outputs: best_x[n],
+ * S_out[z][n] (final solutions), trace[max_iters][3 z + 1] (int64,
+ * optional): per iteration the energies of all solutions after the Tabu
+ * search, after the IM step, after the mutation, then the best energy;
+ * init_E[z] (optional): energies after Call_IM_Solution_Set. */
+int32_t orc_run(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t seed,
+                uint8_t* best_x, uint8_t* S_out, int64_t* trace, int64_t* init_E,
+                orc_result* res)
+{
+    const int32_t z = prm->z;
+    uint8_t* S = (uint8_t*)malloc((size_t)z * n);
+    int64_t* E = (int64_t*)malloc(sizeof(int64_t) * (size_t)z);
+    int64_t* eta = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    int32_t* eta_hat = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t best_E = INT64_MAX;
+    int improved = 0;
+
+    orc_init_solutions(n, z, seed, S);                 /* Generate_Initial_Solution_Set */
+    orc_initial_pass(Q, n, prm, seed, S, E);           /* Call_IM_Solution_Set */
     orc_best_update(S, E, z, n, &best_E, best_x, &improved);
     if (init_E) memcpy(init_E, E, sizeof(int64_t) * (size_t)z);
     if (res) res->init_best_E = best_E;
-
-    /* Weight_Effect_Extraction (Eq. 6) */
-    orc_eta(Q, n, eta);
+    orc_eta(Q, n, eta);                                /* Weight_Effect_Extraction (Eq. 6) */
     orc_eta_hat(eta, n, eta_hat);
 
     int32_t t = 0, stale = 0;
     while (t < prm->max_iters && (prm->patience <= 0 || stale < prm->patience)) {
-        improved = 0;
         int64_t* tr = trace ? trace + (int64_t)t * (3 * z + 1) : NULL;
-        /* Tabu search on every solution (Algorithm 1) */
-        for (int32_t p = 0; p < z; ++p)
-            E[p] = orc_tabu(Q, n, S + (int64_t)p * n, prm->alpha, prm->c, T + (int64_t)p * n, C);
-        orc_best_update(S, E, z, n, &best_E, best_x, &improved);
-        if (tr) memcpy(tr, E, sizeof(int64_t) * (size_t)z);
-        /* Deviation_Extraction (Eq. 8), Control_Parameters_Aggregation (Algorithm 3) */
-        orc_gamma(S, z, n, gam);
-        for (int32_t p = 0; p < z; ++p) {
-            orc_delta(T + (int64_t)p * n, n, del);
-            orc_aggregate(eta_hat, gam, del, n, prm->w1, prm->w2, prm->w3, A + (int64_t)p * n);
-        }
-        /* Call_IM_Partial_Solution_Set (Algorithm 4), then Mutation */
-        for (int32_t p = 0; p < z; ++p) {
-            uint8_t* x = S + (int64_t)p * n;
-            const int32_t* Ap = A + (int64_t)p * n;
-            orc_subqubo_sizes(K, prm->m_min, prm->m_max, seed, (uint32_t)p, (uint32_t)t, sizes);
-            orc_select(Ap, n, sizes, K, idx);
-            memcpy(S_pre, x, (size_t)n);
-            memset(in_sel + (int64_t)p * n, 0, (size_t)n);
-            int32_t off = 0;
-            msel[p] = 0;
-            for (int32_t k = 0; k < K; ++k) {
-                int32_t m = sizes[k];
-                /* every subQUBO of this call is built from the state before
-                 * the call (Jacobi merge, reading S16) */
-                orc_subqubo(Q, n, S_pre, idx + off, m, Qs, NULL);
-                for (int32_t a = 0; a < m; ++a) xs[a] = S_pre[idx[off + a]];
-                orc_anneal(Qs, m, xs, prm->sweeps, beta, nlog, seed, (uint32_t)(p * K + k),
-                           (uint32_t)t, NULL);
-                for (int32_t a = 0; a < m; ++a) {
-                    x[idx[off + a]] = xs[a];
-                    in_sel[(int64_t)p * n + idx[off + a]] = 1;
-                }
-                off += m;
-                msel[p] += m;
-            }
-            E[p] = orc_energy(Q, n, x);
-        }
-        orc_best_update(S, E, z, n, &best_E, best_x, &improved);
-        if (tr) memcpy(tr + z, E, sizeof(int64_t) * (size_t)z);
-        double r = prm->mut_mode == 0 ? orc_mutation_rate(t) : prm->mut_rate;
-        for (int32_t p = 0; p < z; ++p) {
-            uint8_t* x = S + (int64_t)p * n;
-            const int32_t* Ap = A + (int64_t)p * n;
-            int32_t L = (int32_t)floor((double)(n - msel[p]) * r);
-            orc_mutate(Ap, n, in_sel + (int64_t)p * n, L, seed, (uint32_t)p, (uint32_t)t, x);
-            E[p] = orc_energy(Q, n, x);
-        }
-        orc_best_update(S, E, z, n, &best_E, best_x, &improved);
-        if (tr) {
-            memcpy(tr + 2 * z, E, sizeof(int64_t) * (size_t)z);
-            tr[3 * z] = best_E;
-        }
+        improved = orc_step(Q, n, prm, seed, t, eta_hat, S, E, tr, &best_E, best_x, NULL, NULL);
+        if (tr) tr[3 * z] = best_E;
         /* MRAnnealer.NextRate is r_{t+1}; termination rule (Section 3, end) */
         stale = improved ? 0 : stale + 1;
         t += 1;
     }
     if (S_out) memcpy(S_out, S, (size_t)z * n);
     if (res) { res->iters = t; res->best_E = best_E; }
-    free(S); free(E); free(T); free(C); free(A); free(gam); free(del); free(eta); free(eta_hat);
-    free(Qs); free(xs); free(sizes); free(idx); free(S_pre); free(in_sel); free(msel); free(beta);
+    free(S); free(E); free(eta); free(eta_hat);
     return t;
 }

@@ -33,7 +33,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC", "-shared",
                            "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -89,6 +89,8 @@ def lib():
                 "orc_anneal": (i64, [vp, i32, vp, i32, vp, vp, u64, u32, u32, vp]),
                 "orc_mutate": (i32, [vp, i32, vp, i32, u64, u32, u32, vp]),
                 "orc_run": (i32, [vp, i32, C.POINTER(Params), u64, vp, vp, vp, vp, C.POINTER(Result)]),
+                "orc_step": (i32, [vp, i32, C.POINTER(Params), u64, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
+                "orc_initial_pass": (None, [vp, i32, C.POINTER(Params), u64, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -301,3 +303,31 @@ def run(Q, prm: Params, seed: int, trace: bool = True):
     return dict(best_x=best_x, best_E=int(res.best_E), S=S,
                 trace=tr[:it] if tr is not None else None, init_E=init_E,
                 init_best_E=int(res.init_best_E), iters=int(it))
+
+
+def step(Q, prm: Params, seed: int, t: int, S, best_E=None, best_x=None):
+    """One outer iteration of Algorithm 2 from the solution set S (not
+    modified).  Returns dict(S, E, trace3, best_E, best_x, T, A, improved)."""
+    Q, n = _q(Q)
+    S = _u8(S).copy()
+    z = prm.z
+    assert S.shape == (z, n)
+    eh = eta_hat(eta(Q))
+    E = np.zeros(z, np.int64)
+    tr = np.zeros(3 * z, np.int64)
+    bE = np.array([np.iinfo(np.int64).max if best_E is None else best_E], np.int64)
+    bx = np.zeros(n, np.uint8) if best_x is None else _u8(best_x).copy()
+    T = np.zeros((z, n), np.int32)
+    A = np.zeros((z, n), np.int32)
+    imp = lib().orc_step(_p(Q), n, C.byref(prm), seed, t, _p(eh), _p(S), _p(E), _p(tr), _p(bE), _p(bx),
+                         _p(T), _p(A))
+    return dict(S=S, E=E, trace3=tr, best_E=int(bE[0]), best_x=bx, T=T, A=A, improved=int(imp))
+
+
+def initial_pass(Q, prm: Params, seed: int, S):
+    """Call_IM_Solution_Set on S (not modified).  Returns (S_after, E)."""
+    Q, n = _q(Q)
+    S = _u8(S).copy()
+    E = np.zeros(prm.z, np.int64)
+    lib().orc_initial_pass(_p(Q), n, C.byref(prm), seed, _p(S), _p(E))
+    return S, E

@@ -1,0 +1,689 @@
+// api.cu -- the extern "C" entry points of libicd2s.so (declared in
+// include/icd2s.h): argument checks, device memory owned by the handles,
+// host tables, and the orchestration of one outer iteration of Algorithm 2
+// as a fixed sequence of kernel launches on the caller's stream.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/icd2s.h"
+#include "common.cuh"
+
+using namespace icd2s;
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}
+
+void icd2s::note_launch(int kernels) { g_launches.fetch_add((unsigned long long)kernels, std::memory_order_relaxed); }
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(e_ == cudaErrorMemoryAllocation ? ICD2S_ERR_OOM : ICD2S_ERR_CUDA,          \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define REQ(cond, code, ...)                \
+    do {                                    \
+        if (!(cond)) return fail(code, __VA_ARGS__); \
+    } while (0)
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Host tables.  The cosine temperature schedule of the emulated Ising
+// machine, BETA[k] = round(2^24 / T_k) with
+// T_k = T_min + (T_max - T_min)(1 + cos(pi k / (K - 1))) / 2 (T_0 = T_min when
+// K = 1), and NLOG[j] = round(2^24 (-ln((j + 0.5) / 4096))): the test
+// l * BETA[k] < NLOG[u >> 20] accepts a move of gain l > 0 with the
+// Metropolis probability exp(-l / T_k) quantised to 1/4096.  Built with
+// -ffp-contract=off so the doubles round identically on every host.
+void make_beta(int sweeps, double T_max, double T_min, uint32_t* beta)
+{
+    for (int k = 0; k < sweeps; ++k) {
+        double T;
+        if (sweeps > 1)
+            T = T_min + (T_max - T_min) * (1.0 + std::cos(M_PI * (double)k / (double)(sweeps - 1))) / 2.0;
+        else
+            T = T_min;
+        const double b = 16777216.0 / T;
+        beta[k] = (b < 4294967295.0) ? (uint32_t)std::llround(b) : 4294967295u;
+    }
+}
+
+void make_nlog(uint32_t* nlog)
+{
+    for (int j = 0; j < 4096; ++j) nlog[j] = (uint32_t)std::llround(16777216.0 * -std::log(((double)j + 0.5) / 4096.0));
+}
+
+// Mutation rate of the MRAnnealer, Eq. 5: r_t = 0.3 (1 + cos(pi t / 15)) 0.99^t.
+double mutation_rate(int t) { return 0.3 * (1.0 + std::cos(M_PI * (double)t / 15.0)) * std::pow(0.99, (double)t); }
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+}  // namespace
+
+struct icd2s_qubo {
+    int n = 0, ld = 0;
+    int8_t* Q = nullptr;
+    int32_t* diag = nullptr;
+    int32_t* eta = nullptr;
+    int32_t* etahat = nullptr;
+    // scratch of icd2s_energy (grown on demand)
+    int cap = 0;
+    uint8_t* xpad = nullptr;
+    int32_t* hpad = nullptr;
+};
+
+struct icd2s_state {
+    icd2s_qubo* q = nullptr;
+    int R = 0;
+    uint64_t seed = 0;
+    Dev d{};
+    // device buffers owned by the state (Dev holds the same pointers)
+    uint8_t* X = nullptr; int32_t* G = nullptr; int64_t* E = nullptr;
+    int32_t* T = nullptr; int32_t* C = nullptr;
+    int32_t* gamma = nullptr; int32_t* A = nullptr; int32_t* delta = nullptr; int32_t* order = nullptr;
+    uint8_t* sel = nullptr;
+    int32_t* FL = nullptr; int32_t* FCNT = nullptr; unsigned long long* DEACC = nullptr; unsigned int* DONE = nullptr;
+    uint8_t* best_x = nullptr; int64_t* best_E = nullptr; int32_t* flags = nullptr;
+    int32_t* idx = nullptr; int32_t* off = nullptr;
+    uint8_t* scratch = nullptr;  // [R][ld] bytes: masks, unpadded host staging
+    int64_t* counters = nullptr; // [0] anneal attempts
+    uint32_t* nlog = nullptr;
+    uint32_t* beta = nullptr; int beta_cap = 0;
+    int beta_sweeps = -1; double beta_tmax = 0, beta_tmin = 0;
+    bool have_select = false; int sel_K = 0;
+    int tabu_w = 0;  // 4-variable groups per thread in the Tabu kernel (0: automatic)
+    // phase timing of icd2s_step: events [2 * phase] / [2 * phase + 1]
+    bool timing = false, timed_step = false;
+    cudaEvent_t ev[2 * ICD2S_PHASES] = {};
+};
+
+// Records the start (which == 0) or end (which == 1) event of a phase.
+static void mark(icd2s_state* st, int phase, int which, cudaStream_t s)
+{
+    if (st->timing) cudaEventRecord(st->ev[2 * phase + which], s);
+}
+
+static void free_state(icd2s_state* st)
+{
+    void* ptrs[] = {st->X, st->G, st->E, st->T, st->C, st->gamma, st->A, st->delta, st->order, st->sel,
+                    st->FL, st->FCNT, st->DEACC, st->DONE, st->best_x, st->best_E, st->flags, st->idx,
+                    st->off, st->scratch, st->counters, st->nlog, st->beta};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : st->ev)
+        if (e) cudaEventDestroy(e);
+    delete st;
+}
+
+static int ensure_beta(icd2s_state* st, int sweeps, double T_max, double T_min, cudaStream_t s)
+{
+    if (sweeps == st->beta_sweeps && T_max == st->beta_tmax && T_min == st->beta_tmin) return ICD2S_OK;
+    if (sweeps > st->beta_cap) {
+        if (st->beta) CK(cudaFree(st->beta));
+        st->beta = nullptr;
+        CK(dalloc(&st->beta, (size_t)sweeps));
+        st->beta_cap = sweeps;
+    }
+    std::vector<uint32_t> b((size_t)sweeps);
+    make_beta(sweeps, T_max, T_min, b.data());
+    CK(cudaMemcpyAsync(st->beta, b.data(), sizeof(uint32_t) * sweeps, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // the host vector dies here
+    st->beta_sweeps = sweeps; st->beta_tmax = T_max; st->beta_tmin = T_min;
+    return ICD2S_OK;
+}
+
+static int check_params(const icd2s_state* st, const icd2s_params* p)
+{
+    const int n = st->q->n;
+    REQ(p, ICD2S_ERR_ARG, "params is NULL");
+    REQ(p->z == st->R, ICD2S_ERR_ARG, "params z=%d differs from the state's %d replicas", p->z, st->R);
+    REQ(p->K >= 1 && p->K <= 64, ICD2S_ERR_RANGE, "K=%d outside 1..64", p->K);
+    REQ(p->m_min >= 1 && p->m_min <= p->m_max && p->m_max <= kMaxM, ICD2S_ERR_RANGE,
+        "subQUBO sizes m_min=%d m_max=%d outside 1..256", p->m_min, p->m_max);
+    REQ((long long)p->K * p->m_max <= n, ICD2S_ERR_ARG, "K*m_max=%lld exceeds n=%d", (long long)p->K * p->m_max, n);
+    const int mi = p->m_init > 0 ? p->m_init : p->m_max;
+    REQ(mi <= kMaxM && mi <= n, ICD2S_ERR_RANGE, "m_init=%d outside 1..min(256, n)", mi);
+    REQ(p->alpha >= 0, ICD2S_ERR_ARG, "alpha < 0");
+    REQ(tabu_smem_bytes(n, p->alpha) <= 227 * 1024, ICD2S_ERR_RANGE,
+        "alpha=%d with n=%d needs more shared memory than a CTA has", p->alpha, n);
+    REQ(p->c >= 1 && p->c <= n, ICD2S_ERR_ARG, "tenure c=%d outside 1..n", p->c);
+    REQ(p->sweeps >= 1 && p->sweeps <= (1 << 24), ICD2S_ERR_RANGE, "sweeps=%d", p->sweeps);
+    REQ(p->T_min > 0 && p->T_max >= p->T_min, ICD2S_ERR_ARG, "need 0 < T_min <= T_max");
+    const int64_t wl = (int64_t)1 << 24;
+    REQ(p->w1 >= -wl && p->w1 <= wl && p->w2 >= -wl && p->w2 <= wl && p->w3 >= -wl && p->w3 <= wl, ICD2S_ERR_RANGE,
+        "|w| must be <= 2^24 (Q16)");
+    REQ(p->mut_mode == 0 || (p->mut_mode == 1 && p->mut_rate >= 0 && p->mut_rate <= 1), ICD2S_ERR_ARG,
+        "mut_mode must be 0 or 1 with 0 <= mut_rate <= 1");
+    REQ(p->max_iters >= 0, ICD2S_ERR_ARG, "max_iters < 0");
+    return ICD2S_OK;
+}
+
+extern "C" {
+
+const char* icd2s_last_error(void) { return g_err; }
+
+int32_t icd2s_version(void) { return 100; }
+
+int icd2s_default_params(int32_t n, icd2s_params* out)
+{
+    REQ(out, ICD2S_ERR_ARG, "out is NULL");
+    REQ(n >= 1 && n <= kMaxN, ICD2S_ERR_RANGE, "n=%d outside 1..%d", n, kMaxN);
+    std::memset(out, 0, sizeof *out);
+    const int m = n < 50 ? n : 50;
+    int c = n / 150;
+    if (c < 2) c = 2;
+    if (c > n) c = n;
+    out->z = 4; out->K = 1; out->m_min = m; out->m_max = m; out->m_init = m;
+    out->alpha = 5 * n; out->c = c; out->sweeps = 256; out->T_max = 100.0; out->T_min = 1.0;
+    out->w1 = 65536; out->w2 = 65536; out->w3 = 32768;
+    out->mut_mode = 0; out->mut_rate = 0.0; out->patience = 30; out->max_iters = 100;
+    return ICD2S_OK;
+}
+
+int icd2s_tables(int32_t sweeps, double T_max, double T_min, uint32_t* beta, uint32_t* nlog)
+{
+    REQ(sweeps >= 0, ICD2S_ERR_ARG, "sweeps < 0");
+    if (beta && sweeps > 0) make_beta(sweeps, T_max, T_min, beta);
+    if (nlog) make_nlog(nlog);
+    return ICD2S_OK;
+}
+
+// ----------------------------------------------------------------------------- problem
+int icd2s_qubo_create(const int8_t* Q_host, int32_t n, icd2s_qubo** out)
+{
+    REQ(Q_host && out, ICD2S_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    REQ(n >= 1 && n <= kMaxN, ICD2S_ERR_RANGE, "n=%d outside 1..%d", n, kMaxN);
+    auto* q = new icd2s_qubo();
+    q->n = n;
+    q->ld = round_up(n, kLdAlign);
+    auto bail = [&](int code) {
+        if (q->Q) cudaFree(q->Q);
+        if (q->diag) cudaFree(q->diag);
+        if (q->eta) cudaFree(q->eta);
+        if (q->etahat) cudaFree(q->etahat);
+        delete q;
+        return code;
+    };
+    int* mism = nullptr;
+    cudaError_t e;
+    if ((e = dalloc(&q->Q, (size_t)n * q->ld)) != cudaSuccess || (e = dalloc(&q->diag, q->ld)) != cudaSuccess ||
+        (e = dalloc(&q->eta, q->ld)) != cudaSuccess || (e = dalloc(&q->etahat, q->ld)) != cudaSuccess ||
+        (e = dalloc(&mism, 1)) != cudaSuccess)
+        return bail(fail(ICD2S_ERR_OOM, "device allocation failed: %s", cudaGetErrorString(e)));
+    int bad = 0;
+    if ((e = cudaMemset(q->Q, 0, (size_t)n * q->ld)) == cudaSuccess &&
+        (e = cudaMemcpy2D(q->Q, q->ld, Q_host, n, n, n, cudaMemcpyHostToDevice)) == cudaSuccess &&
+        (e = cudaMemset(mism, 0, sizeof(int))) == cudaSuccess &&
+        (e = launch_prepare(q->Q, n, q->ld, q->eta, q->etahat, q->diag, mism, 0)) == cudaSuccess &&
+        (e = cudaMemcpy(&bad, mism, sizeof(int), cudaMemcpyDeviceToHost)) == cudaSuccess) {
+        cudaFree(mism);
+        if (bad) return bail(fail(ICD2S_ERR_ASYMMETRIC, "Q is not symmetric (%d mismatched entries)", bad));
+        *out = q;
+        return ICD2S_OK;
+    }
+    cudaFree(mism);
+    return bail(fail(ICD2S_ERR_CUDA, "qubo_create: %s", cudaGetErrorString(e)));
+}
+
+int icd2s_qubo_destroy(icd2s_qubo* q)
+{
+    if (!q) return ICD2S_OK;
+    void* ptrs[] = {q->Q, q->diag, q->eta, q->etahat, q->xpad, q->hpad};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete q;
+    return ICD2S_OK;
+}
+
+int icd2s_qubo_size(const icd2s_qubo* q, int32_t* n_out)
+{
+    REQ(q && n_out, ICD2S_ERR_ARG, "NULL argument");
+    *n_out = q->n;
+    return ICD2S_OK;
+}
+
+int icd2s_energy(icd2s_qubo* q, const uint8_t* x_dev, int32_t count, int64_t* E_dev, void* stream)
+{
+    REQ(q && (count == 0 || (x_dev && E_dev)), ICD2S_ERR_ARG, "NULL argument");
+    REQ(count >= 0, ICD2S_ERR_ARG, "count < 0");
+    if (count == 0) return ICD2S_OK;
+    cudaStream_t s = S(stream);
+    if (count > q->cap) {
+        CK(cudaStreamSynchronize(s));
+        if (q->xpad) cudaFree(q->xpad);
+        if (q->hpad) cudaFree(q->hpad);
+        q->xpad = nullptr; q->hpad = nullptr; q->cap = 0;
+        CK(dalloc(&q->xpad, (size_t)count * q->ld));
+        CK(dalloc(&q->hpad, (size_t)count * q->ld));
+        q->cap = count;
+    }
+    Dev d{};
+    d.Q = q->Q; d.diag = q->diag; d.etahat = q->etahat; d.n = q->n; d.ld = q->ld; d.R = count;
+    CK(launch_pad_rows(x_dev, q->n, count, q->xpad, q->ld, s));
+    CK(launch_recompute(d, q->xpad, q->ld, count, q->hpad, E_dev, s));
+    return ICD2S_OK;
+}
+
+// ----------------------------------------------------------------------------- solutions
+int icd2s_state_create(icd2s_qubo* q, int32_t replicas, uint64_t seed, icd2s_state** out)
+{
+    REQ(q && out, ICD2S_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    REQ(replicas >= 1 && replicas <= kMaxReplicas, ICD2S_ERR_RANGE, "replicas=%d outside 1..%d", replicas,
+        kMaxReplicas);
+    auto* st = new icd2s_state();
+    st->q = q; st->R = replicas; st->seed = seed;
+    const size_t RL = (size_t)replicas * q->ld;
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, cnt) if (e == cudaSuccess) e = dalloc(&st->ptr, (cnt))
+    ALLOC(X, RL); ALLOC(G, RL); ALLOC(E, replicas); ALLOC(T, RL); ALLOC(C, RL); ALLOC(gamma, q->ld);
+    ALLOC(A, RL); ALLOC(delta, RL); ALLOC(order, RL); ALLOC(sel, RL); ALLOC(FL, RL); ALLOC(FCNT, replicas);
+    ALLOC(DEACC, replicas); ALLOC(DONE, replicas); ALLOC(best_x, q->ld); ALLOC(best_E, 1); ALLOC(flags, 4);
+    ALLOC(idx, RL); ALLOC(off, (size_t)replicas * 64 + 1); ALLOC(scratch, RL); ALLOC(counters, 4);
+    ALLOC(nlog, 4096);
+#undef ALLOC
+    if (e != cudaSuccess) {
+        free_state(st);
+        return fail(ICD2S_ERR_OOM, "device allocation failed: %s", cudaGetErrorString(e));
+    }
+    Dev& d = st->d;
+    d.Q = q->Q; d.diag = q->diag; d.etahat = q->etahat; d.n = q->n; d.ld = q->ld; d.R = replicas;
+    d.X = st->X; d.G = st->G; d.E = st->E; d.T = st->T; d.C = st->C; d.gamma = st->gamma; d.A = st->A;
+    d.delta = st->delta; d.order = st->order; d.sel = st->sel; d.FL = st->FL; d.FCNT = st->FCNT;
+    d.DEACC = st->DEACC; d.DONE = st->DONE; d.best_x = st->best_x; d.best_E = st->best_E; d.flags = st->flags;
+    d.k0 = (uint32_t)(seed & 0xffffffffu); d.k1 = (uint32_t)(seed >> 32);
+    uint32_t nl[4096];
+    make_nlog(nl);
+    const int64_t big = INT64_MAX;
+    int rc = ICD2S_OK;
+    if ((e = cudaMemset(st->T, 0, RL * 4)) != cudaSuccess || (e = cudaMemset(st->C, 0, RL * 4)) != cudaSuccess ||
+        (e = cudaMemset(st->FCNT, 0, replicas * 4)) != cudaSuccess ||
+        (e = cudaMemset(st->DEACC, 0, replicas * 8)) != cudaSuccess ||
+        (e = cudaMemset(st->DONE, 0, replicas * 4)) != cudaSuccess || (e = cudaMemset(st->flags, 0, 16)) != cudaSuccess ||
+        (e = cudaMemset(st->counters, 0, 32)) != cudaSuccess || (e = cudaMemset(st->best_x, 0, q->ld)) != cudaSuccess ||
+        (e = cudaMemcpy(st->best_E, &big, 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(st->nlog, nl, sizeof nl, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = launch_init_x(d, 0)) != cudaSuccess || (e = launch_recompute(d, d.X, d.ld, d.R, d.G, d.E, 0)) != cudaSuccess ||
+        (e = cudaDeviceSynchronize()) != cudaSuccess)
+        rc = fail(ICD2S_ERR_CUDA, "state_create: %s", cudaGetErrorString(e));
+    if (rc != ICD2S_OK) { free_state(st); return rc; }
+    *out = st;
+    return ICD2S_OK;
+}
+
+int icd2s_state_destroy(icd2s_state* st)
+{
+    if (st) free_state(st);
+    return ICD2S_OK;
+}
+
+int icd2s_state_load(icd2s_state* st, const uint8_t* x, int32_t x_is_device, void* stream)
+{
+    REQ(st && x, ICD2S_ERR_ARG, "NULL argument");
+    cudaStream_t s = S(stream);
+    const int n = st->q->n, R = st->R;
+    const uint8_t* src = x;
+    if (!x_is_device) {
+        CK(cudaMemcpyAsync(st->scratch, x, (size_t)R * n, cudaMemcpyHostToDevice, s));
+        src = st->scratch;
+    }
+    CK(launch_pad_rows(src, n, R, st->X, st->q->ld, s));
+    CK(launch_recompute(st->d, st->X, st->q->ld, R, st->G, st->E, s));
+    return ICD2S_OK;
+}
+
+int icd2s_get_state(icd2s_state* st, uint8_t* x, int32_t* g, int64_t* E)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    const int n = st->q->n, ld = st->q->ld, R = st->R;
+    CK(cudaDeviceSynchronize());
+    if (x) CK(cudaMemcpy2D(x, n, st->X, ld, n, R, cudaMemcpyDeviceToHost));
+    if (g) CK(cudaMemcpy2D(g, (size_t)n * 4, st->G, (size_t)ld * 4, (size_t)n * 4, R, cudaMemcpyDeviceToHost));
+    if (E) CK(cudaMemcpy(E, st->E, (size_t)R * 8, cudaMemcpyDeviceToHost));
+    return ICD2S_OK;
+}
+
+int icd2s_get_best(icd2s_state* st, uint8_t* x_best, int64_t* E_best)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    CK(cudaDeviceSynchronize());
+    if (x_best) CK(cudaMemcpy(x_best, st->best_x, st->q->n, cudaMemcpyDeviceToHost));
+    if (E_best) CK(cudaMemcpy(E_best, st->best_E, 8, cudaMemcpyDeviceToHost));
+    return ICD2S_OK;
+}
+
+int icd2s_get_tabu(icd2s_state* st, int32_t* T, int32_t* C)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    const int n = st->q->n, ld = st->q->ld, R = st->R;
+    CK(cudaDeviceSynchronize());
+    if (T) CK(cudaMemcpy2D(T, (size_t)n * 4, st->T, (size_t)ld * 4, (size_t)n * 4, R, cudaMemcpyDeviceToHost));
+    if (C) CK(cudaMemcpy2D(C, (size_t)n * 4, st->C, (size_t)ld * 4, (size_t)n * 4, R, cudaMemcpyDeviceToHost));
+    return ICD2S_OK;
+}
+
+int icd2s_get_control(icd2s_state* st, int32_t* A, int32_t* gamma, int32_t* delta)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    REQ(st->have_select, ICD2S_ERR_STATE, "no selection has been made yet");
+    const int n = st->q->n, ld = st->q->ld, R = st->R;
+    CK(cudaDeviceSynchronize());
+    if (A) CK(cudaMemcpy2D(A, (size_t)n * 4, st->A, (size_t)ld * 4, (size_t)n * 4, R, cudaMemcpyDeviceToHost));
+    if (delta)
+        CK(cudaMemcpy2D(delta, (size_t)n * 4, st->delta, (size_t)ld * 4, (size_t)n * 4, R, cudaMemcpyDeviceToHost));
+    if (gamma) CK(cudaMemcpy(gamma, st->gamma, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    return ICD2S_OK;
+}
+
+// ----------------------------------------------------------------------------- steps
+int icd2s_tabu(icd2s_state* st, int32_t alpha, int32_t c, void* stream)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    const int n = st->q->n;
+    REQ(alpha >= 0, ICD2S_ERR_ARG, "alpha < 0");
+    REQ(c >= 1 && c <= n, ICD2S_ERR_ARG, "tenure c=%d outside 1..n", c);
+    REQ(tabu_smem_bytes(n, alpha) <= 227 * 1024, ICD2S_ERR_RANGE, "alpha=%d too large for n=%d", alpha, n);
+    CK(launch_tabu(st->d, alpha, c, st->tabu_w, S(stream)));
+    return ICD2S_OK;
+}
+
+static int select_impl(icd2s_state* st, int64_t w1, int64_t w2, int64_t w3, int K, int m_min, int m_max,
+                       uint32_t iter, cudaStream_t s)
+{
+    const int n = st->q->n;
+    REQ(K >= 1 && K <= 64, ICD2S_ERR_RANGE, "K=%d outside 1..64", K);
+    REQ(m_min >= 1 && m_min <= m_max && m_max <= kMaxM, ICD2S_ERR_RANGE, "sizes %d..%d outside 1..256", m_min, m_max);
+    REQ((long long)K * m_max <= n, ICD2S_ERR_ARG, "K*m_max exceeds n");
+    const int64_t wl = (int64_t)1 << 24;
+    REQ(w1 >= -wl && w1 <= wl && w2 >= -wl && w2 <= wl && w3 >= -wl && w3 <= wl, ICD2S_ERR_RANGE, "|w| > 2^24");
+    CK(launch_gamma(st->d, s));
+    CK(launch_sizes(st->R, K, m_min, m_max, st->d.k0, st->d.k1, iter, st->off, s));
+    CK(launch_select(st->d, w1, w2, w3, K, st->off, st->idx, s));
+    st->have_select = true;
+    st->sel_K = K;
+    return ICD2S_OK;
+}
+
+int icd2s_select_subqubos(icd2s_state* st, const icd2s_select_params* sp, int32_t* idx_dev, int32_t* off_dev,
+                          void* stream)
+{
+    REQ(st && sp && idx_dev && off_dev, ICD2S_ERR_ARG, "NULL argument");
+    cudaStream_t s = S(stream);
+    int rc = select_impl(st, sp->w1, sp->w2, sp->w3, sp->K, sp->m_min, sp->m_max, sp->iter, s);
+    if (rc) return rc;
+    const int cnt = st->R * sp->K;
+    int total = 0;
+    CK(cudaMemcpyAsync(&total, st->off + cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpyAsync(off_dev, st->off, sizeof(int) * (cnt + 1), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(idx_dev, st->idx, sizeof(int) * (size_t)total, cudaMemcpyDeviceToDevice, s));
+    return ICD2S_OK;
+}
+
+static int anneal_impl(icd2s_state* st, const int32_t* idx, const int32_t* off, int count, int per_replica,
+                       int m_max, int block_m, int block_base, int sweeps, double T_max, double T_min, uint32_t iter,
+                       uint8_t* mask, int ldm, int64_t* dE, cudaStream_t s)
+{
+    int rc = ensure_beta(st, sweeps, T_max, T_min, s);
+    if (rc) return rc;
+    AnnealArgs a{};
+    a.idx = idx; a.off = off; a.count = count; a.per_replica = per_replica; a.block_m = block_m;
+    a.block_base = block_base; a.beta = st->beta; a.sweeps = sweeps; a.nlog = st->nlog; a.iter = iter;
+    a.slot_base = 0; a.mask = mask; a.ldm = ldm; a.dE = dE; a.attempts_acc = st->counters; a.m_max = m_max;
+    CK(launch_anneal(st->d, a, s));
+    return ICD2S_OK;
+}
+
+int icd2s_anneal_subqubos_batch(icd2s_state* st, const int32_t* idx_dev, const int32_t* off_dev, int32_t count,
+                                const icd2s_anneal_params* ap, uint8_t* flips_dev, int64_t* dE_dev, void* stream)
+{
+    REQ(st && idx_dev && off_dev && ap && flips_dev, ICD2S_ERR_ARG, "NULL argument");
+    REQ(count >= 0, ICD2S_ERR_ARG, "count < 0");
+    REQ(ap->per_replica >= 1 && (long long)count <= (long long)st->R * ap->per_replica, ICD2S_ERR_ARG,
+        "count=%d exceeds replicas * per_replica", count);
+    REQ(ap->sweeps >= 1 && ap->T_min > 0 && ap->T_max >= ap->T_min, ICD2S_ERR_ARG, "bad anneal parameters");
+    cudaStream_t s = S(stream);
+    const int n = st->q->n;
+    std::vector<int32_t> off((size_t)count + 1);
+    CK(cudaMemcpyAsync(off.data(), off_dev, sizeof(int32_t) * (count + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int m_max = 1;
+    for (int i = 0; i < count; ++i) {
+        const int m = off[i + 1] - off[i];
+        REQ(m >= 1 && m <= kMaxM && m <= n, ICD2S_ERR_RANGE, "subQUBO %d has size %d (allowed 1..256, <= n)", i, m);
+        if (m > m_max) m_max = m;
+    }
+    CK(cudaMemsetAsync(flips_dev, 0, (size_t)st->R * n, s));
+    return anneal_impl(st, idx_dev, off_dev, count, ap->per_replica, m_max, 0, 0, ap->sweeps, ap->T_max, ap->T_min,
+                       ap->iter, flips_dev, n, dE_dev, s);
+}
+
+int icd2s_apply_flips_update_gains(icd2s_state* st, const uint8_t* flips_dev, void* stream)
+{
+    REQ(st && flips_dev, ICD2S_ERR_ARG, "NULL argument");
+    cudaStream_t s = S(stream);
+    CK(launch_compact_mask(st->d, flips_dev, st->q->n, s));
+    CK(launch_apply(st->d, s));
+    return ICD2S_OK;
+}
+
+static int mutate_impl(icd2s_state* st, int mut_mode, double mut_rate, uint32_t iter, uint8_t* mask, cudaStream_t s)
+{
+    REQ(st->have_select, ICD2S_ERR_STATE, "mutate needs a selection (icd2s_select_subqubos) first");
+    REQ(mut_mode == 0 || (mut_mode == 1 && mut_rate >= 0 && mut_rate <= 1), ICD2S_ERR_ARG, "bad mutation rate");
+    const double r = mut_mode == 0 ? mutation_rate((int)iter) : mut_rate;
+    if (mask) CK(cudaMemsetAsync(mask, 0, (size_t)st->R * st->q->n, s));
+    CK(launch_mutate(st->d, st->sel_K, st->off, r, iter, mask, st->q->n, s));
+    CK(launch_apply(st->d, s));
+    return ICD2S_OK;
+}
+
+int icd2s_mutate(icd2s_state* st, const icd2s_mutate_params* mp, uint8_t* flips_dev, void* stream)
+{
+    REQ(st && mp, ICD2S_ERR_ARG, "NULL argument");
+    return mutate_impl(st, mp->mut_mode, mp->mut_rate, mp->iter, flips_dev, S(stream));
+}
+
+int icd2s_best_update(icd2s_state* st, void* stream)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    CK(launch_best(st->d, nullptr, 0, S(stream)));
+    return ICD2S_OK;
+}
+
+int icd2s_initial_pass(icd2s_state* st, const icd2s_params* p, void* stream)
+{
+    REQ(st && p, ICD2S_ERR_ARG, "NULL argument");
+    int rc = check_params(st, p);
+    if (rc) return rc;
+    cudaStream_t s = S(stream);
+    const int m = p->m_init > 0 ? p->m_init : p->m_max;
+    for (int l = 0; l < st->q->n / m; ++l) {
+        rc = anneal_impl(st, nullptr, nullptr, st->R, 1, m, m, l * m, p->sweeps, p->T_max, p->T_min,
+                         0x80000000u | (uint32_t)l, nullptr, 0, nullptr, s);
+        if (rc) return rc;
+        CK(launch_apply(st->d, s));
+    }
+    return ICD2S_OK;
+}
+
+static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* trace_it, cudaStream_t s)
+{
+    const int R = st->R;
+    int rc = ensure_beta(st, p->sweeps, p->T_max, p->T_min, s);
+    if (rc) return rc;
+    mark(st, 0, 0, s);
+    CK(launch_tabu(st->d, p->alpha, p->c, st->tabu_w, s));                       // Algorithm 1
+    mark(st, 0, 1, s);
+    CK(launch_best(st->d, trace_it, 0, s));
+    mark(st, 1, 0, s);
+    rc = select_impl(st, p->w1, p->w2, p->w3, p->K, p->m_min, p->m_max, (uint32_t)t, s);  // Eq. 6-8, Alg. 3
+    if (rc) return rc;
+    mark(st, 1, 1, s);
+    mark(st, 2, 0, s);
+    rc = anneal_impl(st, st->idx, st->off, R * p->K, p->K, p->m_max, 0, 0, p->sweeps, p->T_max, p->T_min,
+                     (uint32_t)t, nullptr, 0, nullptr, s);                        // Eq. 4, Algorithm 4
+    if (rc) return rc;
+    mark(st, 2, 1, s);
+    mark(st, 3, 0, s);
+    CK(launch_apply(st->d, s));
+    mark(st, 3, 1, s);
+    CK(launch_best(st->d, trace_it ? trace_it + R : nullptr, 0, s));
+    const double r = p->mut_mode == 0 ? mutation_rate(t) : p->mut_rate;        // Eq. 5
+    mark(st, 4, 0, s);
+    CK(launch_mutate(st->d, st->sel_K, st->off, r, (uint32_t)t, nullptr, st->q->n, s));
+    mark(st, 4, 1, s);
+    mark(st, 5, 0, s);
+    CK(launch_apply(st->d, s));
+    mark(st, 5, 1, s);
+    mark(st, 6, 0, s);
+    CK(launch_best(st->d, trace_it ? trace_it + 2 * R : nullptr, 1, s));
+    mark(st, 6, 1, s);
+    st->timed_step = st->timing;
+    return ICD2S_OK;
+}
+
+int icd2s_set_timing(icd2s_state* st, int32_t enable)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    if (enable && !st->ev[0])
+        for (cudaEvent_t& e : st->ev) CK(cudaEventCreate(&e));
+    st->timing = enable != 0;
+    st->timed_step = false;
+    return ICD2S_OK;
+}
+
+int icd2s_get_phase_ms(icd2s_state* st, double* ms)
+{
+    REQ(st && ms, ICD2S_ERR_ARG, "NULL argument");
+    REQ(st->timed_step, ICD2S_ERR_STATE, "no timed step: enable icd2s_set_timing, then run icd2s_step");
+    CK(cudaEventSynchronize(st->ev[2 * ICD2S_PHASES - 1]));
+    for (int ph = 0; ph < ICD2S_PHASES; ++ph) {
+        float f = 0.f;
+        CK(cudaEventElapsedTime(&f, st->ev[2 * ph], st->ev[2 * ph + 1]));
+        ms[ph] = f;
+    }
+    return ICD2S_OK;
+}
+
+int icd2s_kernel_launches(uint64_t* count)
+{
+    REQ(count, ICD2S_ERR_ARG, "NULL argument");
+    *count = g_launches.load();
+    return ICD2S_OK;
+}
+
+int icd2s_step(icd2s_state* st, const icd2s_params* p, int32_t t, void* stream)
+{
+    REQ(st && p, ICD2S_ERR_ARG, "NULL argument");
+    int rc = check_params(st, p);
+    if (rc) return rc;
+    REQ(t >= 0, ICD2S_ERR_ARG, "t < 0");
+    return step_impl(st, p, t, nullptr, S(stream));
+}
+
+int icd2s_step_host(icd2s_state* st, const icd2s_params* p, int32_t t, const uint8_t* x_in, uint8_t* x_out,
+                    int64_t* E_out, void* stream)
+{
+    REQ(st && p, ICD2S_ERR_ARG, "NULL argument");
+    int rc = check_params(st, p);
+    if (rc) return rc;
+    cudaStream_t s = S(stream);
+    const int n = st->q->n, ld = st->q->ld, R = st->R;
+    if (x_in) {
+        CK(cudaMemcpyAsync(st->scratch, x_in, (size_t)R * n, cudaMemcpyHostToDevice, s));
+        CK(launch_pad_rows(st->scratch, n, R, st->X, ld, s));
+        CK(launch_recompute(st->d, st->X, ld, R, st->G, st->E, s));
+    }
+    rc = step_impl(st, p, t, nullptr, s);
+    if (rc) return rc;
+    if (x_out) CK(cudaMemcpy2DAsync(x_out, n, st->X, ld, n, R, cudaMemcpyDeviceToHost, s));
+    if (E_out) CK(cudaMemcpyAsync(E_out, st->E, (size_t)R * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return ICD2S_OK;
+}
+
+int icd2s_run(icd2s_qubo* q, const icd2s_params* p, uint64_t seed, uint8_t* x_out, int64_t* E_out,
+              icd2s_stats* stats, int64_t* trace, uint8_t* S_out)
+{
+    REQ(q && p, ICD2S_ERR_ARG, "NULL argument");
+    icd2s_state* st = nullptr;
+    REQ(p->z >= 1 && p->z <= kMaxReplicas, ICD2S_ERR_RANGE, "z=%d outside 1..%d", p->z, kMaxReplicas);
+    int rc = icd2s_state_create(q, p->z, seed, &st);
+    if (rc) return rc;
+    struct Guard { icd2s_state* s; int64_t* tr; cudaEvent_t e0, e1; ~Guard() {
+        if (tr) cudaFree(tr);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        icd2s_state_destroy(s); } } guard{st, nullptr, nullptr, nullptr};
+    rc = check_params(st, p);
+    if (rc) return rc;
+    const int R = st->R;
+    const size_t tr_len = (size_t)(p->max_iters > 0 ? p->max_iters : 1) * (3 * R + 1);
+    if (trace) CK(dalloc(&guard.tr, tr_len));
+    CK(cudaEventCreate(&guard.e0));
+    CK(cudaEventCreate(&guard.e1));
+    cudaStream_t s = 0;
+    CK(cudaEventRecord(guard.e0, s));
+    rc = icd2s_initial_pass(st, p, s);
+    if (rc) return rc;
+    CK(launch_best(st->d, nullptr, 0, s));
+    CK(cudaMemsetAsync(st->flags, 0, 8, s));
+    int64_t init_best = 0;
+    CK(cudaMemcpyAsync(&init_best, st->best_E, 8, cudaMemcpyDeviceToHost, s));
+    int t = 0;
+    int32_t flags[2] = {0, 0};
+    while (t < p->max_iters && (p->patience <= 0 || flags[1] < p->patience)) {
+        rc = step_impl(st, p, t, guard.tr ? guard.tr + (size_t)t * (3 * R + 1) : nullptr, s);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(flags, st->flags, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        ++t;
+    }
+    CK(cudaEventRecord(guard.e1, s));
+    CK(cudaStreamSynchronize(s));
+    int64_t bestE = 0;
+    CK(cudaMemcpy(&bestE, st->best_E, 8, cudaMemcpyDeviceToHost));
+    if (x_out) CK(cudaMemcpy(x_out, st->best_x, q->n, cudaMemcpyDeviceToHost));
+    if (E_out) *E_out = bestE;
+    if (trace && t > 0) CK(cudaMemcpy(trace, guard.tr, sizeof(int64_t) * (size_t)t * (3 * R + 1), cudaMemcpyDeviceToHost));
+    if (S_out) CK(cudaMemcpy2D(S_out, q->n, st->X, q->ld, q->n, R, cudaMemcpyDeviceToHost));
+    if (stats) {
+        int64_t att = 0;
+        CK(cudaMemcpy(&att, st->counters, 8, cudaMemcpyDeviceToHost));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, guard.e0, guard.e1));
+        stats->iters = t; stats->best_E = bestE; stats->init_best_E = init_best; stats->anneal_attempts = att;
+        stats->tabu_moves = (int64_t)t * R * p->alpha; stats->device_ms = ms;
+    }
+    return ICD2S_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// common.cuh -- internal declarations of the IC-D2S sm_103a library.
+//
+// Device layouts (all row-major, rows padded to LD = round_up(n, 128) bytes /
+// elements so that every row starts 16-byte aligned and vector loads never
+// need a tail case; padding entries are zero and never selected):
+//   Q      int8  [n][LD]       the QUBO matrix (Eq. 1)
+//   diag   int32 [LD]          Q_ii
+//   etahat int32 [LD]          eta_j / max eta in Q16 (Eq. 6)
+//   X      uint8 [R][LD]       solutions (replicas)
+//   G      int32 [R][LD]       1-flip gains g_i = (1-2x_i)(Q_ii + 2 sum_{j!=i} Q_ij x_j)
+//   E      int64 [R]           energies (Eq. 1)
+//   T, C   int32 [R][LD]       Tabu toggle counts and final tabu memory (Algorithm 1)
+//   A      int32 [R][LD]       aggregated control parameter (Algorithm 3, Q16)
+//   order  int32 [R][LD]       variables ranked by (A desc, index asc)
+//   sel    uint8 [R][LD]       1 where the variable is in S' (last selection)
+//   FL     int32 [R][LD]       flip lists: index | (old x << 31), FCNT[R] entries
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace icd2s {
+
+constexpr int kLdAlign = 128;
+constexpr int kMaxN = 16384;
+constexpr int kMaxM = 256;
+constexpr int kMaxReplicas = 4096;
+
+constexpr uint32_t kTagInit = 1u, kTagAnneal = 2u, kTagMut = 3u, kTagSize = 4u;
+
+inline int round_up(int v, int a) { return (v + a - 1) / a * a; }
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): the two Philox
+// multipliers act on words 0 and 2; the high halves are mixed with words 1/3
+// and the round key; the key advances by the two Weyl increments per round.
+struct u32x4 { uint32_t v[4]; };
+
+__host__ __device__ __forceinline__ u32x4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                   uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+#if defined(__CUDA_ARCH__)
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+#else
+        const uint64_t m0 = (uint64_t)0xD2511F53u * c0, m1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t lo0 = (uint32_t)m0, hi0 = (uint32_t)(m0 >> 32);
+        const uint32_t lo1 = (uint32_t)m1, hi1 = (uint32_t)(m1 >> 32);
+#endif
+        const uint32_t t0 = hi1 ^ c1 ^ k0, t2 = hi0 ^ c3 ^ k1;
+        c0 = t0; c1 = lo1; c2 = t2; c3 = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+    u32x4 o; o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+    return o;
+}
+
+// Device view of one problem + solution set, passed by value to kernels.
+struct Dev {
+    const int8_t* Q;       // [n][ld]
+    const int32_t* diag;   // [ld]
+    const int32_t* etahat; // [ld]
+    int n, ld, R;
+    uint8_t* X; int32_t* G; int64_t* E;
+    int32_t* T; int32_t* C;
+    int32_t* gamma; int32_t* A; int32_t* delta; int32_t* order; uint8_t* sel;
+    int32_t* FL; int32_t* FCNT; unsigned long long* DEACC; unsigned int* DONE;
+    uint8_t* best_x; int64_t* best_E; int32_t* flags; // flags[0] improved, [1] stale, [2] error
+    uint32_t k0, k1; // Philox key = seed halves
+};
+
+// Counts kernel launches (process-wide, for reporting).
+void note_launch(int kernels);
+
+// ---- launchers (each returns cudaGetLastError() of its launch) ----
+cudaError_t launch_prepare(const int8_t* Q, int n, int ld, int32_t* eta, int32_t* etahat, int32_t* diag,
+                           int* mismatches, cudaStream_t s);
+cudaError_t launch_init_x(const Dev& d, cudaStream_t s);
+cudaError_t launch_recompute(const Dev& d, const uint8_t* X, int ldx, int R, int32_t* G, int64_t* E,
+                             cudaStream_t s);  // gains + energies of X (padded rows)
+cudaError_t launch_pad_rows(const uint8_t* src, int n, int rows, uint8_t* dst, int ld, cudaStream_t s);
+cudaError_t launch_tabu(const Dev& d, int alpha, int c, int w_words, cudaStream_t s);
+size_t tabu_smem_bytes(int n, int alpha);
+cudaError_t launch_gamma(const Dev& d, cudaStream_t s);
+cudaError_t launch_sizes(int R, int K, int m_min, int m_max, uint32_t k0, uint32_t k1, uint32_t iter,
+                         int32_t* off, cudaStream_t s);
+cudaError_t launch_select(const Dev& d, int64_t w1, int64_t w2, int64_t w3, int K, const int32_t* off,
+                          int32_t* idx, cudaStream_t s);
+cudaError_t launch_mutate(const Dev& d, int K, const int32_t* off, double rate, uint32_t iter,
+                          uint8_t* mask, int ldm, cudaStream_t s);
+struct AnnealArgs {
+    const int32_t* idx; const int32_t* off; int count; int per_replica;
+    int block_m; int block_base;          // idx == nullptr: contiguous block [base, base+m)
+    const uint32_t* beta; int sweeps; const uint32_t* nlog; uint32_t iter; uint32_t slot_base;
+    uint8_t* mask; int ldm;               // mask output (nullptr: flip lists FL/FCNT)
+    int64_t* dE; int64_t* attempts_acc;   // optional outputs
+    int m_max;
+};
+cudaError_t launch_anneal(const Dev& d, const AnnealArgs& a, cudaStream_t s);
+cudaError_t launch_compact_mask(const Dev& d, const uint8_t* mask, int ldm, cudaStream_t s);
+cudaError_t launch_apply(const Dev& d, cudaStream_t s);
+cudaError_t launch_best(const Dev& d, int64_t* trace_slot, int iter_end, cudaStream_t s);
+
+}  // namespace icd2s

@@ -1,0 +1,299 @@
+"""Thin ctypes binding of ``libicd2s.so`` (declared in ``include/icd2s.h``).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+Each ``icd2s_*`` function here calls the C entry point of the same name and
+raises ``ICD2SError`` on a non-zero status.  Device buffers are passed as raw
+addresses (e.g. ``torch.Tensor.data_ptr()``), streams as ``cudaStream_t``
+integers (e.g. ``torch.cuda.current_stream().cuda_stream``) or 0.
+
+There is no CPU fallback: if the shared library is missing the first call
+raises, naming the build step (``python -m paper_2502_13947_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libicd2s.so")
+
+OK, ERR_ARG, ERR_ASYMMETRIC, ERR_RANGE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_INVARIANT, ERR_STATE = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+
+# every entry point declared in include/icd2s.h
+EXPORTS = (
+    "icd2s_last_error", "icd2s_version", "icd2s_default_params", "icd2s_qubo_create", "icd2s_qubo_destroy",
+    "icd2s_qubo_size", "icd2s_energy", "icd2s_state_create", "icd2s_state_destroy", "icd2s_state_load",
+    "icd2s_get_state", "icd2s_get_best", "icd2s_tabu", "icd2s_get_tabu", "icd2s_select_subqubos",
+    "icd2s_get_control", "icd2s_anneal_subqubos_batch", "icd2s_apply_flips_update_gains", "icd2s_mutate",
+    "icd2s_best_update", "icd2s_initial_pass", "icd2s_step", "icd2s_step_host", "icd2s_run", "icd2s_tables",
+    "icd2s_set_timing", "icd2s_get_phase_ms", "icd2s_kernel_launches",
+)
+PHASES = ("tabu", "select", "anneal", "apply_anneal", "mutate", "apply_mutate", "best")
+
+
+class ICD2SError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("icd2s error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("z", C.c_int32), ("K", C.c_int32), ("m_min", C.c_int32), ("m_max", C.c_int32), ("m_init", C.c_int32),
+        ("alpha", C.c_int32), ("c", C.c_int32), ("sweeps", C.c_int32), ("T_max", C.c_double), ("T_min", C.c_double),
+        ("w1", C.c_int64), ("w2", C.c_int64), ("w3", C.c_int64), ("mut_mode", C.c_int32), ("mut_rate", C.c_double),
+        ("patience", C.c_int32), ("max_iters", C.c_int32), ("reserved", C.c_int32 * 8),
+    ]
+
+
+class AnnealParams(C.Structure):
+    _fields_ = [("sweeps", C.c_int32), ("T_max", C.c_double), ("T_min", C.c_double), ("iter", C.c_uint32),
+                ("per_replica", C.c_int32)]
+
+
+class SelectParams(C.Structure):
+    _fields_ = [("w1", C.c_int64), ("w2", C.c_int64), ("w3", C.c_int64), ("K", C.c_int32), ("m_min", C.c_int32),
+                ("m_max", C.c_int32), ("iter", C.c_uint32)]
+
+
+class MutateParams(C.Structure):
+    _fields_ = [("mut_mode", C.c_int32), ("mut_rate", C.c_double), ("iter", C.c_uint32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("best_E", C.c_int64), ("init_best_E", C.c_int64),
+                ("anneal_attempts", C.c_int64), ("tabu_moves", C.c_int64), ("device_ms", C.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Loads the library (once).  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ICD2SError(ERR_STATE, "%s is missing: build it with `python -m paper_2502_13947_gb300.build` "
+                                            "(or __graft_entry__.build())" % LIB_PATH)
+            L = C.CDLL(LIB_PATH)
+            vp, i32, i64, u32, u64, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
+            P = C.POINTER
+            sig = {
+                "icd2s_last_error": (C.c_char_p, []),
+                "icd2s_version": (i32, []),
+                "icd2s_default_params": (C.c_int, [i32, P(Params)]),
+                "icd2s_qubo_create": (C.c_int, [vp, i32, P(vp)]),
+                "icd2s_qubo_destroy": (C.c_int, [vp]),
+                "icd2s_qubo_size": (C.c_int, [vp, P(i32)]),
+                "icd2s_energy": (C.c_int, [vp, vp, i32, vp, vp]),
+                "icd2s_state_create": (C.c_int, [vp, i32, u64, P(vp)]),
+                "icd2s_state_destroy": (C.c_int, [vp]),
+                "icd2s_state_load": (C.c_int, [vp, vp, i32, vp]),
+                "icd2s_get_state": (C.c_int, [vp, vp, vp, vp]),
+                "icd2s_get_best": (C.c_int, [vp, vp, vp]),
+                "icd2s_tabu": (C.c_int, [vp, i32, i32, vp]),
+                "icd2s_get_tabu": (C.c_int, [vp, vp, vp]),
+                "icd2s_select_subqubos": (C.c_int, [vp, P(SelectParams), vp, vp, vp]),
+                "icd2s_get_control": (C.c_int, [vp, vp, vp, vp]),
+                "icd2s_anneal_subqubos_batch": (C.c_int, [vp, vp, vp, i32, P(AnnealParams), vp, vp, vp]),
+                "icd2s_apply_flips_update_gains": (C.c_int, [vp, vp, vp]),
+                "icd2s_mutate": (C.c_int, [vp, P(MutateParams), vp, vp]),
+                "icd2s_best_update": (C.c_int, [vp, vp]),
+                "icd2s_initial_pass": (C.c_int, [vp, P(Params), vp]),
+                "icd2s_step": (C.c_int, [vp, P(Params), i32, vp]),
+                "icd2s_step_host": (C.c_int, [vp, P(Params), i32, vp, vp, vp, vp]),
+                "icd2s_run": (C.c_int, [vp, P(Params), u64, vp, vp, P(Stats), vp, vp]),
+                "icd2s_tables": (C.c_int, [i32, f64, f64, vp, vp]),
+                "icd2s_set_timing": (C.c_int, [vp, i32]),
+                "icd2s_get_phase_ms": (C.c_int, [vp, vp]),
+                "icd2s_kernel_launches": (C.c_int, [P(u64)]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+        return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise ICD2SError(rc, lib().icd2s_last_error().decode(errors="replace"))
+
+
+def _np(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _s(stream):
+    return C.c_void_p(int(stream) if stream else 0)
+
+
+# --------------------------------------------------------------------------- entry points
+def icd2s_version() -> int:
+    return int(lib().icd2s_version())
+
+
+def icd2s_default_params(n: int, **overrides) -> Params:
+    p = Params()
+    _check(lib().icd2s_default_params(n, C.byref(p)))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def icd2s_qubo_create(Q: np.ndarray) -> C.c_void_p:
+    Q = np.ascontiguousarray(Q, dtype=np.int8)
+    if Q.ndim != 2 or Q.shape[0] != Q.shape[1]:
+        raise ValueError("Q must be square")
+    h = C.c_void_p()
+    _check(lib().icd2s_qubo_create(_np(Q), Q.shape[0], C.byref(h)))
+    return h
+
+
+def icd2s_qubo_destroy(h) -> None:
+    _check(lib().icd2s_qubo_destroy(h))
+
+
+def icd2s_qubo_size(h) -> int:
+    n = C.c_int32()
+    _check(lib().icd2s_qubo_size(h, C.byref(n)))
+    return n.value
+
+
+def icd2s_energy(q, x_dev: int, count: int, E_dev: int, stream=0) -> None:
+    _check(lib().icd2s_energy(q, C.c_void_p(x_dev), count, C.c_void_p(E_dev), _s(stream)))
+
+
+def icd2s_state_create(q, replicas: int, seed: int) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().icd2s_state_create(q, replicas, C.c_uint64(seed), C.byref(h)))
+    return h
+
+
+def icd2s_state_destroy(st) -> None:
+    _check(lib().icd2s_state_destroy(st))
+
+
+def icd2s_state_load(st, x, x_is_device: bool = False, stream=0) -> None:
+    if x_is_device:
+        _check(lib().icd2s_state_load(st, C.c_void_p(int(x)), 1, _s(stream)))
+    else:
+        x = np.ascontiguousarray(x, dtype=np.uint8)
+        _check(lib().icd2s_state_load(st, _np(x), 0, _s(stream)))
+
+
+def icd2s_get_state(st, R: int, n: int):
+    x = np.zeros((R, n), np.uint8)
+    g = np.zeros((R, n), np.int32)
+    E = np.zeros(R, np.int64)
+    _check(lib().icd2s_get_state(st, _np(x), _np(g), _np(E)))
+    return x, g, E
+
+
+def icd2s_get_best(st, n: int):
+    x = np.zeros(n, np.uint8)
+    E = np.zeros(1, np.int64)
+    _check(lib().icd2s_get_best(st, _np(x), _np(E)))
+    return x, int(E[0])
+
+
+def icd2s_tabu(st, alpha: int, c: int, stream=0) -> None:
+    _check(lib().icd2s_tabu(st, alpha, c, _s(stream)))
+
+
+def icd2s_get_tabu(st, R: int, n: int):
+    T = np.zeros((R, n), np.int32)
+    Cm = np.zeros((R, n), np.int32)
+    _check(lib().icd2s_get_tabu(st, _np(T), _np(Cm)))
+    return T, Cm
+
+
+def icd2s_select_subqubos(st, sp: SelectParams, idx_dev: int, off_dev: int, stream=0) -> None:
+    _check(lib().icd2s_select_subqubos(st, C.byref(sp), C.c_void_p(idx_dev), C.c_void_p(off_dev), _s(stream)))
+
+
+def icd2s_get_control(st, R: int, n: int):
+    A = np.zeros((R, n), np.int32)
+    gam = np.zeros(n, np.int32)
+    dl = np.zeros((R, n), np.int32)
+    _check(lib().icd2s_get_control(st, _np(A), _np(gam), _np(dl)))
+    return A, gam, dl
+
+
+def icd2s_anneal_subqubos_batch(st, idx_dev: int, off_dev: int, count: int, ap: AnnealParams, flips_dev: int,
+                                dE_dev: int = 0, stream=0) -> None:
+    _check(lib().icd2s_anneal_subqubos_batch(st, C.c_void_p(idx_dev), C.c_void_p(off_dev), count, C.byref(ap),
+                                             C.c_void_p(flips_dev), C.c_void_p(dE_dev or None), _s(stream)))
+
+
+def icd2s_apply_flips_update_gains(st, flips_dev: int, stream=0) -> None:
+    _check(lib().icd2s_apply_flips_update_gains(st, C.c_void_p(flips_dev), _s(stream)))
+
+
+def icd2s_mutate(st, mp: MutateParams, flips_dev: int = 0, stream=0) -> None:
+    _check(lib().icd2s_mutate(st, C.byref(mp), C.c_void_p(flips_dev or None), _s(stream)))
+
+
+def icd2s_best_update(st, stream=0) -> None:
+    _check(lib().icd2s_best_update(st, _s(stream)))
+
+
+def icd2s_initial_pass(st, p: Params, stream=0) -> None:
+    _check(lib().icd2s_initial_pass(st, C.byref(p), _s(stream)))
+
+
+def icd2s_step(st, p: Params, t: int, stream=0) -> None:
+    _check(lib().icd2s_step(st, C.byref(p), t, _s(stream)))
+
+
+def icd2s_step_host(st, p: Params, t: int, x_in=None, x_out=None, E_out=None, stream=0) -> None:
+    """Host-buffer step.  x_in / x_out / E_out are numpy arrays (pinned memory
+    may be passed as numpy views of pinned torch tensors) or None."""
+    _check(lib().icd2s_step_host(st, C.byref(p), t, _np(x_in), _np(x_out), _np(E_out), _s(stream)))
+
+
+def icd2s_run(q, p: Params, seed: int, trace: bool = False, want_S: bool = False):
+    n = icd2s_qubo_size(q)
+    x = np.zeros(n, np.uint8)
+    E = np.zeros(1, np.int64)
+    st = Stats()
+    tr = np.zeros((max(p.max_iters, 1), 3 * p.z + 1), np.int64) if trace else None
+    S = np.zeros((p.z, n), np.uint8) if want_S else None
+    _check(lib().icd2s_run(q, C.byref(p), C.c_uint64(seed), _np(x), _np(E), C.byref(st), _np(tr), _np(S)))
+    out = dict(best_x=x, best_E=int(E[0]), iters=st.iters, init_best_E=st.init_best_E,
+               anneal_attempts=st.anneal_attempts, tabu_moves=st.tabu_moves, device_ms=st.device_ms)
+    if trace:
+        out["trace"] = tr[:st.iters]
+    if want_S:
+        out["S"] = S
+    return out
+
+
+def icd2s_tables(sweeps: int, T_max: float, T_min: float):
+    b = np.zeros(max(sweeps, 1), np.uint32)
+    t = np.zeros(4096, np.uint32)
+    _check(lib().icd2s_tables(sweeps, T_max, T_min, _np(b), _np(t)))
+    return b[:sweeps], t
+
+
+def icd2s_set_timing(st, enable: bool = True) -> None:
+    _check(lib().icd2s_set_timing(st, 1 if enable else 0))
+
+
+def icd2s_get_phase_ms(st) -> dict:
+    ms = np.zeros(len(PHASES), np.float64)
+    _check(lib().icd2s_get_phase_ms(st, _np(ms)))
+    return dict(zip(PHASES, ms.tolist()))
+
+
+def icd2s_kernel_launches() -> int:
+    c = C.c_uint64()
+    _check(lib().icd2s_kernel_launches(C.byref(c)))
+    return int(c.value)

@@ -1,0 +1,86 @@
+"""The C-ABI library without a GPU: it builds for sm_103a, loads, exports
+every entry point that include/icd2s.h declares, computes its host tables
+exactly as the oracle does, and rejects bad arguments before touching CUDA."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2502_13947_gb300 import build as B
+from paper_2502_13947_gb300 import icd2s as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "icd2s.h")
+
+
+@pytest.fixture(scope="module")
+def built():
+    B.build()
+    return I.lib()
+
+
+def declared_entry_points():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const char\*|int32_t|int)\s+(icd2s_\w+)\s*\(", src, re.M)))
+
+
+def test_header_and_binding_agree():
+    assert declared_entry_points() == sorted(I.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(built):
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (icd2s_\w+)", out))
+    missing = set(declared_entry_points()) - exported
+    assert not missing, missing
+    for name in declared_entry_points():
+        assert hasattr(built, name)
+
+
+def test_library_targets_sm_103a_only(built):
+    out = subprocess.run(["cuobjdump", "--list-elf", B.LIB], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    arches = set(re.findall(r"sm_\d+a?", out.stdout))
+    assert arches == {"sm_103a"}, arches
+
+
+def test_host_tables_equal_the_oracles(built, orc):
+    for sweeps, tmax, tmin in [(1, 50.0, 2.0), (7, 100.0, 1.0), (256, 812.5, 0.75), (1024, 3000.0, 1.0)]:
+        b, t = I.icd2s_tables(sweeps, tmax, tmin)
+        assert np.array_equal(b, orc.beta_table(sweeps, tmax, tmin))
+        assert np.array_equal(t, orc.nlog_table())
+
+
+def test_default_params_follow_table_1(built):
+    p = I.icd2s_default_params(2500)
+    assert (p.z, p.alpha, p.c, p.w1, p.w2, p.w3, p.m_max, p.K) == (4, 12500, 16, 65536, 65536, 32768, 50, 1)
+    p = I.icd2s_default_params(64)
+    assert p.c == 2 and p.m_max == 50 and p.alpha == 320
+    assert I.icd2s_default_params(3).m_max == 3
+
+
+def test_argument_errors_are_reported_without_a_gpu(built):
+    with pytest.raises(I.ICD2SError) as e:
+        I.icd2s_default_params(0)
+    assert e.value.code == I.ERR_RANGE and "n=0" in str(e.value)
+    L = built
+    h = ctypes.c_void_p()
+    assert L.icd2s_qubo_create(None, 5, ctypes.byref(h)) == I.ERR_ARG
+    Q = np.zeros((4, 4), np.int8)
+    assert L.icd2s_qubo_create(Q.ctypes.data_as(ctypes.c_void_p), 20000, ctypes.byref(h)) == I.ERR_RANGE
+    assert b"n=20000" in L.icd2s_last_error()
+    assert L.icd2s_state_create(None, 4, 1, ctypes.byref(h)) == I.ERR_ARG
+    assert L.icd2s_tabu(None, 10, 2, None) == I.ERR_ARG
+    assert L.icd2s_qubo_destroy(None) == I.OK and L.icd2s_state_destroy(None) == I.OK
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(I, "LIB_PATH", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(I, "_lib", None)
+    with pytest.raises(I.ICD2SError) as e:
+        I.icd2s_version()
+    assert "missing" in str(e.value)

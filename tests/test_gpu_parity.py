@@ -1,0 +1,280 @@
+"""GPU parity: every step of the CUDA path, called through the C ABI, equals
+the CPU oracle bit for bit on the same seeded inputs (integer, byte and index
+results are exact by construction, so the bar is equality)."""
+import numpy as np
+import pytest
+
+from paper_2502_13947_gb300 import build as B
+from paper_2502_13947_gb300 import icd2s as I
+from paper_2502_13947_gb300.instances import make_qubo, random_solutions, random_subsets
+
+from .gpu_util import dev, lib_params, orc_params, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch_cuda()
+    B.build()
+    return I.lib()
+
+
+class Problem:
+    def __init__(self, n, density, seed, R=None, state_seed=11):
+        self.n = n
+        self.Q = make_qubo(n, density, seed)
+        self.q = I.icd2s_qubo_create(self.Q)
+        self.st = None
+        if R:
+            self.st = I.icd2s_state_create(self.q, R, state_seed)
+            self.R = R
+            self.seed = state_seed
+
+    def load(self, X):
+        I.icd2s_state_load(self.st, X)
+
+    def state(self):
+        return I.icd2s_get_state(self.st, self.R, self.n)
+
+    def close(self):
+        if self.st:
+            I.icd2s_state_destroy(self.st)
+        I.icd2s_qubo_destroy(self.q)
+
+
+# ----------------------------------------------------------------------------- Eq. 1
+@pytest.mark.parametrize("n,count,density", [(1, 1, 1.0), (64, 3, 1.0), (129, 5, 0.5), (300, 70, 0.3),
+                                             (2500, 9, 0.1), (4097, 2, 1.0)])
+def test_energy(L, orc, n, count, density):
+    torch = torch_cuda()
+    P = Problem(n, density, n + count)
+    X = random_solutions(n, count, 3)
+    E = torch.zeros(count, dtype=torch.int64, device="cuda")
+    Xd = dev(X)
+    I.icd2s_energy(P.q, Xd.data_ptr(), count, E.data_ptr())
+    assert np.array_equal(E.cpu().numpy(), orc.energy_batch(P.Q, X))
+    P.close()
+
+
+def test_asymmetric_q_is_rejected(L):
+    Q = make_qubo(40, 1.0, 1)
+    Q[3, 7] = np.int8(Q[7, 3] + 1 if Q[7, 3] < 100 else Q[7, 3] - 1)
+    with pytest.raises(I.ICD2SError) as e:
+        I.icd2s_qubo_create(Q)
+    assert e.value.code == I.ERR_ASYMMETRIC
+
+
+# ----------------------------------------------------------------------------- init
+@pytest.mark.parametrize("n,R", [(64, 1), (300, 7), (1000, 33)])
+def test_initial_solutions_gains_and_energies(L, orc, n, R):
+    P = Problem(n, 1.0, 5, R=R, state_seed=0xABCDEF0123)
+    x, g, E = P.state()
+    assert np.array_equal(x, orc.init_solutions(n, R, 0xABCDEF0123))
+    for p in range(R):
+        assert np.array_equal(g[p], orc.gains(P.Q, x[p]))
+    assert np.array_equal(E, orc.energy_batch(P.Q, x))
+    P.close()
+
+
+# ----------------------------------------------------------------------------- Algorithm 1
+@pytest.mark.parametrize("n,R,alpha,c,density", [
+    (64, 4, 320, 2, 1.0),        # one warp
+    (300, 3, 900, 3, 0.5),       # ragged n
+    (2500, 2, 2000, 16, 0.1),    # 1 group of 4 per thread
+    (5000, 2, 800, 33, 0.5),     # 2 groups per thread
+    (10000, 1, 300, 66, 0.5),    # 3 groups per thread
+    (13001, 1, 150, 86, 0.5),    # 4 groups per thread, ragged
+    (50, 2, 0, 2, 1.0),          # alpha = 0: nothing moves
+    (40, 2, 200, 40, 1.0),       # c = n
+])
+def test_tabu(L, orc, n, R, alpha, c, density):
+    P = Problem(n, density, n, R=R)
+    X0 = random_solutions(n, R, n + alpha)
+    P.load(X0)
+    I.icd2s_tabu(P.st, alpha, c)
+    x, g, E = P.state()
+    T, Cm = I.icd2s_get_tabu(P.st, R, n)
+    for p in range(R):
+        xo, Eo, To, Co = orc.tabu(P.Q, X0[p], alpha, c)
+        assert np.array_equal(x[p], xo), p
+        assert E[p] == Eo
+        assert np.array_equal(T[p], To) and np.array_equal(Cm[p], Co)
+        assert np.array_equal(g[p], orc.gains(P.Q, xo))
+    P.close()
+
+
+# ----------------------------------------------------------------------------- Eq. 6-8, Alg. 3, selection
+@pytest.mark.parametrize("n,R,K,m_min,m_max", [(500, 6, 3, 8, 40), (333, 4, 1, 64, 64), (2500, 3, 16, 32, 150)])
+def test_control_parameters_and_selection(L, orc, n, R, K, m_min, m_max):
+    torch = torch_cuda()
+    P = Problem(n, 0.5, 7, R=R, state_seed=99)
+    X0 = random_solutions(n, R, 1)
+    P.load(X0)
+    I.icd2s_tabu(P.st, 3 * n, 3)
+    x, _, _ = P.state()
+    T, _ = I.icd2s_get_tabu(P.st, R, n)
+    it = 5
+    sp = I.SelectParams(w1=65536, w2=65536, w3=32768, K=K, m_min=m_min, m_max=m_max, iter=it)
+    idx = torch.zeros(R * K * m_max + 1, dtype=torch.int32, device="cuda")
+    off = torch.zeros(R * K + 1, dtype=torch.int32, device="cuda")
+    I.icd2s_select_subqubos(P.st, sp, idx.data_ptr(), off.data_ptr())
+    A, gam, dl = I.icd2s_get_control(P.st, R, n)
+    idx, off = idx.cpu().numpy(), off.cpu().numpy()
+    gam_o = orc.gamma(x)
+    assert np.array_equal(gam, gam_o)
+    eh = orc.eta_hat(orc.eta(P.Q))
+    for p in range(R):
+        d_o = orc.delta(T[p])
+        A_o = orc.aggregate(eh, gam_o, d_o)
+        assert np.array_equal(dl[p], d_o) and np.array_equal(A[p], A_o)
+        sizes = orc.subqubo_sizes(K, m_min, m_max, 99, p, it)
+        assert np.array_equal(np.diff(off[p * K:(p + 1) * K + 1]), sizes)
+        got = idx[off[p * K]:off[(p + 1) * K]]
+        assert np.array_equal(got, orc.select(A_o, sizes))
+    P.close()
+
+
+# ----------------------------------------------------------------------------- Eq. 4, Algorithm 4
+SIZES = [1, 5, 16, 31, 32, 33, 64, 65, 100, 128, 129, 200, 256]
+
+
+@pytest.mark.parametrize("sweeps,T_max", [(1, 50.0), (7, 400.0), (64, 2000.0)])
+def test_anneal(L, orc, sweeps, T_max):
+    torch = torch_cuda()
+    n, R, it = 2000, 3, 17
+    K = len(SIZES) // R + 1
+    P = Problem(n, 1.0, 21, R=R, state_seed=1234)
+    X0 = random_solutions(n, R, 2)
+    P.load(X0)
+    groups, offs = [], [0]
+    count = 0
+    for p in range(R):
+        sz = [SIZES[(p * K + k) % len(SIZES)] for k in range(K)]
+        g = random_subsets(n, sz, 100 + p)
+        off = 0
+        for m in sz:
+            groups.append((p, g[off:off + m]))
+            offs.append(offs[-1] + m)
+            off += m
+            count += 1
+    idx = np.concatenate([g for _, g in groups]).astype(np.int32)
+    off = np.array(offs, np.int32)
+    mask = torch.zeros((R, n), dtype=torch.uint8, device="cuda")
+    dE = torch.zeros(count, dtype=torch.int64, device="cuda")
+    ap = I.AnnealParams(sweeps=sweeps, T_max=T_max, T_min=1.0, iter=it, per_replica=K)
+    I.icd2s_anneal_subqubos_batch(P.st, dev(idx).data_ptr(), dev(off).data_ptr(), count, ap, mask.data_ptr(),
+                                  dE.data_ptr())
+    mask, dE = mask.cpu().numpy(), dE.cpu().numpy()
+    beta = orc.beta_table(sweeps, T_max, 1.0)
+    nlog = orc.nlog_table()
+    want = np.zeros((R, n), np.uint8)
+    for s, (p, S) in enumerate(groups):
+        Qs, _ = orc.subqubo(P.Q, X0[p], S)
+        xs1, dEo, _ = orc.anneal(Qs, X0[p][S], beta, nlog, 1234, s, it)
+        want[p, S] = xs1 != X0[p][S]
+        assert dE[s] == dEo, (s, len(S))
+    assert np.array_equal(mask, want)
+    x, _, _ = P.state()
+    assert np.array_equal(x, X0)  # the anneal call leaves the solutions alone
+    P.close()
+
+
+def test_anneal_rejects_oversized_subqubos(L):
+    torch = torch_cuda()
+    P = Problem(600, 1.0, 1, R=1)
+    off = dev(np.array([0, 257], np.int32))
+    idx = dev(np.arange(257, dtype=np.int32))
+    mask = torch.zeros((1, 600), dtype=torch.uint8, device="cuda")
+    with pytest.raises(I.ICD2SError) as e:
+        I.icd2s_anneal_subqubos_batch(P.st, idx.data_ptr(), off.data_ptr(), 1,
+                                      I.AnnealParams(sweeps=4, T_max=10.0, T_min=1.0, iter=0, per_replica=1),
+                                      mask.data_ptr())
+    assert e.value.code == I.ERR_RANGE
+    P.close()
+
+
+# ----------------------------------------------------------------------------- write-back
+@pytest.mark.parametrize("n,R", [(64, 2), (1000, 5), (2500, 4), (3000, 3)])
+def test_apply_flips_update_gains(L, orc, n, R):
+    P = Problem(n, 0.7, n, R=R)
+    X0 = random_solutions(n, R, 9)
+    P.load(X0)
+    rng = np.random.default_rng(n)
+    M = np.zeros((R, n), np.uint8)
+    M[0] = 0                                            # nothing flips
+    M[1] = rng.random(n) < 0.02
+    if R > 2:
+        M[2] = 1                                        # everything flips
+    for p in range(3, R):
+        M[p] = rng.random(n) < 0.3
+    I.icd2s_apply_flips_update_gains(P.st, dev(M).data_ptr())
+    x, g, E = P.state()
+    X1 = X0 ^ M
+    assert np.array_equal(x, X1)
+    assert np.array_equal(E, orc.energy_batch(P.Q, X1))
+    for p in range(R):
+        assert np.array_equal(g[p], orc.gains(P.Q, X1[p]))
+    # a second round on the updated state
+    I.icd2s_apply_flips_update_gains(P.st, dev(M[::-1].copy()).data_ptr())
+    x, g, E = P.state()
+    X2 = X1 ^ M[::-1]
+    assert np.array_equal(x, X2) and np.array_equal(E, orc.energy_batch(P.Q, X2))
+    P.close()
+
+
+# ----------------------------------------------------------------------------- mutation
+@pytest.mark.parametrize("mode,rate,t", [(0, 0.0, 3), (1, 0.3, 8), (0, 0.0, 15), (1, 1.0, 1)])
+def test_mutate(L, orc, mode, rate, t):
+    torch = torch_cuda()
+    n, R, K, m_min, m_max = 700, 4, 2, 20, 60
+    P = Problem(n, 0.4, 3, R=R, state_seed=77)
+    X0 = random_solutions(n, R, 4)
+    P.load(X0)
+    I.icd2s_tabu(P.st, 2 * n, 4)
+    x1, _, _ = P.state()
+    T, _ = I.icd2s_get_tabu(P.st, R, n)
+    sp = I.SelectParams(w1=65536, w2=65536, w3=32768, K=K, m_min=m_min, m_max=m_max, iter=t)
+    idx = torch.zeros(R * K * m_max + 1, dtype=torch.int32, device="cuda")
+    off = torch.zeros(R * K + 1, dtype=torch.int32, device="cuda")
+    I.icd2s_select_subqubos(P.st, sp, idx.data_ptr(), off.data_ptr())
+    mask = torch.zeros((R, n), dtype=torch.uint8, device="cuda")
+    I.icd2s_mutate(P.st, I.MutateParams(mut_mode=mode, mut_rate=rate, iter=t), mask.data_ptr())
+    x2, g2, E2 = P.state()
+    mask = mask.cpu().numpy()
+    eh = orc.eta_hat(orc.eta(P.Q))
+    gam = orc.gamma(x1)
+    r = orc.mutation_rate(t) if mode == 0 else rate
+    for p in range(R):
+        A = orc.aggregate(eh, gam, orc.delta(T[p]))
+        sizes = orc.subqubo_sizes(K, m_min, m_max, 77, p, t)
+        sel = np.zeros(n, np.uint8)
+        sel[orc.select(A, sizes)] = 1
+        L_ = int(np.floor((n - sizes.sum()) * r))
+        xo, _ = orc.mutate(A, sel, L_, 77, p, t, x1[p])
+        assert np.array_equal(x2[p], xo), p
+        assert np.array_equal(mask[p], (xo != x1[p]).astype(np.uint8))
+        assert E2[p] == orc.energy(P.Q, xo)
+        assert np.array_equal(g2[p], orc.gains(P.Q, xo))
+    P.close()
+
+
+def test_mutate_before_select_is_an_error(L):
+    P = Problem(100, 1.0, 1, R=2)
+    with pytest.raises(I.ICD2SError) as e:
+        I.icd2s_mutate(P.st, I.MutateParams(mut_mode=0, mut_rate=0.0, iter=0))
+    assert e.value.code == I.ERR_STATE
+    P.close()
+
+
+# ----------------------------------------------------------------------------- Call_IM_Solution_Set
+@pytest.mark.parametrize("n,z,m", [(64, 8, 16), (300, 3, 40), (1000, 2, 64)])
+def test_initial_pass(L, orc, n, z, m):
+    P = Problem(n, 1.0, 8, R=z, state_seed=5)
+    lp = lib_params(I, n, z=z, m_min=m, m_max=m, m_init=m, sweeps=32, T_max=500.0)
+    I.icd2s_initial_pass(P.st, lp)
+    x, g, E = P.state()
+    S0 = orc.init_solutions(n, z, 5)
+    So, Eo = orc.initial_pass(P.Q, orc_params(orc, lp), 5, S0)
+    assert np.array_equal(x, So) and np.array_equal(E, Eo)
+    P.close()

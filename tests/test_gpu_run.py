@@ -1,0 +1,104 @@
+"""GPU parity of whole trajectories: Algorithm 2 run by the library (through
+the C ABI) equals the oracle's run bit for bit -- every energy after every
+phase of every iteration, the final solutions and the best solution -- and a
+full-size outer iteration of the n = 2500 workload equals the oracle's."""
+import numpy as np
+import pytest
+
+from paper_2502_13947_gb300 import build as B
+from paper_2502_13947_gb300 import icd2s as I
+from paper_2502_13947_gb300.instances import make_qubo, random_solutions
+
+from .gpu_util import lib_params, orc_params, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch_cuda()
+    B.build()
+    return I.lib()
+
+
+def _compare_runs(orc, Q, lp, seed):
+    q = I.icd2s_qubo_create(Q)
+    try:
+        g = I.icd2s_run(q, lp, seed, trace=True, want_S=True)
+    finally:
+        I.icd2s_qubo_destroy(q)
+    o = orc.run(Q, orc_params(orc, lp), seed)
+    assert g["iters"] == o["iters"]
+    assert g["init_best_E"] == o["init_best_E"]
+    assert np.array_equal(g["trace"], o["trace"])
+    assert np.array_equal(g["S"], o["S"])
+    assert g["best_E"] == o["best_E"] and np.array_equal(g["best_x"], o["best_x"])
+    return g, o
+
+
+def test_run_dense_n64_m16_z8_200_iterations(L, orc):
+    """Dense n = 64, subQUBO 16, 8 replicas, 200 outer iterations x 256
+    cosine-schedule sweeps, alpha = 5n, c = 2, the Eq. 5 mutation rate."""
+    n = 64
+    Q = make_qubo(n, 1.0, 2024)
+    lp = lib_params(I, n, z=8, K=1, m_min=16, m_max=16, m_init=16, alpha=5 * n, c=2, sweeps=256,
+                    T_max=600.0, T_min=1.0, mut_mode=0, patience=0, max_iters=200)
+    g, o = _compare_runs(orc, Q, lp, 7)
+    assert g["iters"] == 200
+    assert g["anneal_attempts"] == 8 * (n // 16) * 256 * 16 + 200 * 8 * 256 * 16
+
+
+def test_run_with_patience_and_constant_rate(L, orc):
+    n = 150
+    Q = make_qubo(n, 0.3, 5)
+    lp = lib_params(I, n, z=5, K=1, m_min=24, m_max=24, m_init=24, alpha=2 * n, c=3, sweeps=40, T_max=900.0,
+                    mut_mode=1, mut_rate=0.05, patience=4, max_iters=300)
+    g, o = _compare_runs(orc, Q, lp, 3)
+    assert g["iters"] < 300
+
+
+def test_run_batched_uneven_subqubos(L, orc):
+    n = 600
+    Q = make_qubo(n, 0.5, 8)
+    lp = lib_params(I, n, z=3, K=6, m_min=8, m_max=70, m_init=37, alpha=n, c=4, sweeps=24, T_max=2000.0,
+                    mut_mode=0, patience=0, max_iters=6)
+    _compare_runs(orc, Q, lp, 11)
+
+
+def test_run_tiny_instances_reach_the_optimum(L, orc):
+    import itertools
+    for n, seed in [(12, 1), (16, 2)]:
+        Q = make_qubo(n, 1.0, seed)
+        X = np.array(list(itertools.product([0, 1], repeat=n)), dtype=np.int64)
+        opt = int(np.einsum("ki,ij,kj->k", X, Q.astype(np.int64), X).min())
+        lp = lib_params(I, n, z=4, m_min=4, m_max=4, m_init=4, sweeps=64, T_max=300.0, patience=0, max_iters=30)
+        g, _ = _compare_runs(orc, Q, lp, 1000 + seed)
+        assert g["best_E"] == opt
+
+
+@pytest.mark.slow
+def test_full_size_step_n2500_density01_m64_z128(L, orc):
+    """One whole outer iteration at the benchmark's sizes (n = 2500, 10 %
+    density, subQUBO 64, 128 replicas, 1024 sweeps, alpha = 5n, c = 16,
+    mutation rate 1 %), launched exactly as the benchmark launches it."""
+    n, z = 2500, 128
+    Q = make_qubo(n, 0.1, 1)
+    lp = lib_params(I, n, z=z, K=1, m_min=64, m_max=64, m_init=64, alpha=5 * n, c=16, sweeps=1024,
+                    T_max=1500.0, T_min=1.0, mut_mode=1, mut_rate=0.01)
+    S0 = random_solutions(n, z, 42)
+    q = I.icd2s_qubo_create(Q)
+    st = I.icd2s_state_create(q, z, 9)
+    try:
+        I.icd2s_state_load(st, S0)
+        I.icd2s_step(st, lp, 0)
+        x, g, E = I.icd2s_get_state(st, z, n)
+        bx, bE = I.icd2s_get_best(st, n)
+    finally:
+        I.icd2s_state_destroy(st)
+        I.icd2s_qubo_destroy(q)
+    o = orc.step(Q, orc_params(orc, lp), 9, 0, S0)
+    assert np.array_equal(x, o["S"])
+    assert np.array_equal(E, o["E"])
+    assert bE == o["best_E"] and np.array_equal(bx, o["best_x"])
+    for p in range(0, z, 16):      # gains: a sample of replicas, each against its definition
+        assert np.array_equal(g[p], orc.gains(Q, x[p]))
