@@ -163,7 +163,8 @@ def test_anneal(L, orc, sweeps, T_max):
     mask = torch.zeros((R, n), dtype=torch.uint8, device="cuda")
     dE = torch.zeros(count, dtype=torch.int64, device="cuda")
     ap = I.AnnealParams(sweeps=sweeps, T_max=T_max, T_min=1.0, iter=it, per_replica=K)
-    I.icd2s_anneal_subqubos_batch(P.st, dev(idx).data_ptr(), dev(off).data_ptr(), count, ap, mask.data_ptr(),
+    idx_d, off_d = dev(idx), dev(off)   # keep the tensors alive while the library uses them
+    I.icd2s_anneal_subqubos_batch(P.st, idx_d.data_ptr(), off_d.data_ptr(), count, ap, mask.data_ptr(),
                                   dE.data_ptr())
     mask, dE = mask.cpu().numpy(), dE.cpu().numpy()
     beta = orc.beta_table(sweeps, T_max, 1.0)
@@ -208,7 +209,8 @@ def test_apply_flips_update_gains(L, orc, n, R):
         M[2] = 1                                        # everything flips
     for p in range(3, R):
         M[p] = rng.random(n) < 0.3
-    I.icd2s_apply_flips_update_gains(P.st, dev(M).data_ptr())
+    M_d = dev(M)
+    I.icd2s_apply_flips_update_gains(P.st, M_d.data_ptr())
     x, g, E = P.state()
     X1 = X0 ^ M
     assert np.array_equal(x, X1)
@@ -216,7 +218,8 @@ def test_apply_flips_update_gains(L, orc, n, R):
     for p in range(R):
         assert np.array_equal(g[p], orc.gains(P.Q, X1[p]))
     # a second round on the updated state
-    I.icd2s_apply_flips_update_gains(P.st, dev(M[::-1].copy()).data_ptr())
+    M2_d = dev(M[::-1].copy())
+    I.icd2s_apply_flips_update_gains(P.st, M2_d.data_ptr())
     x, g, E = P.state()
     X2 = X1 ^ M[::-1]
     assert np.array_equal(x, X2) and np.array_equal(E, orc.energy_batch(P.Q, X2))
