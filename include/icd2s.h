@@ -228,6 +228,32 @@ int icd2s_get_phase_ms(icd2s_state* st, double* ms);
 /* Number of kernel launches the library has made in this process. */
 int icd2s_kernel_launches(uint64_t* count);
 
+/* Flip write-back that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- code
+ * whose device memory is owned and handed out by someone else (a host
+ * framework with a fixed budget, a plugin inside another allocator) or that
+ * must not allocate once running.  It does what
+ * icd2s_apply_flips_update_gains does, on buffers the caller owns:
+ *   Q_dev      int8 [n][ld]        the symmetric QUBO matrix, row stride ld
+ *                                  (ld % 4 == 0, n <= ld; padding bytes unread
+ *                                  for the result), 4-byte aligned
+ *   flips_dev  uint8 [replicas][n] 1 = flip this variable
+ *   x_dev      uint8 [replicas][ld] solutions, updated in place (4-byte aligned)
+ *   g_dev      int32 [replicas][ld] exact gains of x_dev, updated in place
+ *                                  (16-byte aligned)
+ *   E_dev      int64 [replicas]    energies of x_dev, updated in place
+ * Its scratch (flip lists, per-replica counters, the diagonal of Q) is one
+ * static device array of about 4.3 MB that every GPU loading the library
+ * holds until the process exits; limits: 1 <= n <= 16384, replicas <= 4096,
+ * replicas * ld <= 1048576 -- larger sizes return ICD2S_ERR_RANGE.  The
+ * first call on a device (with that device current) looks up the array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the array: calls whose GPU work overlaps race and must be ordered by
+ * the caller.  No device memory is allocated or freed. */
+int icd2s_apply_flips_static(const int8_t* Q_dev, int32_t n, int32_t ld, int32_t replicas,
+                             const uint8_t* flips_dev, uint8_t* x_dev, int32_t* g_dev, int64_t* E_dev,
+                             void* stream);
+
 /* Host copies of the library's tables, for checking: BETA[sweeps] (Q24
  * inverse temperatures of the cosine schedule) and NLOG[4096] (Q24 -ln). */
 int icd2s_tables(int32_t sweeps, double T_max, double T_min, uint32_t* beta, uint32_t* nlog);

@@ -48,6 +48,12 @@ int fail(int code, const char* fmt, ...)
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+}  // namespace
+
+void icd2s::set_error_message(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
+namespace {
+
 // Host tables.  The cosine temperature schedule of the emulated Ising
 // machine, BETA[k] = round(2^24 / T_k) with
 // T_k = T_min + (T_max - T_min)(1 + cos(pi k / (K - 1))) / 2 (T_0 = T_min when

@@ -72,6 +72,9 @@ struct Dev {
 // Counts kernel launches (process-wide, for reporting).
 void note_launch(int kernels);
 
+// Sets the calling thread's icd2s_last_error() message.
+void set_error_message(const char* msg);
+
 // ---- launchers (each returns cudaGetLastError() of its launch) ----
 cudaError_t launch_prepare(const int8_t* Q, int n, int ld, int32_t* eta, int32_t* etahat, int32_t* diag,
                            int* mismatches, cudaStream_t s);

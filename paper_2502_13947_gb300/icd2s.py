@@ -30,7 +30,7 @@ EXPORTS = (
     "icd2s_get_state", "icd2s_get_best", "icd2s_tabu", "icd2s_get_tabu", "icd2s_select_subqubos",
     "icd2s_get_control", "icd2s_anneal_subqubos_batch", "icd2s_apply_flips_update_gains", "icd2s_mutate",
     "icd2s_best_update", "icd2s_initial_pass", "icd2s_step", "icd2s_step_host", "icd2s_run", "icd2s_tables",
-    "icd2s_set_timing", "icd2s_get_phase_ms", "icd2s_kernel_launches",
+    "icd2s_set_timing", "icd2s_get_phase_ms", "icd2s_kernel_launches", "icd2s_apply_flips_static",
 )
 PHASES = ("tabu", "select", "anneal", "apply_anneal", "mutate", "apply_mutate", "best")
 
@@ -113,6 +113,7 @@ def lib():
                 "icd2s_set_timing": (C.c_int, [vp, i32]),
                 "icd2s_get_phase_ms": (C.c_int, [vp, vp]),
                 "icd2s_kernel_launches": (C.c_int, [P(u64)]),
+                "icd2s_apply_flips_static": (C.c_int, [vp, i32, i32, i32, vp, vp, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -297,3 +298,11 @@ def icd2s_kernel_launches() -> int:
     c = C.c_uint64()
     _check(lib().icd2s_kernel_launches(C.byref(c)))
     return int(c.value)
+
+
+def icd2s_apply_flips_static(Q_dev: int, n: int, ld: int, replicas: int, flips_dev: int, x_dev: int, g_dev: int,
+                             E_dev: int, stream=0) -> None:
+    """Allocation-free flip write-back on caller-owned device buffers (see
+    include/icd2s.h): for callers that cannot call cudaMalloc."""
+    _check(lib().icd2s_apply_flips_static(C.c_void_p(Q_dev), n, ld, replicas, C.c_void_p(flips_dev),
+                                          C.c_void_p(x_dev), C.c_void_p(g_dev), C.c_void_p(E_dev), _s(stream)))
