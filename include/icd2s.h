@@ -21,7 +21,8 @@
  *  - Handles are not thread-safe: one thread at a time per handle.
  *  - All energies are exact int64; gains are exact int32 (|g| <= 200 n + 100).
  *  - Limits: 1 <= n <= 16384, entries of Q are int8, 1 <= replicas <= 4096,
- *    subQUBO size 1..256.  Violations return ICD2S_ERR_RANGE / ICD2S_ERR_ARG.
+ *    subQUBO size 1..256, sweeps 1..16384.  Violations return ICD2S_ERR_RANGE /
+ *    ICD2S_ERR_ARG.
  *  - Random numbers are Philox4x32-10 (Salmon et al., SC'11) keyed by the
  *    64-bit seed; every draw is a pure function of (seed, counter), so
  *    results do not depend on launch geometry or scheduling.
@@ -224,6 +225,25 @@ int icd2s_run(icd2s_qubo* q, const icd2s_params* p, uint64_t seed, uint8_t* x_ou
 #define ICD2S_PHASES 7
 int icd2s_set_timing(icd2s_state* st, int32_t enable);
 int icd2s_get_phase_ms(icd2s_state* st, double* ms);
+
+/* Kernel variants used by a state (launch configuration only: every variant
+ * computes the same results bit for bit).  tabu_variant indexes the Tabu
+ * kernel's (variables per thread, block size) builds, -1 = default;
+ * anneal_warps_per_cta = subQUBOs per CTA of the Ising-machine kernel,
+ * 0 = default. */
+typedef struct icd2s_tuning {
+    int32_t tabu_variant;
+    int32_t anneal_warps_per_cta;
+    int32_t reserved[6];
+} icd2s_tuning;
+int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t);
+int icd2s_get_tuning(icd2s_state* st, icd2s_tuning* t);
+
+/* Autotuner: times every Tabu variant that fits n and every anneal CTA size
+ * on this state with the parameters p (each trial restores the solutions it
+ * changed), keeps the fastest for the state, and returns the choice in
+ * `chosen` (may be NULL).  Synchronises `stream`. */
+int icd2s_autotune(icd2s_state* st, const icd2s_params* p, icd2s_tuning* chosen, void* stream);
 
 /* Number of kernel launches the library has made in this process. */
 int icd2s_kernel_launches(uint64_t* count);

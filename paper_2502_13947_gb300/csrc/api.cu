@@ -121,9 +121,10 @@ struct icd2s_state {
     int64_t* counters = nullptr; // [0] anneal attempts
     uint32_t* nlog = nullptr;
     uint32_t* beta = nullptr; int beta_cap = 0;
+    int* limtab = nullptr;  // [beta_cap][4096] acceptance limits of the schedule
     int beta_sweeps = -1; double beta_tmax = 0, beta_tmin = 0;
     bool have_select = false; int sel_K = 0;
-    int tabu_w = 0;  // 4-variable groups per thread in the Tabu kernel (0: automatic)
+    icd2s_tuning tune{-1, 0, {0}};  // kernel variants (see icd2s_set_tuning)
     // phase timing of icd2s_step: events [2 * phase] / [2 * phase + 1]
     bool timing = false, timed_step = false;
     cudaEvent_t ev[2 * ICD2S_PHASES] = {};
@@ -139,7 +140,7 @@ static void free_state(icd2s_state* st)
 {
     void* ptrs[] = {st->X, st->G, st->E, st->T, st->C, st->gamma, st->A, st->delta, st->order, st->sel,
                     st->FL, st->FCNT, st->DEACC, st->DONE, st->best_x, st->best_E, st->flags, st->idx,
-                    st->off, st->scratch, st->counters, st->nlog, st->beta};
+                    st->off, st->scratch, st->counters, st->nlog, st->beta, st->limtab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : st->ev)
@@ -150,15 +151,22 @@ static void free_state(icd2s_state* st)
 static int ensure_beta(icd2s_state* st, int sweeps, double T_max, double T_min, cudaStream_t s)
 {
     if (sweeps == st->beta_sweeps && T_max == st->beta_tmax && T_min == st->beta_tmin) return ICD2S_OK;
+    REQ(sweeps >= 1 && sweeps <= kMaxSweeps, ICD2S_ERR_RANGE, "sweeps=%d outside 1..%d", sweeps, kMaxSweeps);
     if (sweeps > st->beta_cap) {
+        CK(cudaStreamSynchronize(s));
         if (st->beta) CK(cudaFree(st->beta));
+        if (st->limtab) CK(cudaFree(st->limtab));
         st->beta = nullptr;
+        st->limtab = nullptr;
+        st->beta_cap = 0;
         CK(dalloc(&st->beta, (size_t)sweeps));
+        CK(dalloc(&st->limtab, (size_t)sweeps * 4096));
         st->beta_cap = sweeps;
     }
     std::vector<uint32_t> b((size_t)sweeps);
     make_beta(sweeps, T_max, T_min, b.data());
     CK(cudaMemcpyAsync(st->beta, b.data(), sizeof(uint32_t) * sweeps, cudaMemcpyHostToDevice, s));
+    CK(launch_limtab(st->beta, sweeps, st->nlog, st->limtab, s));
     CK(cudaStreamSynchronize(s));  // the host vector dies here
     st->beta_sweeps = sweeps; st->beta_tmax = T_max; st->beta_tmin = T_min;
     return ICD2S_OK;
@@ -179,7 +187,8 @@ static int check_params(const icd2s_state* st, const icd2s_params* p)
     REQ(tabu_smem_bytes(n, p->alpha) <= 227 * 1024, ICD2S_ERR_RANGE,
         "alpha=%d with n=%d needs more shared memory than a CTA has", p->alpha, n);
     REQ(p->c >= 1 && p->c <= n, ICD2S_ERR_ARG, "tenure c=%d outside 1..n", p->c);
-    REQ(p->sweeps >= 1 && p->sweeps <= (1 << 24), ICD2S_ERR_RANGE, "sweeps=%d", p->sweeps);
+    REQ(p->sweeps >= 1 && p->sweeps <= kMaxSweeps, ICD2S_ERR_RANGE, "sweeps=%d outside 1..%d", p->sweeps,
+        kMaxSweeps);
     REQ(p->T_min > 0 && p->T_max >= p->T_min, ICD2S_ERR_ARG, "need 0 < T_min <= T_max");
     const int64_t wl = (int64_t)1 << 24;
     REQ(p->w1 >= -wl && p->w1 <= wl && p->w2 >= -wl && p->w2 <= wl && p->w3 >= -wl && p->w3 <= wl, ICD2S_ERR_RANGE,
@@ -416,7 +425,7 @@ int icd2s_tabu(icd2s_state* st, int32_t alpha, int32_t c, void* stream)
     REQ(alpha >= 0, ICD2S_ERR_ARG, "alpha < 0");
     REQ(c >= 1 && c <= n, ICD2S_ERR_ARG, "tenure c=%d outside 1..n", c);
     REQ(tabu_smem_bytes(n, alpha) <= 227 * 1024, ICD2S_ERR_RANGE, "alpha=%d too large for n=%d", alpha, n);
-    CK(launch_tabu(st->d, alpha, c, st->tabu_w, S(stream)));
+    CK(launch_tabu(st->d, alpha, c, st->tune.tabu_variant, S(stream)));
     return ICD2S_OK;
 }
 
@@ -461,8 +470,9 @@ static int anneal_impl(icd2s_state* st, const int32_t* idx, const int32_t* off, 
     if (rc) return rc;
     AnnealArgs a{};
     a.idx = idx; a.off = off; a.count = count; a.per_replica = per_replica; a.block_m = block_m;
-    a.block_base = block_base; a.beta = st->beta; a.sweeps = sweeps; a.nlog = st->nlog; a.iter = iter;
+    a.block_base = block_base; a.limtab = st->limtab; a.sweeps = sweeps; a.iter = iter;
     a.slot_base = 0; a.mask = mask; a.ldm = ldm; a.dE = dE; a.attempts_acc = st->counters; a.m_max = m_max;
+    a.warps_per_cta = st->tune.anneal_warps_per_cta;
     CK(launch_anneal(st->d, a, s));
     return ICD2S_OK;
 }
@@ -546,7 +556,7 @@ static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* tra
     int rc = ensure_beta(st, p->sweeps, p->T_max, p->T_min, s);
     if (rc) return rc;
     mark(st, 0, 0, s);
-    CK(launch_tabu(st->d, p->alpha, p->c, st->tabu_w, s));                       // Algorithm 1
+    CK(launch_tabu(st->d, p->alpha, p->c, st->tune.tabu_variant, s));                     // Algorithm 1
     mark(st, 0, 1, s);
     CK(launch_best(st->d, trace_it, 0, s));
     mark(st, 1, 0, s);
@@ -596,6 +606,108 @@ int icd2s_get_phase_ms(icd2s_state* st, double* ms)
         CK(cudaEventElapsedTime(&f, st->ev[2 * ph], st->ev[2 * ph + 1]));
         ms[ph] = f;
     }
+    return ICD2S_OK;
+}
+
+int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t)
+{
+    REQ(st && t, ICD2S_ERR_ARG, "NULL argument");
+    REQ(t->tabu_variant < 0 || tabu_variant_fits(t->tabu_variant, st->q->n), ICD2S_ERR_ARG,
+        "Tabu variant %d does not cover n=%d", t->tabu_variant, st->q->n);
+    REQ(t->anneal_warps_per_cta >= 0 && t->anneal_warps_per_cta <= 4, ICD2S_ERR_ARG,
+        "anneal_warps_per_cta=%d outside 0..4", t->anneal_warps_per_cta);
+    st->tune = *t;
+    return ICD2S_OK;
+}
+
+int icd2s_get_tuning(icd2s_state* st, icd2s_tuning* t)
+{
+    REQ(st && t, ICD2S_ERR_ARG, "NULL argument");
+    *t = st->tune;
+    return ICD2S_OK;
+}
+
+// Times the variants on the live workload.  The solutions are backed up in
+// temporary buffers and restored after every trial; the trial selection
+// overwrites the last one, so the caller must select again before
+// icd2s_mutate.
+int icd2s_autotune(icd2s_state* st, const icd2s_params* p, icd2s_tuning* chosen, void* stream)
+{
+    REQ(st && p, ICD2S_ERR_ARG, "NULL argument");
+    int rc = check_params(st, p);
+    if (rc) return rc;
+    cudaStream_t s = S(stream);
+    rc = ensure_beta(st, p->sweeps, p->T_max, p->T_min, s);
+    if (rc) return rc;
+    const int R = st->R, ld = st->q->ld, n = st->q->n;
+    const size_t RL = (size_t)R * ld;
+    uint8_t* xb = nullptr;
+    int32_t* gb = nullptr;
+    int64_t* eb = nullptr;
+    struct Backup { uint8_t*& x; int32_t*& g; int64_t*& e;
+        ~Backup() { if (x) cudaFree(x); if (g) cudaFree(g); if (e) cudaFree(e); } } backup{xb, gb, eb};
+    CK(cudaStreamSynchronize(s));
+    CK(dalloc(&xb, RL));
+    CK(dalloc(&gb, RL));
+    CK(dalloc(&eb, (size_t)R));
+    CK(cudaMemcpyAsync(xb, st->X, RL, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(gb, st->G, RL * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(eb, st->E, (size_t)R * 8, cudaMemcpyDeviceToDevice, s));
+    auto restore = [&]() -> int {
+        CK(cudaMemcpyAsync(st->X, xb, RL, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(st->G, gb, RL * 4, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(st->E, eb, (size_t)R * 8, cudaMemcpyDeviceToDevice, s));
+        return ICD2S_OK;
+    };
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } eg{e0, e1};
+    icd2s_tuning best = st->tune;
+    const int alpha = p->alpha < 2000 ? p->alpha : 2000;
+    float best_ms = 1e30f;
+    for (int v = 0; v < tabu_num_variants(); ++v) {
+        if (!tabu_variant_fits(v, n)) continue;
+        float vbest = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            if ((rc = restore())) return rc;
+            CK(cudaEventRecord(e0, s));
+            CK(launch_tabu(st->d, alpha, p->c, v, s));
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < vbest) vbest = ms;
+        }
+        if (vbest < best_ms) { best_ms = vbest; best.tabu_variant = v; }
+    }
+    if ((rc = restore())) return rc;
+    rc = select_impl(st, p->w1, p->w2, p->w3, p->K, p->m_min, p->m_max, 0u, s);
+    if (rc) return rc;
+    AnnealArgs a{};
+    a.idx = st->idx; a.off = st->off; a.count = R * p->K; a.per_replica = p->K; a.limtab = st->limtab;
+    a.sweeps = p->sweeps < 128 ? p->sweeps : 128; a.iter = 0; a.mask = st->scratch; a.ldm = ld; a.m_max = p->m_max;
+    best_ms = 1e30f;
+    const int max_wpb = p->m_max > 128 ? 3 : 4;
+    for (int w = 1; w <= max_wpb; ++w) {
+        a.warps_per_cta = w;
+        float vbest = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            CK(cudaEventRecord(e0, s));
+            CK(launch_anneal(st->d, a, s));
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < vbest) vbest = ms;
+        }
+        if (vbest < best_ms) { best_ms = vbest; best.anneal_warps_per_cta = w; }
+    }
+    if ((rc = restore())) return rc;
+    CK(cudaStreamSynchronize(s));
+    st->have_select = false;
+    st->tune = best;
+    if (chosen) *chosen = best;
     return ICD2S_OK;
 }
 

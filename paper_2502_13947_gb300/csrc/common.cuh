@@ -24,6 +24,7 @@ constexpr int kLdAlign = 128;
 constexpr int kMaxN = 16384;
 constexpr int kMaxM = 256;
 constexpr int kMaxReplicas = 4096;
+constexpr int kMaxSweeps = 16384;   // the acceptance-limit table is sweeps x 4096 int32
 
 constexpr uint32_t kTagInit = 1u, kTagAnneal = 2u, kTagMut = 3u, kTagSize = 4u;
 
@@ -94,12 +95,17 @@ cudaError_t launch_mutate(const Dev& d, int K, const int32_t* off, double rate, 
 struct AnnealArgs {
     const int32_t* idx; const int32_t* off; int count; int per_replica;
     int block_m; int block_base;          // idx == nullptr: contiguous block [base, base+m)
-    const uint32_t* beta; int sweeps; const uint32_t* nlog; uint32_t iter; uint32_t slot_base;
+    const int* limtab; int sweeps; uint32_t iter; uint32_t slot_base;   // limtab: [sweeps][4096]
     uint8_t* mask; int ldm;               // mask output (nullptr: flip lists FL/FCNT)
     int64_t* dE; int64_t* attempts_acc;   // optional outputs
     int m_max;
+    int warps_per_cta;                    // 0: default
 };
+bool tabu_variant_fits(int variant, int n);
+int tabu_num_variants();
+int tabu_default_variant(int n);
 cudaError_t launch_anneal(const Dev& d, const AnnealArgs& a, cudaStream_t s);
+cudaError_t launch_limtab(const uint32_t* beta, int sweeps, const uint32_t* nlog, int* lim, cudaStream_t s);
 cudaError_t launch_compact_mask(const Dev& d, const uint8_t* mask, int ldm, cudaStream_t s);
 cudaError_t launch_apply(const Dev& d, cudaStream_t s);
 cudaError_t launch_best(const Dev& d, int64_t* trace_slot, int iter_end, cudaStream_t s);

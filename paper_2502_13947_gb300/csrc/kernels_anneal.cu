@@ -1,31 +1,43 @@
 // kernels_anneal.cu -- the emulated Ising machine (Eq. 4, Algorithm 4).
 //
 // One warp per subQUBO S (m <= 32 P variables, ascending indices).  Lane l
-// owns the P consecutive positions b = l P .. l P + P - 1.
+// owns the P positions b = l + 32 q (q = 0..P-1), so the sweep order
+// (position-major) is q-major across lanes: the first accepted position is
+// found from P ballots without any shuffle.
 //
-// Gather (Eq. 4): Q' = Q[S, S] is staged as int8 in shared memory (m rows of
-// 32 P bytes).  The boundary bias b_i = sum_{j not in S} 2 Q_ij x_j is never
-// formed explicitly: the local gain of position a in the biased subQUBO,
+// Gather (Eq. 4): Q' = Q[S, S] is staged as int8 in shared memory in a
+// permuted layout, Qs[r][l P + q] = Q'[r][l + 32 q], so that the P entries a
+// lane needs from row r are one contiguous P-byte load; the diagonal is
+// stored as 0, so the row update of a flip leaves the flipped position alone.
+// The boundary bias b_i = sum_{j not in S} 2 Q_ij x_j is never formed
+// explicitly: the local gain of position a in the biased subQUBO,
 // (1 - 2 x_a)(Q_aa + b_a + 2 sum_{c in S, c != a} Q_ac x_c), equals the global
 // gain g_a, which the solution set already tracks exactly; so the gains of S
 // are read straight from G.
 //
 // Anneal: sweeps k = 0..K-1 visit positions 0..m-1 in order; attempt (k, b)
 // draws u = Philox(ctr = (k / 4, (TAG_ANNEAL << 24) | b, slot, iter)).word[k mod 4]
-// and accepts iff l_b <= 0 or l_b * BETA[k] < NLOG[u >> 20].  A sweep is run
-// as a sequence of "first accept" rounds: every lane tests all of its
-// positions at or after the current one against the current gains, a ballot
-// finds the first accepted position, that flip is applied (each lane
-// updates its gains from one P-byte row segment of Q'), and the scan resumes
-// just after it.  Positions before the first accept would have been tested
-// with exactly these gains by a one-at-a-time sweep, so the trajectory is
-// identical to the sequential one; a sweep costs (accepts + 1) rounds
-// instead of m dependent steps.  Each lane draws one Philox block per owned
-// position every 4 sweeps, so no random words are wasted or exchanged.
+// and accepts iff l_b <= 0 or l_b * BETA[k] < NLOG[u >> 20].  For integer
+// gains this is l_b <= LIM[k][u >> 20] with LIM[k][j] = floor((NLOG[j] - 1) /
+// BETA[k]) (0 when NLOG[j] = 0, unbounded when BETA[k] = 0): a per-schedule
+// table built once on the device (k_limtab), so an attempt costs one
+// L1-resident load and one compare.  A sweep runs as "first accept"
+// rounds: every lane tests its positions at or after the current one
+// against the current gains, P ballots (masked by warp-uniform "not yet
+// visited" lane masks) locate the first accepted position,
+// that flip is applied (each lane updates its gains from one P-byte row
+// segment of Q'), and the scan resumes just after it.  Positions before the
+// first accept would have been tested with exactly these gains by a
+// one-at-a-time sweep, so the trajectory is identical to the sequential one;
+// a sweep costs (accepts + 1) rounds instead of m dependent steps.  Each
+// lane draws one Philox block per owned position every 4 sweeps, so no
+// random words are wasted or exchanged.
 //
 // Output: the changed positions, either as a 0/1 mask [R][ldm] or appended
 // to the replica's flip list (index | old x << 31) for k_apply; and the
 // subQUBO energy change (sum of the accepted gains).
+#include <climits>
+
 #include "common.cuh"
 
 namespace icd2s {
@@ -37,9 +49,18 @@ template <> struct RowSeg<2> { using T = uint16_t; };
 template <> struct RowSeg<4> { using T = uint32_t; };
 template <> struct RowSeg<8> { using T = unsigned long long; };
 
+// Largest gain accepted by the test l * beta < thr (see above).
+__device__ __forceinline__ int accept_limit(uint32_t thr, uint32_t beta)
+{
+    if (thr == 0u) return 0;        // no positive gain passes
+    if (beta == 0u) return INT_MAX; // every gain passes
+    return (int)((thr - 1u) / beta);
+}
+
 template <int P>
 __global__ __launch_bounds__(128) void k_anneal(Dev d, AnnealArgs a)
 {
+    using Seg = typename RowSeg<P>::T;
     constexpr int MC = 32 * P;  // row length (bytes) of the staged Q'
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -63,94 +84,116 @@ __global__ __launch_bounds__(128) void k_anneal(Dev d, AnnealArgs a)
     bool valid[P];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
-        const int b = lane * P + q;
+        const int b = lane + 32 * q;
         valid[q] = b < m;
         col[q] = valid[q] ? (S ? __ldg(S + b) : a.block_base + b) : 0;
     }
-    // gather Q[S, S]
+    // gather Q[S, S] into the permuted layout, diagonal as 0
+#pragma unroll 4
     for (int r = 0; r < m; ++r) {
         const int ir = S ? __ldg(S + r) : a.block_base + r;
         const int8_t* row = d.Q + (size_t)ir * ld;
-        typename RowSeg<P>::T packed = 0;
+        Seg packed = 0;
 #pragma unroll
         for (int q = 0; q < P; ++q) {
-            const uint8_t v = valid[q] ? (uint8_t)__ldg(row + col[q]) : (uint8_t)0;
-            packed |= (typename RowSeg<P>::T)v << (8 * q);
+            const bool take = valid[q] && (lane + 32 * q != r);
+            const uint8_t v = take ? (uint8_t)__ldg(row + col[q]) : (uint8_t)0;
+            packed |= (Seg)v << (8 * q);
         }
-        *reinterpret_cast<typename RowSeg<P>::T*>(Qs + (size_t)r * MC + lane * P) = packed;
+        *reinterpret_cast<Seg*>(Qs + (size_t)r * MC + lane * P) = packed;
     }
     __syncwarp();
 
-    int l[P];
-    unsigned xb = 0;
+    int l[P], sg[P];       // gains and signs 1 - 2 x of the owned positions
+    unsigned X[P];         // warp-uniform: bit lane of X[q] = x at position lane + 32 q
     const int32_t* grow = d.G + (size_t)p * ld;
     const uint8_t* xrow = d.X + (size_t)p * ld;
+    unsigned x0 = 0;
 #pragma unroll
     for (int q = 0; q < P; ++q) {
+        const int xv = valid[q] ? (int)xrow[col[q]] : 0;
         l[q] = valid[q] ? grow[col[q]] : 0;
-        xb |= (valid[q] ? (unsigned)xrow[col[q]] : 0u) << q;
+        sg[q] = 1 - 2 * xv;
+        x0 |= (unsigned)xv << q;
+        X[q] = __ballot_sync(0xffffffffu, xv != 0);
     }
-    const unsigned x0 = xb;
     const uint32_t slot = a.slot_base + (uint32_t)s;
-    long long dE = 0;
+    int dE = 0;  // |f_sub| <= m (200 n + 100) + 100 m^2 < 2^30, so the running change fits int32
 
-    for (int k4 = 0; k4 < a.sweeps; k4 += 4) {
-        uint32_t thr[4][P];
+    // acceptance limits of 4 consecutive sweeps: Philox block k4/4 of every owned
+    // position, looked up in the schedule's table (issued one block ahead, so
+    // the table loads overlap the previous block's sweeps)
+    auto load_limits = [&](int k4, int (&out)[4][P]) {
 #pragma unroll
         for (int q = 0; q < P; ++q) {
-            if (valid[q]) {
-                const u32x4 u = philox10((uint32_t)(k4 >> 2), (kTagAnneal << 24) | (uint32_t)(lane * P + q), slot,
-                                         a.iter, d.k0, d.k1);
+            const u32x4 u = philox10((uint32_t)(k4 >> 2), (kTagAnneal << 24) | (uint32_t)(lane + 32 * q), slot,
+                                     a.iter, d.k0, d.k1);
 #pragma unroll
-                for (int r = 0; r < 4; ++r) thr[r][q] = __ldg(a.nlog + (u.v[r] >> 20));
-            } else {
-#pragma unroll
-                for (int r = 0; r < 4; ++r) thr[r][q] = 0;
+            for (int r = 0; r < 4; ++r) {
+                const int k = k4 + r < a.sweeps ? k4 + r : a.sweeps - 1;
+                out[r][q] = valid[q] ? __ldg(a.limtab + (size_t)k * 4096 + (u.v[r] >> 20)) : INT_MIN;
             }
         }
+    };
+    int limA[4][P];
+    load_limits(0, limA);
+    for (int k4 = 0; k4 < a.sweeps; k4 += 4) {
+        int limB[4][P];
+        if (k4 + 4 < a.sweeps) load_limits(k4 + 4, limB);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int k = k4 + r;
             if (k >= a.sweeps) break;
-            const unsigned long long bk = __ldg(a.beta + k);
-            int start = 0;
-            while (true) {
-                int fq = P;
+            int lim[P];
+            unsigned M[P];  // lanes whose position q has not been visited in this sweep
 #pragma unroll
-                for (int q = P - 1; q >= 0; --q) {
-                    const int b = lane * P + q;
-                    const bool acc = valid[q] && b >= start &&
-                                     (l[q] <= 0 || (unsigned long long)(unsigned)l[q] * bk < thr[r][q]);
-                    fq = acc ? q : fq;
-                }
-                const unsigned any = __ballot_sync(0xffffffffu, fq < P);
-                if (any == 0u) break;
-                const int L = __ffs(any) - 1;
-                const int v = __shfl_sync(0xffffffffu, fq | (int)(((xb >> (fq & 31)) & 1u) << 8), L);
-                const int qs = v & 0xff;
-                const int si = 1 - 2 * (v >> 8);
-                const int bsel = L * P + qs;
-                const typename RowSeg<P>::T seg =
-                    *reinterpret_cast<const typename RowSeg<P>::T*>(Qs + (size_t)bsel * MC + lane * P);
+            for (int q = 0; q < P; ++q) {
+                lim[q] = limA[r][q];
+                M[q] = 0xffffffffu;
+            }
+            while (true) {
+                unsigned B[P];
+#pragma unroll
+                for (int q = 0; q < P; ++q) B[q] = __ballot_sync(0xffffffffu, l[q] <= lim[q]) & M[q];
+                int qs = -1;
+                unsigned bq = 0u, xq = 0u;
+#pragma unroll
+                for (int q = P - 1; q >= 0; --q)
+                    if (B[q]) { qs = q; bq = B[q]; xq = X[q]; }
+                if (qs < 0) break;
+                const int L = __ffs(bq) - 1;
+                const int si2 = ((xq >> L) & 1u) ? -2 : 2;
+                const Seg seg = *reinterpret_cast<const Seg*>(Qs + (size_t)(L + 32 * qs) * MC + lane * P);
+                const bool own = lane == L;  // selects, not a branch: no reconvergence per round
 #pragma unroll
                 for (int q = 0; q < P; ++q) {
-                    const bool is_i = (lane == L) && (q == qs);
+                    const bool me = own && q == qs;
                     const int qv = (int)(int8_t)(uint8_t)(seg >> (8 * q));
-                    const int sq = 1 - 2 * (int)((xb >> q) & 1u);
-                    if (is_i) { dE += l[q]; l[q] = -l[q]; }
-                    else l[q] += 2 * qv * si * sq;
+                    const int upd = l[q] + qv * (si2 * sg[q]);  // the flipped position adds Q'_ii = 0
+                    dE += me ? l[q] : 0;
+                    l[q] = me ? -l[q] : upd;
+                    sg[q] = me ? -sg[q] : sg[q];
                 }
-                if (lane == L) xb ^= 1u << qs;
-                start = bsel + 1;
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    if (q == qs) X[q] ^= 1u << L;
+                    M[q] = q < qs ? 0u : (q == qs ? (M[q] & (0xfffffffeu << L)) : M[q]);
+                }
             }
         }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < P; ++q) limA[r][q] = limB[r][q];
     }
 
-    const unsigned changed = xb ^ x0;
+    unsigned changed = 0;
+#pragma unroll
+    for (int q = 0; q < P; ++q) changed |= (unsigned)(valid[q] && (((X[q] >> lane) & 1u) != ((x0 >> q) & 1u))) << q;
     if (a.mask) {
 #pragma unroll
         for (int q = 0; q < P; ++q)
-            if (valid[q] && ((changed >> q) & 1u)) a.mask[(size_t)p * a.ldm + col[q]] = 1;
+            if ((changed >> q) & 1u) a.mask[(size_t)p * a.ldm + col[q]] = 1;
     } else {
         const int cnt = __popc(changed);
         int incl = cnt;
@@ -172,13 +215,33 @@ __global__ __launch_bounds__(128) void k_anneal(Dev d, AnnealArgs a)
                 ++pos;
             }
     }
+    long long dEl = dE;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dE += __shfl_xor_sync(0xffffffffu, dE, o);
+    for (int o = 16; o > 0; o >>= 1) dEl += __shfl_xor_sync(0xffffffffu, dEl, o);
     if (lane == 0) {
-        if (a.dE) a.dE[s] = dE;
+        if (a.dE) a.dE[s] = dEl;
         if (a.attempts_acc) atomicAdd(reinterpret_cast<unsigned long long*>(a.attempts_acc),
                                       (unsigned long long)a.sweeps * (unsigned long long)m);
     }
+}
+
+// LIM[k][j] for the whole schedule: the largest gain that attempt (k, j) accepts.
+__global__ void k_limtab(const uint32_t* __restrict__ beta, int sweeps, const uint32_t* __restrict__ nlog,
+                         int* __restrict__ lim)
+{
+    const size_t total = (size_t)sweeps * 4096;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+        lim[e] = accept_limit(nlog[e & 4095], beta[e >> 12]);
+}
+
+cudaError_t launch_limtab(const uint32_t* beta, int sweeps, const uint32_t* nlog, int* lim, cudaStream_t s)
+{
+    const size_t total = (size_t)sweeps * 4096;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_limtab<<<blocks, 256, 0, s>>>(beta, sweeps, nlog, lim);
+    note_launch(1);
+    return cudaGetLastError();
 }
 
 template <int P>
@@ -198,10 +261,15 @@ cudaError_t launch_anneal(const Dev& d, const AnnealArgs& a, cudaStream_t s)
 {
     if (a.count <= 0) return cudaSuccess;
     const int m = a.m_max;
-    if (m <= 32) return launch_anneal_p<1>(d, a, 2, s);
-    if (m <= 64) return launch_anneal_p<2>(d, a, 2, s);
-    if (m <= 128) return launch_anneal_p<4>(d, a, 2, s);
-    if (m <= 256) return launch_anneal_p<8>(d, a, 1, s);
+    // warps (subQUBOs) per CTA: shared memory is 1 KiB / 4 KiB / 16 KiB / 64 KiB per warp
+    int wpb = a.warps_per_cta;
+    if (wpb <= 0) wpb = m <= 128 ? 2 : 1;
+    if (m > 128 && wpb > 3) wpb = 3;
+    if (wpb > 4) wpb = 4;
+    if (m <= 32) return launch_anneal_p<1>(d, a, wpb, s);
+    if (m <= 64) return launch_anneal_p<2>(d, a, wpb, s);
+    if (m <= 128) return launch_anneal_p<4>(d, a, wpb, s);
+    if (m <= 256) return launch_anneal_p<8>(d, a, wpb, s);
     return cudaErrorInvalidValue;
 }
 

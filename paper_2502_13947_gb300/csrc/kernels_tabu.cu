@@ -1,26 +1,35 @@
 // kernels_tabu.cu -- Tabu search (Algorithm 1, Section 2.4) on every replica.
 //
 // One CTA per replica.  Thread t owns the W groups of 4 consecutive
-// variables j = 4 (t + w NT) + {0..3}; their gains g_j and tabu memory C_j
-// live in registers for the whole search.  One iteration is:
-//   1. every thread knows the chosen move (i, g_i, x_i) from the previous
+// variables j = 4 (t + w NT) + {0..3}.  Per owned variable it keeps, in
+// registers for the whole search:
+//   gf_j = (1 - 2 x_j) g_j   the gain with the variable's sign folded in, so a
+//                            move i only adds 2 Q_ij (1 - 2 x_i) to it (one
+//                            multiply-add per variable) and the moved variable
+//                            keeps its value (g_i -> -g_i and x_i -> 1 - x_i);
+//   fa_j                     the first iteration at which j may move again:
+//                            C_j <= 0 at iteration t  <=>  t >= fa_j, with
+//                            fa_i = t + c when i moves at iteration t (C_i += c
+//                            and the same-iteration decrement leave c - 1).
+// One iteration is:
+//   1. every thread knows the chosen move (g_i, i, x_i) from the previous
 //      block-wide arg-min;
 //   2. it streams its 4W bytes of row i of Q (coalesced 4-byte loads; the row
 //      index is only known after the arg-min, so there is nothing to
-//      prefetch -- the rows stay hot in L2) and applies
-//      g_j += 2 Q_ij (1 - 2 x_i)(1 - 2 x_j) for j != i, g_i = -g_i,
-//      C_i += c, then C_j -= 1 where positive;
-//   3. it takes the arg-min of g over its non-tabu variables, the warp takes
-//      the arg-min with two redux.sync (gain, then index), and one
-//      __syncthreads publishes the per-warp minima; every thread reduces
-//      those itself, so the loop has exactly one barrier.
+//      prefetch -- rows stay hot in L1/L2) and applies the update;
+//   3. it takes the arg-min over its free variables as the minimum of 32-bit
+//      keys (g + 2^26) << 5 | local index (the local index orders a thread's
+//      variables by j), the warp takes the arg-min with two redux.sync (gain,
+//      then global index), and one __syncthreads publishes the per-warp
+//      minima; every thread reduces those itself, so the loop has exactly one
+//      barrier.
 // Ties go to the lowest index, exactly as a scan in index order would.
 // The objective OV is tracked in int64 by every thread (uniform).  The move
 // log (uint16 per iteration) stays in shared memory; after the last
 // iteration the moves made after the best visit are undone in one pass:
 // variables moved an odd number of times flip back, and their rows of Q
 // correct the gains (x_min is reconstructed without copying x on every
-// improvement).
+// improvement).  The tabu memory returned is C_j = max(0, fa_j - alpha).
 #include <climits>
 
 #include "common.cuh"
@@ -29,22 +38,20 @@ namespace icd2s {
 
 namespace {
 
-__device__ __forceinline__ void warp_argmin(int g, unsigned jx, int& wg, unsigned& wjx)
-{
-    wg = __reduce_min_sync(0xffffffffu, g);
-    wjx = __reduce_min_sync(0xffffffffu, g == wg ? jx : 0xffffffffu);
-}
+constexpr unsigned kKeyBias = 1u << 26;  // |g| <= 200 n + 100 < 2^22, so g + bias < 2^27
+constexpr int kKeyShift = 5;             // local index 4 w + b < 32 (W <= 8); (g + bias) << 5 < 2^32
 
-__device__ __forceinline__ unsigned long long pack_key(int g, unsigned jx)
+__device__ __forceinline__ unsigned long long pack_key(unsigned hi, unsigned lo)
 {
-    return ((unsigned long long)((unsigned)g ^ 0x80000000u) << 32) | jx;
+    return ((unsigned long long)hi << 32) | lo;
 }
 
 }  // namespace
 
-template <int W>
-__global__ __launch_bounds__(1024) void k_tabu(Dev d, int alpha, int c)
+template <int W, int MAXT>
+__global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
 {
+    static_assert(4 * W <= (1 << kKeyShift), "the local index must fit the key");
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* wkeys = reinterpret_cast<unsigned long long*>(smem);         // [2][32]
     int* nF = reinterpret_cast<int*>(smem + 512);                                     // [1]
@@ -63,52 +70,55 @@ __global__ __launch_bounds__(1024) void k_tabu(Dev d, int alpha, int c)
     for (int j = tid; j < ld / 32; j += NT) undo[j] = 0;
     if (tid == 0) *nF = 0;
 
-    int g[W][4], C[W][4];
+    int gf[W][4], fa[W][4];
     unsigned xb = 0;  // bit 4w+b = x of the owned variable
 #pragma unroll
     for (int w = 0; w < W; ++w) {
         const int j0 = 4 * (tid + w * NT);
+        int gv[4] = {0, 0, 0, 0};
+        uint32_t xv = 0;
         if (j0 < ld) {
-            const int4 gv = *reinterpret_cast<const int4*>(grow + j0);
-            const uint32_t xv = *reinterpret_cast<const uint32_t*>(xrow + j0);
-            g[w][0] = gv.x; g[w][1] = gv.y; g[w][2] = gv.z; g[w][3] = gv.w;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) xb |= ((xv >> (8 * b)) & 1u) << (4 * w + b);
-        } else {
-#pragma unroll
-            for (int b = 0; b < 4; ++b) g[w][b] = 0;
+            const int4 g4 = *reinterpret_cast<const int4*>(grow + j0);
+            xv = *reinterpret_cast<const uint32_t*>(xrow + j0);
+            gv[0] = g4.x; gv[1] = g4.y; gv[2] = g4.z; gv[3] = g4.w;
         }
 #pragma unroll
-        for (int b = 0; b < 4; ++b) C[w][b] = 0;
+        for (int b = 0; b < 4; ++b) {
+            const unsigned xj = (xv >> (8 * b)) & 1u;
+            xb |= xj << (4 * w + b);
+            gf[w][b] = xj ? -gv[b] : gv[b];
+            fa[w][b] = (j0 + b < n) ? 0 : INT_MAX;  // padding never becomes free
+        }
     }
 
-    // arg-min over the owned non-tabu variables, then the warp's, published to slot `slot`
-    auto local_argmin = [&](int slot) {
-        int bg = INT_MAX;
-        unsigned bjx = 0xffffffffu;
+    // the warp's arg-min over free variables at iteration `itn`, published to slot `slot`
+    auto warp_argmin = [&](int itn, int slot) {
+        unsigned tk = 0xffffffffu;
 #pragma unroll
         for (int w = 0; w < W; ++w)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const int j = 4 * (tid + w * NT) + b;
-                if (j < n && C[w][b] <= 0 && g[w][b] < bg) {
-                    bg = g[w][b];
-                    bjx = ((unsigned)j << 1) | ((xb >> (4 * w + b)) & 1u);
-                }
+                const int k = 4 * w + b;
+                const int g = ((xb >> k) & 1u) ? -gf[w][b] : gf[w][b];
+                const unsigned key = ((unsigned)(g + (int)kKeyBias) << kKeyShift) | (unsigned)k;
+                tk = itn >= fa[w][b] ? min(tk, key) : tk;
             }
-        int wg; unsigned wjx;
-        warp_argmin(bg, bjx, wg, wjx);
-        if (lane == 0) wkeys[slot * 32 + warp] = pack_key(wg, wjx);
+        const unsigned wg = __reduce_min_sync(0xffffffffu, tk >> kKeyShift);
+        const unsigned k = tk & ((1u << kKeyShift) - 1u);
+        const unsigned j = 4u * (unsigned)(tid + (int)(k >> 2) * NT) + (k & 3u);
+        const unsigned cand = (tk != 0xffffffffu && (tk >> kKeyShift) == wg) ? ((j << 1) | ((xb >> k) & 1u)) : 0xffffffffu;
+        const unsigned wj = __reduce_min_sync(0xffffffffu, cand);
+        if (lane == 0) wkeys[slot * 32 + warp] = pack_key(wg, wj);
     };
     auto block_argmin = [&](int slot) -> unsigned long long {
         const unsigned long long k = lane < NW ? wkeys[slot * 32 + lane] : ~0ull;
         const unsigned hi = __reduce_min_sync(0xffffffffu, (unsigned)(k >> 32));
         const unsigned lo = __reduce_min_sync(0xffffffffu, (unsigned)(k >> 32) == hi ? (unsigned)k : 0xffffffffu);
-        return ((unsigned long long)hi << 32) | lo;
+        return pack_key(hi, lo);
     };
 
     __syncthreads();  // shared-memory clears visible
-    local_argmin(0);
+    warp_argmin(0, 0);
     __syncthreads();
     unsigned long long key = block_argmin(0);
 
@@ -116,39 +126,40 @@ __global__ __launch_bounds__(1024) void k_tabu(Dev d, int alpha, int c)
     int best_it = -1;
 
     for (int it = 0; it < alpha; ++it) {
-        const int gi = (int)((unsigned)(key >> 32) ^ 0x80000000u);
+        const int gi = (int)(unsigned)(key >> 32) - (int)kKeyBias;
         const unsigned jx = (unsigned)key;
         const int i = (int)(jx >> 1);
-        const int si = 1 - 2 * (int)(jx & 1u);
+        const int si2 = (jx & 1u) ? -2 : 2;       // 2 (1 - 2 x_i)
         const int8_t* row = Q + (size_t)i * ld;
-        int q[W][4];
+        int rv[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             const int j0 = 4 * (tid + w * NT);
-            const int v = j0 < ld ? __ldg(reinterpret_cast<const int*>(row + j0)) : 0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) q[w][b] = (int)(int8_t)(v >> (8 * b));
+            rv[w] = j0 < ld ? __ldg(reinterpret_cast<const int*>(row + j0)) : 0;
         }
 #pragma unroll
         for (int w = 0; w < W; ++w)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int j = 4 * (tid + w * NT) + b;
-                const int sj = 1 - 2 * (int)((xb >> (4 * w + b)) & 1u);
-                if (j == i) {
-                    g[w][b] = -g[w][b];
-                    xb ^= 1u << (4 * w + b);
-                    C[w][b] += c;
-                } else {
-                    g[w][b] += 2 * q[w][b] * si * sj;
-                }
-                C[w][b] = C[w][b] > 0 ? C[w][b] - 1 : C[w][b];
+            for (int b = 0; b < 4; ++b) gf[w][b] += (int)(int8_t)(rv[w] >> (8 * b)) * si2;
+        // the moved variable keeps its folded gain, flips, and becomes tabu
+        const int rel = (i >> 2) - tid;  // the owner has rel = w NT for its group w
+        const int bi = i & 3;
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            if (rel == w * NT) {
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (b == bi) {
+                        gf[w][b] -= (int)(int8_t)(rv[w] >> (8 * b)) * si2;
+                        xb ^= 1u << (4 * w + b);
+                        fa[w][b] = it + c;
+                    }
             }
         OV += gi;
         if (OV < OVmin) { OVmin = OV; best_it = it; }
         if (tid == 0) { Ts[i] += 1; mlog[it] = (uint16_t)i; }
         const int slot = (it + 1) & 1;
-        local_argmin(slot);
+        warp_argmin(it + 1, slot);
         __syncthreads();
         key = block_argmin(slot);
     }
@@ -187,10 +198,10 @@ __global__ __launch_bounds__(1024) void k_tabu(Dev d, int alpha, int c)
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             const int j0 = 4 * (tid + w * NT);
-            const int rv = j0 < ld ? __ldg(reinterpret_cast<const int*>(row + j0)) : 0;
+            const int r4 = j0 < ld ? __ldg(reinterpret_cast<const int*>(row + j0)) : 0;
 #pragma unroll
             for (int b = 0; b < 4; ++b)
-                if (j0 + b != i) acc[w][b] += di * (int)(int8_t)(rv >> (8 * b));
+                if (j0 + b != i) acc[w][b] += di * (int)(int8_t)(r4 >> (8 * b));
         }
     }
     int32_t* Cout = d.C + (size_t)p * ld;
@@ -204,17 +215,18 @@ __global__ __launch_bounds__(1024) void k_tabu(Dev d, int alpha, int c)
         for (int b = 0; b < 4; ++b) {
             const int j = j0 + b;
             int xj = (int)((xb >> (4 * w + b)) & 1u);
-            int gj = 0;
+            int gj = 0, cj = 0;
             if (j < n) {
                 const int dj = d.diag[j];
-                const int h = ((1 - 2 * xj) * g[w][b] - dj) / 2 + acc[w][b];
+                const int h = (gf[w][b] - dj) / 2 + acc[w][b];   // (1 - 2x) g = Q_jj + 2 h
                 xj ^= (int)((undo[j >> 5] >> (j & 31)) & 1u);
                 gj = (1 - 2 * xj) * (dj + 2 * h);
+                cj = fa[w][b] > alpha ? fa[w][b] - alpha : 0;
             } else {
                 xj = 0;
             }
             gv[b] = gj;
-            cv[b] = C[w][b];
+            cv[b] = cj;
             xv |= (uint32_t)xj << (8 * b);
         }
         *reinterpret_cast<int4*>(grow + j0) = make_int4(gv[0], gv[1], gv[2], gv[3]);
@@ -230,32 +242,59 @@ size_t tabu_smem_bytes(int n, int alpha)
     return 528 + 4 * (size_t)ld + (size_t)ld / 8 + 2 * (size_t)alpha + 16;
 }
 
-template <int W>
+template <int W, int MAXT>
 static cudaError_t launch_tabu_w(const Dev& d, int alpha, int c, cudaStream_t s)
 {
     int nt = (d.n + 4 * W - 1) / (4 * W);
     nt = (nt + 31) / 32 * 32;
-    if (nt > 1024) return cudaErrorInvalidConfiguration;
+    if (nt > MAXT) return cudaErrorInvalidConfiguration;
     const size_t sm = tabu_smem_bytes(d.n, alpha);
-    cudaError_t e = cudaFuncSetAttribute(k_tabu<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_tabu<W, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_tabu<W><<<d.R, nt, sm, s>>>(d, alpha, c);
+    k_tabu<W, MAXT><<<d.R, nt, sm, s>>>(d, alpha, c);
     note_launch(1);
     return cudaGetLastError();
 }
 
-// w_words: 4-variable groups per thread (1..4); 0 picks the smallest that fits 1024 threads.
-cudaError_t launch_tabu(const Dev& d, int alpha, int c, int w_words, cudaStream_t s)
+// Variants of the Tabu kernel: 4-variable groups per thread W and the block
+// size they are compiled for (fewer, wider threads cut the per-move
+// reduction and barrier work; the block must still cover n).
+struct TabuVariant { int W, maxt; };
+static const TabuVariant kTabuVariants[] = {{1, 1024}, {2, 1024}, {3, 1024}, {4, 1024}, {4, 256}, {8, 256}};
+constexpr int kNumTabuVariants = sizeof(kTabuVariants) / sizeof(kTabuVariants[0]);
+
+bool tabu_variant_fits(int variant, int n)
 {
-    if (w_words <= 0) {
-        w_words = 1;
-        while (w_words < 4 && (d.n + 4 * w_words - 1) / (4 * w_words) > 1024) ++w_words;
-    }
-    switch (w_words) {
-        case 1: return launch_tabu_w<1>(d, alpha, c, s);
-        case 2: return launch_tabu_w<2>(d, alpha, c, s);
-        case 3: return launch_tabu_w<3>(d, alpha, c, s);
-        case 4: return launch_tabu_w<4>(d, alpha, c, s);
+    if (variant < 0 || variant >= kNumTabuVariants) return false;
+    const TabuVariant v = kTabuVariants[variant];
+    return (n + 4 * v.W - 1) / (4 * v.W) <= v.maxt;
+}
+
+int tabu_num_variants() { return kNumTabuVariants; }
+
+// The default: the widest 256-thread variant that covers n, else the
+// narrowest 1024-thread one.
+int tabu_default_variant(int n)
+{
+    if (tabu_variant_fits(4, n)) return 4;
+    if (tabu_variant_fits(5, n)) return 5;
+    for (int v = 0; v < 4; ++v)
+        if (tabu_variant_fits(v, n)) return v;
+    return -1;
+}
+
+// variant: index into kTabuVariants; < 0 picks the default.
+cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_t s)
+{
+    if (variant < 0) variant = tabu_default_variant(d.n);
+    if (!tabu_variant_fits(variant, d.n)) return cudaErrorInvalidConfiguration;
+    switch (variant) {
+        case 0: return launch_tabu_w<1, 1024>(d, alpha, c, s);
+        case 1: return launch_tabu_w<2, 1024>(d, alpha, c, s);
+        case 2: return launch_tabu_w<3, 1024>(d, alpha, c, s);
+        case 3: return launch_tabu_w<4, 1024>(d, alpha, c, s);
+        case 4: return launch_tabu_w<4, 256>(d, alpha, c, s);
+        case 5: return launch_tabu_w<8, 256>(d, alpha, c, s);
         default: return cudaErrorInvalidValue;
     }
 }

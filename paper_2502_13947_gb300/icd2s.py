@@ -31,6 +31,7 @@ EXPORTS = (
     "icd2s_get_control", "icd2s_anneal_subqubos_batch", "icd2s_apply_flips_update_gains", "icd2s_mutate",
     "icd2s_best_update", "icd2s_initial_pass", "icd2s_step", "icd2s_step_host", "icd2s_run", "icd2s_tables",
     "icd2s_set_timing", "icd2s_get_phase_ms", "icd2s_kernel_launches", "icd2s_apply_flips_static",
+    "icd2s_set_tuning", "icd2s_get_tuning", "icd2s_autotune",
 )
 PHASES = ("tabu", "select", "anneal", "apply_anneal", "mutate", "apply_mutate", "best")
 
@@ -114,6 +115,9 @@ def lib():
                 "icd2s_get_phase_ms": (C.c_int, [vp, vp]),
                 "icd2s_kernel_launches": (C.c_int, [P(u64)]),
                 "icd2s_apply_flips_static": (C.c_int, [vp, i32, i32, i32, vp, vp, vp, vp, vp]),
+                "icd2s_set_tuning": (C.c_int, [vp, vp]),
+                "icd2s_get_tuning": (C.c_int, [vp, vp]),
+                "icd2s_autotune": (C.c_int, [vp, P(Params), vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -306,3 +310,24 @@ def icd2s_apply_flips_static(Q_dev: int, n: int, ld: int, replicas: int, flips_d
     include/icd2s.h): for callers that cannot call cudaMalloc."""
     _check(lib().icd2s_apply_flips_static(C.c_void_p(Q_dev), n, ld, replicas, C.c_void_p(flips_dev),
                                           C.c_void_p(x_dev), C.c_void_p(g_dev), C.c_void_p(E_dev), _s(stream)))
+
+
+class Tuning(C.Structure):
+    _fields_ = [("tabu_variant", C.c_int32), ("anneal_warps_per_cta", C.c_int32), ("reserved", C.c_int32 * 6)]
+
+
+def icd2s_set_tuning(st, tabu_variant: int = -1, anneal_warps_per_cta: int = 0) -> None:
+    t = Tuning(tabu_variant=tabu_variant, anneal_warps_per_cta=anneal_warps_per_cta)
+    _check(lib().icd2s_set_tuning(st, C.byref(t)))
+
+
+def icd2s_get_tuning(st) -> dict:
+    t = Tuning()
+    _check(lib().icd2s_get_tuning(st, C.byref(t)))
+    return dict(tabu_variant=t.tabu_variant, anneal_warps_per_cta=t.anneal_warps_per_cta)
+
+
+def icd2s_autotune(st, p: Params, stream=0) -> dict:
+    t = Tuning()
+    _check(lib().icd2s_autotune(st, C.byref(p), C.byref(t), _s(stream)))
+    return dict(tabu_variant=t.tabu_variant, anneal_warps_per_cta=t.anneal_warps_per_cta)

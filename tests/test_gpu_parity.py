@@ -281,3 +281,45 @@ def test_initial_pass(L, orc, n, z, m):
     So, Eo = orc.initial_pass(P.Q, orc_params(orc, lp), 5, S0)
     assert np.array_equal(x, So) and np.array_equal(E, Eo)
     P.close()
+
+
+# ----------------------------------------------------------------------------- kernel variants
+@pytest.mark.parametrize("variant", range(6))
+def test_every_tabu_variant_gives_the_same_search(L, orc, variant):
+    n, R, alpha, c = 700, 3, 900, 5
+    P = Problem(n, 0.5, 12, R=R)
+    try:
+        I.icd2s_set_tuning(P.st, tabu_variant=variant)
+    except I.ICD2SError as e:
+        assert e.code == I.ERR_ARG  # the variant cannot cover n with its block size
+        P.close()
+        return
+    X0 = random_solutions(n, R, 13)
+    P.load(X0)
+    I.icd2s_tabu(P.st, alpha, c)
+    x, g, E = P.state()
+    T, Cm = I.icd2s_get_tabu(P.st, R, n)
+    for p in range(R):
+        xo, Eo, To, Co = orc.tabu(P.Q, X0[p], alpha, c)
+        assert np.array_equal(x[p], xo) and E[p] == Eo
+        assert np.array_equal(T[p], To) and np.array_equal(Cm[p], Co)
+        assert np.array_equal(g[p], orc.gains(P.Q, xo))
+    P.close()
+
+
+def test_autotune_keeps_the_state_and_the_results(L, orc):
+    n, z = 900, 6
+    P = Problem(n, 0.3, 4, R=z, state_seed=21)
+    lp = lib_params(I, n, z=z, K=2, m_min=20, m_max=100, m_init=50, alpha=2 * n, c=6, sweeps=40, T_max=900.0)
+    S0 = random_solutions(n, z, 8)
+    P.load(S0)
+    x0, g0, E0 = P.state()
+    choice = I.icd2s_autotune(P.st, lp)
+    assert choice == I.icd2s_get_tuning(P.st)
+    x1, g1, E1 = P.state()
+    assert np.array_equal(x0, x1) and np.array_equal(g0, g1) and np.array_equal(E0, E1)
+    I.icd2s_step(P.st, lp, 0)
+    x, g, E = P.state()
+    o = orc.step(P.Q, orc_params(orc, lp), 21, 0, S0)
+    assert np.array_equal(x, o["S"]) and np.array_equal(E, o["E"])
+    P.close()
