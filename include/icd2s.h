@@ -66,7 +66,11 @@ typedef struct icd2s_params {
     double mut_rate;
     int32_t patience;   /* stop after this many iterations without a new best (<= 0: off) */
     int32_t max_iters;  /* hard cap on outer iterations */
-    int32_t reserved[8];
+    int32_t use_graph;  /* 1: icd2s_step / icd2s_run replay one captured CUDA graph per outer
+                           iteration (re-captured when parameters or tuning change); the
+                           iteration number and mutation rate are then read from device memory.
+                           Results are identical; per-phase timing and traces are not available. */
+    int32_t reserved[7];
 } icd2s_params;
 
 /* Per-call anneal parameters (the emulated Ising machine). */

@@ -125,6 +125,18 @@ struct icd2s_state {
     int beta_sweeps = -1; double beta_tmax = 0, beta_tmin = 0;
     bool have_select = false; int sel_K = 0;
     icd2s_tuning tune{-1, 0, {0}};  // kernel variants (see icd2s_set_tuning)
+    // persistent anneal queue (uneven subQUBOs) and the iteration context of a captured step
+    int32_t* lpt = nullptr;      // [R * 64] subQUBOs in largest-first order
+    int32_t* queue = nullptr;    // [1] queue counter
+    int32_t* ctx = nullptr;      // [4] ctx[0] = iteration number read by a replayed step
+    double* rates = nullptr; int rates_cap = 0; int rates_mode = -1; double rates_const = 0;
+    unsigned gen = 0;            // bumped whenever a buffer or a launch configuration changes
+    cudaGraphExec_t graph = nullptr;
+    icd2s_params graph_p{};
+    unsigned graph_gen = 0;
+    int dev_t = -1;              // value of ctx[0] after the last replay (-1: unknown)
+    cudaStream_t own_stream = nullptr;  // captures cannot use the legacy default stream
+    cudaEvent_t join_ev = nullptr;
     // phase timing of icd2s_step: events [2 * phase] / [2 * phase + 1]
     bool timing = false, timed_step = false;
     cudaEvent_t ev[2 * ICD2S_PHASES] = {};
@@ -140,12 +152,40 @@ static void free_state(icd2s_state* st)
 {
     void* ptrs[] = {st->X, st->G, st->E, st->T, st->C, st->gamma, st->A, st->delta, st->order, st->sel,
                     st->FL, st->FCNT, st->DEACC, st->DONE, st->best_x, st->best_E, st->flags, st->idx,
-                    st->off, st->scratch, st->counters, st->nlog, st->beta, st->limtab};
+                    st->off, st->scratch, st->counters, st->nlog, st->beta, st->limtab,
+                    st->lpt, st->queue, st->ctx, st->rates};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (st->graph) cudaGraphExecDestroy(st->graph);
+    if (st->own_stream) cudaStreamDestroy(st->own_stream);
+    if (st->join_ev) cudaEventDestroy(st->join_ev);
     for (cudaEvent_t e : st->ev)
         if (e) cudaEventDestroy(e);
     delete st;
+}
+
+// Mutation rates r_0 .. r_{upto-1} in device memory, for replayed steps.
+static int ensure_rates(icd2s_state* st, int mut_mode, double mut_rate, int upto, cudaStream_t s)
+{
+    if (mut_mode == st->rates_mode && (mut_mode == 1 ? mut_rate == st->rates_const : true) && upto <= st->rates_cap)
+        return ICD2S_OK;
+    int cap = st->rates_cap > 0 ? st->rates_cap : 1024;
+    while (cap < upto) cap *= 2;
+    std::vector<double> r((size_t)cap);
+    for (int t = 0; t < cap; ++t) r[t] = mut_mode == 0 ? mutation_rate(t) : mut_rate;
+    CK(cudaStreamSynchronize(s));
+    if (cap > st->rates_cap) {
+        if (st->rates) CK(cudaFree(st->rates));
+        st->rates = nullptr;
+        st->rates_cap = 0;
+        ++st->gen;
+        CK(dalloc(&st->rates, (size_t)cap));
+        st->rates_cap = cap;
+    }
+    CK(cudaMemcpy(st->rates, r.data(), sizeof(double) * cap, cudaMemcpyHostToDevice));
+    st->rates_mode = mut_mode;
+    st->rates_const = mut_rate;
+    return ICD2S_OK;
 }
 
 static int ensure_beta(icd2s_state* st, int sweeps, double T_max, double T_min, cudaStream_t s)
@@ -156,6 +196,7 @@ static int ensure_beta(icd2s_state* st, int sweeps, double T_max, double T_min, 
         CK(cudaStreamSynchronize(s));
         if (st->beta) CK(cudaFree(st->beta));
         if (st->limtab) CK(cudaFree(st->limtab));
+        ++st->gen;  // a captured step holds the old pointers
         st->beta = nullptr;
         st->limtab = nullptr;
         st->beta_cap = 0;
@@ -322,7 +363,7 @@ int icd2s_state_create(icd2s_qubo* q, int32_t replicas, uint64_t seed, icd2s_sta
     ALLOC(A, RL); ALLOC(delta, RL); ALLOC(order, RL); ALLOC(sel, RL); ALLOC(FL, RL); ALLOC(FCNT, replicas);
     ALLOC(DEACC, replicas); ALLOC(DONE, replicas); ALLOC(best_x, q->ld); ALLOC(best_E, 1); ALLOC(flags, 4);
     ALLOC(idx, RL); ALLOC(off, (size_t)replicas * 64 + 1); ALLOC(scratch, RL); ALLOC(counters, 4);
-    ALLOC(nlog, 4096);
+    ALLOC(nlog, 4096); ALLOC(lpt, (size_t)replicas * 64); ALLOC(queue, 4); ALLOC(ctx, 4);
 #undef ALLOC
     if (e != cudaSuccess) {
         free_state(st);
@@ -429,8 +470,9 @@ int icd2s_tabu(icd2s_state* st, int32_t alpha, int32_t c, void* stream)
     return ICD2S_OK;
 }
 
+// iter_dev: non-null when the iteration number comes from device memory (a replayed step).
 static int select_impl(icd2s_state* st, int64_t w1, int64_t w2, int64_t w3, int K, int m_min, int m_max,
-                       uint32_t iter, cudaStream_t s)
+                       uint32_t iter, cudaStream_t s, const int32_t* iter_dev = nullptr)
 {
     const int n = st->q->n;
     REQ(K >= 1 && K <= 64, ICD2S_ERR_RANGE, "K=%d outside 1..64", K);
@@ -439,7 +481,7 @@ static int select_impl(icd2s_state* st, int64_t w1, int64_t w2, int64_t w3, int 
     const int64_t wl = (int64_t)1 << 24;
     REQ(w1 >= -wl && w1 <= wl && w2 >= -wl && w2 <= wl && w3 >= -wl && w3 <= wl, ICD2S_ERR_RANGE, "|w| > 2^24");
     CK(launch_gamma(st->d, s));
-    CK(launch_sizes(st->R, K, m_min, m_max, st->d.k0, st->d.k1, iter, st->off, s));
+    CK(launch_sizes(st->R, K, m_min, m_max, st->d.k0, st->d.k1, iter, iter_dev, st->off, st->lpt, st->queue, s));
     CK(launch_select(st->d, w1, w2, w3, K, st->off, st->idx, s));
     st->have_select = true;
     st->sel_K = K;
@@ -462,9 +504,12 @@ int icd2s_select_subqubos(icd2s_state* st, const icd2s_select_params* sp, int32_
     return ICD2S_OK;
 }
 
+// queued: the subQUBOs have uneven sizes and were ordered largest-first by
+// the selection (st->lpt), so the persistent kernel takes them from its queue.
 static int anneal_impl(icd2s_state* st, const int32_t* idx, const int32_t* off, int count, int per_replica,
                        int m_max, int block_m, int block_base, int sweeps, double T_max, double T_min, uint32_t iter,
-                       uint8_t* mask, int ldm, int64_t* dE, cudaStream_t s)
+                       uint8_t* mask, int ldm, int64_t* dE, cudaStream_t s, bool queued = false,
+                       const int32_t* iter_dev = nullptr)
 {
     int rc = ensure_beta(st, sweeps, T_max, T_min, s);
     if (rc) return rc;
@@ -473,6 +518,8 @@ static int anneal_impl(icd2s_state* st, const int32_t* idx, const int32_t* off, 
     a.block_base = block_base; a.limtab = st->limtab; a.sweeps = sweeps; a.iter = iter;
     a.slot_base = 0; a.mask = mask; a.ldm = ldm; a.dE = dE; a.attempts_acc = st->counters; a.m_max = m_max;
     a.warps_per_cta = st->tune.anneal_warps_per_cta;
+    a.iter_dev = iter_dev;
+    if (queued) { a.queue = st->queue; a.order = st->lpt; }
     CK(launch_anneal(st->d, a, s));
     return ICD2S_OK;
 }
@@ -516,7 +563,7 @@ static int mutate_impl(icd2s_state* st, int mut_mode, double mut_rate, uint32_t 
     REQ(mut_mode == 0 || (mut_mode == 1 && mut_rate >= 0 && mut_rate <= 1), ICD2S_ERR_ARG, "bad mutation rate");
     const double r = mut_mode == 0 ? mutation_rate((int)iter) : mut_rate;
     if (mask) CK(cudaMemsetAsync(mask, 0, (size_t)st->R * st->q->n, s));
-    CK(launch_mutate(st->d, st->sel_K, st->off, r, iter, mask, st->q->n, s));
+    CK(launch_mutate(st->d, st->sel_K, st->off, r, iter, nullptr, nullptr, mask, st->q->n, s));
     CK(launch_apply(st->d, s));
     return ICD2S_OK;
 }
@@ -530,7 +577,7 @@ int icd2s_mutate(icd2s_state* st, const icd2s_mutate_params* mp, uint8_t* flips_
 int icd2s_best_update(icd2s_state* st, void* stream)
 {
     REQ(st, ICD2S_ERR_ARG, "NULL state");
-    CK(launch_best(st->d, nullptr, 0, S(stream)));
+    CK(launch_best(st->d, nullptr, 0, nullptr, S(stream)));
     return ICD2S_OK;
 }
 
@@ -550,39 +597,91 @@ int icd2s_initial_pass(icd2s_state* st, const icd2s_params* p, void* stream)
     return ICD2S_OK;
 }
 
-static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* trace_it, cudaStream_t s)
+// One outer iteration.  dev_iter: the kernels read t (and the mutation rate)
+// from st->ctx / st->rates, and the last one advances st->ctx[0] -- the form
+// that is captured once and replayed as a CUDA graph.
+static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* trace_it, cudaStream_t s,
+                     bool dev_iter = false)
 {
     const int R = st->R;
+    const int32_t* it_dev = dev_iter ? st->ctx : nullptr;
+    const bool queued = p->K > 1 || p->m_min != p->m_max;  // uneven batch: persistent queue kernel
     int rc = ensure_beta(st, p->sweeps, p->T_max, p->T_min, s);
     if (rc) return rc;
     mark(st, 0, 0, s);
     CK(launch_tabu(st->d, p->alpha, p->c, st->tune.tabu_variant, s));                     // Algorithm 1
     mark(st, 0, 1, s);
-    CK(launch_best(st->d, trace_it, 0, s));
+    CK(launch_best(st->d, trace_it, 0, nullptr, s));
     mark(st, 1, 0, s);
-    rc = select_impl(st, p->w1, p->w2, p->w3, p->K, p->m_min, p->m_max, (uint32_t)t, s);  // Eq. 6-8, Alg. 3
+    rc = select_impl(st, p->w1, p->w2, p->w3, p->K, p->m_min, p->m_max, (uint32_t)t, s, it_dev);  // Eq. 6-8, Alg. 3
     if (rc) return rc;
     mark(st, 1, 1, s);
     mark(st, 2, 0, s);
     rc = anneal_impl(st, st->idx, st->off, R * p->K, p->K, p->m_max, 0, 0, p->sweeps, p->T_max, p->T_min,
-                     (uint32_t)t, nullptr, 0, nullptr, s);                        // Eq. 4, Algorithm 4
+                     (uint32_t)t, nullptr, 0, nullptr, s, queued, it_dev);                 // Eq. 4, Algorithm 4
     if (rc) return rc;
     mark(st, 2, 1, s);
     mark(st, 3, 0, s);
     CK(launch_apply(st->d, s));
     mark(st, 3, 1, s);
-    CK(launch_best(st->d, trace_it ? trace_it + R : nullptr, 0, s));
+    CK(launch_best(st->d, trace_it ? trace_it + R : nullptr, 0, nullptr, s));
     const double r = p->mut_mode == 0 ? mutation_rate(t) : p->mut_rate;        // Eq. 5
     mark(st, 4, 0, s);
-    CK(launch_mutate(st->d, st->sel_K, st->off, r, (uint32_t)t, nullptr, st->q->n, s));
+    CK(launch_mutate(st->d, st->sel_K, st->off, r, (uint32_t)t, it_dev, st->rates, nullptr, st->q->n, s));
     mark(st, 4, 1, s);
     mark(st, 5, 0, s);
     CK(launch_apply(st->d, s));
     mark(st, 5, 1, s);
     mark(st, 6, 0, s);
-    CK(launch_best(st->d, trace_it ? trace_it + 2 * R : nullptr, 1, s));
+    CK(launch_best(st->d, trace_it ? trace_it + 2 * R : nullptr, 1, dev_iter ? st->ctx : nullptr, s));
     mark(st, 6, 1, s);
     st->timed_step = st->timing;
+    return ICD2S_OK;
+}
+
+// Replays the outer iteration as one CUDA graph, capturing it first when
+// there is no graph yet or the parameters, tuning or buffers changed.
+static int graph_step(icd2s_state* st, const icd2s_params* p, int t, cudaStream_t caller)
+{
+    int rc = ensure_beta(st, p->sweeps, p->T_max, p->T_min, caller);
+    if (rc) return rc;
+    rc = ensure_rates(st, p->mut_mode, p->mut_rate, t + 1, caller);
+    if (rc) return rc;
+    cudaStream_t s = caller;
+    if (!s) {  // the legacy stream cannot be captured: run on a private stream joined to it
+        if (!st->own_stream) CK(cudaStreamCreateWithFlags(&st->own_stream, cudaStreamNonBlocking));
+        if (!st->join_ev) CK(cudaEventCreateWithFlags(&st->join_ev, cudaEventDisableTiming));
+        s = st->own_stream;
+        CK(cudaEventRecord(st->join_ev, caller));
+        CK(cudaStreamWaitEvent(s, st->join_ev, 0));
+    }
+    if (!st->graph || st->graph_gen != st->gen || std::memcmp(&st->graph_p, p, sizeof *p) != 0) {
+        if (st->graph) { cudaGraphExecDestroy(st->graph); st->graph = nullptr; }
+        const bool timing = st->timing;
+        st->timing = false;  // no event records inside the graph
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+        rc = step_impl(st, p, 0, nullptr, s, true);
+        st->timing = timing;
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(s, &g);
+        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+        CK(ec);
+        const cudaError_t ei = cudaGraphInstantiate(&st->graph, g, 0);
+        cudaGraphDestroy(g);
+        CK(ei);
+        st->graph_p = *p;
+        st->graph_gen = st->gen;
+        st->dev_t = -1;
+    }
+    if (st->dev_t != t) CK(launch_set_iter(st->ctx, t, s));
+    CK(cudaGraphLaunch(st->graph, s));
+    note_launch(11);  // the kernels of one outer iteration
+    st->dev_t = t + 1;
+    st->timed_step = false;
+    if (!caller) {
+        CK(cudaEventRecord(st->join_ev, s));
+        CK(cudaStreamWaitEvent(caller, st->join_ev, 0));
+    }
     return ICD2S_OK;
 }
 
@@ -617,6 +716,7 @@ int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t)
     REQ(t->anneal_warps_per_cta >= 0 && t->anneal_warps_per_cta <= 4, ICD2S_ERR_ARG,
         "anneal_warps_per_cta=%d outside 0..4", t->anneal_warps_per_cta);
     st->tune = *t;
+    ++st->gen;  // launch configurations changed: re-capture
     return ICD2S_OK;
 }
 
@@ -707,6 +807,7 @@ int icd2s_autotune(icd2s_state* st, const icd2s_params* p, icd2s_tuning* chosen,
     CK(cudaStreamSynchronize(s));
     st->have_select = false;
     st->tune = best;
+    ++st->gen;
     if (chosen) *chosen = best;
     return ICD2S_OK;
 }
@@ -724,7 +825,7 @@ int icd2s_step(icd2s_state* st, const icd2s_params* p, int32_t t, void* stream)
     int rc = check_params(st, p);
     if (rc) return rc;
     REQ(t >= 0, ICD2S_ERR_ARG, "t < 0");
-    return step_impl(st, p, t, nullptr, S(stream));
+    return p->use_graph ? graph_step(st, p, t, S(stream)) : step_impl(st, p, t, nullptr, S(stream));
 }
 
 int icd2s_step_host(icd2s_state* st, const icd2s_params* p, int32_t t, const uint8_t* x_in, uint8_t* x_out,
@@ -740,7 +841,7 @@ int icd2s_step_host(icd2s_state* st, const icd2s_params* p, int32_t t, const uin
         CK(launch_pad_rows(st->scratch, n, R, st->X, ld, s));
         CK(launch_recompute(st->d, st->X, ld, R, st->G, st->E, s));
     }
-    rc = step_impl(st, p, t, nullptr, s);
+    rc = p->use_graph ? graph_step(st, p, t, s) : step_impl(st, p, t, nullptr, s);
     if (rc) return rc;
     if (x_out) CK(cudaMemcpy2DAsync(x_out, n, st->X, ld, n, R, cudaMemcpyDeviceToHost, s));
     if (E_out) CK(cudaMemcpyAsync(E_out, st->E, (size_t)R * 8, cudaMemcpyDeviceToHost, s));
@@ -772,17 +873,21 @@ int icd2s_run(icd2s_qubo* q, const icd2s_params* p, uint64_t seed, uint8_t* x_ou
     CK(cudaEventRecord(guard.e0, s));
     rc = icd2s_initial_pass(st, p, s);
     if (rc) return rc;
-    CK(launch_best(st->d, nullptr, 0, s));
+    CK(launch_best(st->d, nullptr, 0, nullptr, s));
     CK(cudaMemsetAsync(st->flags, 0, 8, s));
     int64_t init_best = 0;
     CK(cudaMemcpyAsync(&init_best, st->best_E, 8, cudaMemcpyDeviceToHost, s));
     int t = 0;
     int32_t flags[2] = {0, 0};
+    const bool graph = p->use_graph && !trace;
     while (t < p->max_iters && (p->patience <= 0 || flags[1] < p->patience)) {
-        rc = step_impl(st, p, t, guard.tr ? guard.tr + (size_t)t * (3 * R + 1) : nullptr, s);
+        if (graph) rc = graph_step(st, p, t, s);
+        else rc = step_impl(st, p, t, guard.tr ? guard.tr + (size_t)t * (3 * R + 1) : nullptr, s);
         if (rc) return rc;
-        CK(cudaMemcpyAsync(flags, st->flags, 8, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+        if (p->patience > 0) {  // the termination test needs this iteration's stale count
+            CK(cudaMemcpyAsync(flags, st->flags, 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
         ++t;
     }
     CK(cudaEventRecord(guard.e1, s));

@@ -86,12 +86,16 @@ cudaError_t launch_pad_rows(const uint8_t* src, int n, int rows, uint8_t* dst, i
 cudaError_t launch_tabu(const Dev& d, int alpha, int c, int w_words, cudaStream_t s);
 size_t tabu_smem_bytes(int n, int alpha);
 cudaError_t launch_gamma(const Dev& d, cudaStream_t s);
+// Iteration context read by the kernels of a captured outer iteration (a CUDA
+// graph replays the same launches, so the iteration number and the mutation
+// rate come from device memory): iter_dev[0] = t, rates[t] = the rate.  When
+// iter_dev is null the kernels use their `iter` / `rate` arguments.
 cudaError_t launch_sizes(int R, int K, int m_min, int m_max, uint32_t k0, uint32_t k1, uint32_t iter,
-                         int32_t* off, cudaStream_t s);
+                         const int32_t* iter_dev, int32_t* off, int32_t* order, int32_t* queue, cudaStream_t s);
 cudaError_t launch_select(const Dev& d, int64_t w1, int64_t w2, int64_t w3, int K, const int32_t* off,
                           int32_t* idx, cudaStream_t s);
 cudaError_t launch_mutate(const Dev& d, int K, const int32_t* off, double rate, uint32_t iter,
-                          uint8_t* mask, int ldm, cudaStream_t s);
+                          const int32_t* iter_dev, const double* rates, uint8_t* mask, int ldm, cudaStream_t s);
 struct AnnealArgs {
     const int32_t* idx; const int32_t* off; int count; int per_replica;
     int block_m; int block_base;          // idx == nullptr: contiguous block [base, base+m)
@@ -100,7 +104,11 @@ struct AnnealArgs {
     int64_t* dE; int64_t* attempts_acc;   // optional outputs
     int m_max;
     int warps_per_cta;                    // 0: default
+    const int32_t* iter_dev;              // non-null: the iteration number is read from here
+    int32_t* queue;                       // non-null: persistent kernel, subQUBOs taken in `order`
+    const int32_t* order;
 };
+int device_sm_count();
 bool tabu_variant_fits(int variant, int n);
 int tabu_num_variants();
 int tabu_default_variant(int n);
@@ -108,6 +116,7 @@ cudaError_t launch_anneal(const Dev& d, const AnnealArgs& a, cudaStream_t s);
 cudaError_t launch_limtab(const uint32_t* beta, int sweeps, const uint32_t* nlog, int* lim, cudaStream_t s);
 cudaError_t launch_compact_mask(const Dev& d, const uint8_t* mask, int ldm, cudaStream_t s);
 cudaError_t launch_apply(const Dev& d, cudaStream_t s);
-cudaError_t launch_best(const Dev& d, int64_t* trace_slot, int iter_end, cudaStream_t s);
+cudaError_t launch_best(const Dev& d, int64_t* trace_slot, int iter_end, int32_t* iter_dev, cudaStream_t s);
+cudaError_t launch_set_iter(int32_t* iter_dev, int t, cudaStream_t s);
 
 }  // namespace icd2s

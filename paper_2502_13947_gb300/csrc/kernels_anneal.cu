@@ -57,16 +57,14 @@ __device__ __forceinline__ int accept_limit(uint32_t thr, uint32_t beta)
     return (int)((thr - 1u) / beta);
 }
 
+// Anneals subQUBO s with the calling warp; Qs is the warp's (32 P)^2-byte
+// shared-memory tile.  Warp-synchronous: no block-level barriers.
 template <int P>
-__global__ __launch_bounds__(128) void k_anneal(Dev d, AnnealArgs a)
+__device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, int s, int lane, int8_t* Qs)
 {
     using Seg = typename RowSeg<P>::T;
     constexpr int MC = 32 * P;  // row length (bytes) of the staged Q'
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    const int s = blockIdx.x * wpb + wib;
-    if (s >= a.count) return;  // whole warp leaves; no block-level barriers below
-    int8_t* Qs = reinterpret_cast<int8_t*>(smem) + (size_t)wib * MC * MC;
+    const uint32_t iter = a.iter_dev ? (uint32_t)*a.iter_dev : a.iter;
 
     const int p = s / a.per_replica;
     const int* S = nullptr;
@@ -127,7 +125,7 @@ __global__ __launch_bounds__(128) void k_anneal(Dev d, AnnealArgs a)
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             const u32x4 u = philox10((uint32_t)(k4 >> 2), (kTagAnneal << 24) | (uint32_t)(lane + 32 * q), slot,
-                                     a.iter, d.k0, d.k1);
+                                     iter, d.k0, d.k1);
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int k = k4 + r < a.sweeps ? k4 + r : a.sweeps - 1;
@@ -225,6 +223,45 @@ __global__ __launch_bounds__(128) void k_anneal(Dev d, AnnealArgs a)
     }
 }
 
+// One warp per subQUBO, subQUBO s = CTA * warps + warp (sizes up to 32 P).
+template <int P>
+__global__ __launch_bounds__(128) void k_anneal(Dev d, AnnealArgs a)
+{
+    constexpr int MC = 32 * P;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const int s = blockIdx.x * wpb + wib;
+    if (s >= a.count) return;  // whole warp leaves; no block-level barriers below
+    anneal_one<P>(d, a, s, lane, reinterpret_cast<int8_t*>(smem) + (size_t)wib * MC * MC);
+}
+
+// Persistent batch of subQUBOs of uneven size: every warp takes the next
+// subQUBO from a device queue in largest-first order (a.order, sizes
+// descending, built by k_sizes) and anneals it with the narrowest lane layout
+// that fits its size.  The queue is one counter; no warp ever waits on
+// another, and each subQUBO's result does not depend on which warp runs it.
+template <int PMAX>
+__global__ __launch_bounds__(128) void k_anneal_queue(Dev d, AnnealArgs a)
+{
+    constexpr int MC = 32 * PMAX;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int8_t* Qs = reinterpret_cast<int8_t*>(smem) + (size_t)wib * MC * MC;
+    while (true) {
+        int next = 0;
+        if (lane == 0) next = atomicAdd(a.queue, 1);
+        next = __shfl_sync(0xffffffffu, next, 0);
+        if (next >= a.count) break;
+        const int s = a.order[next];
+        const int m = a.off[s + 1] - a.off[s];
+        if (m <= 32) anneal_one<1>(d, a, s, lane, Qs);
+        else if (m <= 64) { if constexpr (PMAX >= 2) anneal_one<2>(d, a, s, lane, Qs); }
+        else if (m <= 128) { if constexpr (PMAX >= 4) anneal_one<4>(d, a, s, lane, Qs); }
+        else { if constexpr (PMAX >= 8) anneal_one<8>(d, a, s, lane, Qs); }
+        __syncwarp();  // the tile is reused by the next subQUBO
+    }
+}
+
 // LIM[k][j] for the whole schedule: the largest gain that attempt (k, j) accepts.
 __global__ void k_limtab(const uint32_t* __restrict__ beta, int sweeps, const uint32_t* __restrict__ nlog,
                          int* __restrict__ lim)
@@ -257,6 +294,28 @@ static cudaError_t launch_anneal_p(const Dev& d, const AnnealArgs& a, int wpb, c
     return cudaGetLastError();
 }
 
+// Persistent launch: as many warps as fit on the GPU at once (by shared
+// memory), never more than there are subQUBOs.
+template <int PMAX>
+static cudaError_t launch_anneal_queue(const Dev& d, const AnnealArgs& a, int wpb, cudaStream_t s)
+{
+    constexpr int MC = 32 * PMAX;
+    const size_t per_warp = (size_t)MC * MC;
+    const size_t sm = (size_t)wpb * per_warp;
+    cudaError_t e = cudaFuncSetAttribute(k_anneal_queue<PMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int ctas_per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_anneal_queue<PMAX>, 32 * wpb, sm);
+    if (e != cudaSuccess) return e;
+    if (ctas_per_sm < 1) ctas_per_sm = 1;
+    int blocks = device_sm_count() * ctas_per_sm;
+    const int need = (a.count + wpb - 1) / wpb;
+    if (blocks > need) blocks = need;
+    k_anneal_queue<PMAX><<<blocks, 32 * wpb, sm, s>>>(d, a);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_anneal(const Dev& d, const AnnealArgs& a, cudaStream_t s)
 {
     if (a.count <= 0) return cudaSuccess;
@@ -266,6 +325,13 @@ cudaError_t launch_anneal(const Dev& d, const AnnealArgs& a, cudaStream_t s)
     if (wpb <= 0) wpb = m <= 128 ? 2 : 1;
     if (m > 128 && wpb > 3) wpb = 3;
     if (wpb > 4) wpb = 4;
+    if (a.queue) {
+        if (m <= 32) return launch_anneal_queue<1>(d, a, wpb, s);
+        if (m <= 64) return launch_anneal_queue<2>(d, a, wpb, s);
+        if (m <= 128) return launch_anneal_queue<4>(d, a, wpb, s);
+        if (m <= 256) return launch_anneal_queue<8>(d, a, wpb, s);
+        return cudaErrorInvalidValue;
+    }
     if (m <= 32) return launch_anneal_p<1>(d, a, wpb, s);
     if (m <= 64) return launch_anneal_p<2>(d, a, wpb, s);
     if (m <= 128) return launch_anneal_p<4>(d, a, wpb, s);

@@ -74,10 +74,16 @@ __host__ __device__ inline int next_pow2(int v)
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Also writes, when `order` is given, the subQUBOs in largest-first order
+// (a counting sort by size; the order among equal sizes is immaterial) for
+// the persistent anneal kernel, and resets its queue counter.
 __global__ __launch_bounds__(1024) void k_sizes(int R, int K, int m_min, int m_max, uint32_t k0, uint32_t k1,
-                                                uint32_t iter, int32_t* off)
+                                                uint32_t iter_arg, const int32_t* iter_dev, int32_t* off,
+                                                int32_t* order, int32_t* queue)
 {
     __shared__ int part[1024];
+    __shared__ int start[kMaxM + 2];
+    const uint32_t iter = iter_dev ? (uint32_t)*iter_dev : iter_arg;
     const int total = R * K;
     const int NT = blockDim.x, tid = threadIdx.x;
     const int chunk = (total + NT - 1) / NT;
@@ -102,12 +108,24 @@ __global__ __launch_bounds__(1024) void k_sizes(int R, int K, int m_min, int m_m
     for (int s = lo; s < hi; ++s) { off[s] = run; run += size_of(s); }
     if (hi == total && lo < hi) off[total] = run;
     if (total == 0 && tid == 0) off[0] = 0;
+    if (!order) return;
+    for (int m = tid; m < kMaxM + 2; m += NT) start[m] = 0;
+    __syncthreads();
+    for (int s = lo; s < hi; ++s) atomicAdd(&start[size_of(s)], 1);
+    __syncthreads();
+    if (tid == 0) {  // sizes descending: start[m] = number of subQUBOs larger than m
+        int acc = 0;
+        for (int m = kMaxM; m >= 0; --m) { const int v = start[m]; start[m] = acc; acc += v; }
+        *queue = 0;
+    }
+    __syncthreads();
+    for (int s = lo; s < hi; ++s) order[atomicAdd(&start[size_of(s)], 1)] = s;
 }
 
 cudaError_t launch_sizes(int R, int K, int m_min, int m_max, uint32_t k0, uint32_t k1, uint32_t iter,
-                         int32_t* off, cudaStream_t s)
+                         const int32_t* iter_dev, int32_t* off, int32_t* order, int32_t* queue, cudaStream_t s)
 {
-    k_sizes<<<1, 1024, 0, s>>>(R, K, m_min, m_max, k0, k1, iter, off);
+    k_sizes<<<1, 1024, 0, s>>>(R, K, m_min, m_max, k0, k1, iter, iter_dev, off, order, queue);
     note_launch(1);
     return cudaGetLastError();
 }
@@ -188,11 +206,14 @@ cudaError_t launch_select(const Dev& d, int64_t w1, int64_t w2, int64_t w3, int 
 }
 
 // ---------------------------------------------------------------------------
-__global__ __launch_bounds__(1024) void k_mutate(Dev d, int K, const int32_t* __restrict__ off, double rate,
-                                                 uint32_t iter, uint8_t* mask, int ldm)
+__global__ __launch_bounds__(1024) void k_mutate(Dev d, int K, const int32_t* __restrict__ off, double rate_arg,
+                                                 uint32_t iter_arg, const int32_t* iter_dev, const double* rates,
+                                                 uint8_t* mask, int ldm)
 {
     __shared__ int red[33];
     __shared__ int wsum[32];
+    const uint32_t iter = iter_dev ? (uint32_t)*iter_dev : iter_arg;
+    const double rate = iter_dev ? rates[iter] : rate_arg;
     const int p = blockIdx.x, tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int n = d.n, ld = d.ld;
     const int32_t* Arow = d.A + (size_t)p * ld;
@@ -237,10 +258,10 @@ __global__ __launch_bounds__(1024) void k_mutate(Dev d, int K, const int32_t* __
     }
 }
 
-cudaError_t launch_mutate(const Dev& d, int K, const int32_t* off, double rate, uint32_t iter, uint8_t* mask,
-                          int ldm, cudaStream_t s)
+cudaError_t launch_mutate(const Dev& d, int K, const int32_t* off, double rate, uint32_t iter,
+                          const int32_t* iter_dev, const double* rates, uint8_t* mask, int ldm, cudaStream_t s)
 {
-    k_mutate<<<d.R, 1024, 0, s>>>(d, K, off, rate, iter, mask, ldm);
+    k_mutate<<<d.R, 1024, 0, s>>>(d, K, off, rate, iter, iter_dev, rates, mask, ldm);
     note_launch(1);
     return cudaGetLastError();
 }

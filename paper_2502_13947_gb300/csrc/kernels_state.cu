@@ -199,7 +199,7 @@ cudaError_t launch_gamma(const Dev& d, cudaStream_t s)
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(256) void k_best(const uint8_t* __restrict__ X, int ld, const int64_t* __restrict__ E,
                                               int R, uint8_t* best_x, int64_t* best_E, int32_t* flags,
-                                              int64_t* trace_slot, int iter_end)
+                                              int64_t* trace_slot, int iter_end, int32_t* iter_dev)
 {
     __shared__ long long sE[8];
     __shared__ int sP[8];
@@ -235,14 +235,37 @@ __global__ __launch_bounds__(256) void k_best(const uint8_t* __restrict__ X, int
         if (trace_slot) trace_slot[R] = *best_E;
         flags[1] = flags[0] ? 0 : flags[1] + 1;
         flags[0] = 0;
+        if (iter_dev) *iter_dev += 1;  // the next replay of a captured iteration is t + 1
     }
 }
 
-cudaError_t launch_best(const Dev& d, int64_t* trace_slot, int iter_end, cudaStream_t s)
+cudaError_t launch_best(const Dev& d, int64_t* trace_slot, int iter_end, int32_t* iter_dev, cudaStream_t s)
 {
-    k_best<<<1, 256, 0, s>>>(d.X, d.ld, d.E, d.R, d.best_x, d.best_E, d.flags, trace_slot, iter_end);
+    k_best<<<1, 256, 0, s>>>(d.X, d.ld, d.E, d.R, d.best_x, d.best_E, d.flags, trace_slot, iter_end, iter_dev);
     note_launch(1);
     return cudaGetLastError();
+}
+
+__global__ void k_set_iter(int32_t* iter_dev, int t) { *iter_dev = t; }
+
+cudaError_t launch_set_iter(int32_t* iter_dev, int t, cudaStream_t s)
+{
+    k_set_iter<<<1, 1, 0, s>>>(iter_dev, t);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+int device_sm_count()
+{
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cached[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+        cached[dev] = v;
+    }
+    return cached[dev];
 }
 
 // ---------------------------------------------------------------------------

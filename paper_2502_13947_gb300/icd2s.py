@@ -47,7 +47,7 @@ class Params(C.Structure):
         ("z", C.c_int32), ("K", C.c_int32), ("m_min", C.c_int32), ("m_max", C.c_int32), ("m_init", C.c_int32),
         ("alpha", C.c_int32), ("c", C.c_int32), ("sweeps", C.c_int32), ("T_max", C.c_double), ("T_min", C.c_double),
         ("w1", C.c_int64), ("w2", C.c_int64), ("w3", C.c_int64), ("mut_mode", C.c_int32), ("mut_rate", C.c_double),
-        ("patience", C.c_int32), ("max_iters", C.c_int32), ("reserved", C.c_int32 * 8),
+        ("patience", C.c_int32), ("max_iters", C.c_int32), ("use_graph", C.c_int32), ("reserved", C.c_int32 * 7),
     ]
 
 

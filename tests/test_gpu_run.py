@@ -102,3 +102,47 @@ def test_full_size_step_n2500_density01_m64_z128(L, orc):
     assert bE == o["best_E"] and np.array_equal(bx, o["best_x"])
     for p in range(0, z, 16):      # gains: a sample of replicas, each against its definition
         assert np.array_equal(g[p], orc.gains(Q, x[p]))
+
+
+# ----------------------------------------------------------------------------- CUDA graph replay
+@pytest.mark.parametrize("K,m_min,m_max,patience", [(1, 16, 16, 0), (4, 8, 40, 0), (3, 10, 30, 5)])
+def test_graph_replayed_run_matches_the_oracle(L, orc, K, m_min, m_max, patience):
+    """One outer iteration captured as a CUDA graph and replayed (the
+    iteration number and mutation rate read from device memory); uneven
+    batches go through the persistent queue kernel."""
+    n = 200
+    Q = make_qubo(n, 0.6, 31)
+    lp = lib_params(I, n, z=5, K=K, m_min=m_min, m_max=m_max, m_init=m_max, alpha=n, c=3, sweeps=32,
+                    T_max=1200.0, mut_mode=0, patience=patience, max_iters=25, use_graph=1)
+    q = I.icd2s_qubo_create(Q)
+    try:
+        g = I.icd2s_run(q, lp, 17, trace=False, want_S=True)
+    finally:
+        I.icd2s_qubo_destroy(q)
+    o = orc.run(Q, orc_params(orc, lp), 17)
+    assert g["iters"] == o["iters"]
+    assert np.array_equal(g["S"], o["S"])
+    assert g["best_E"] == o["best_E"] and np.array_equal(g["best_x"], o["best_x"])
+
+
+def test_graph_steps_equal_plain_steps_on_a_stream(L):
+    torch = torch_cuda()
+    n, z = 500, 6
+    Q = make_qubo(n, 0.3, 3)
+    q = I.icd2s_qubo_create(Q)
+    S0 = random_solutions(n, z, 5)
+    out = []
+    for use_graph in (0, 1):
+        lp = lib_params(I, n, z=z, K=3, m_min=12, m_max=70, m_init=50, alpha=n, c=4, sweeps=20, T_max=900.0,
+                        use_graph=use_graph)
+        st = I.icd2s_state_create(q, z, 3)
+        s = torch.cuda.Stream()
+        I.icd2s_state_load(st, S0, stream=s.cuda_stream)
+        for t in (0, 1, 2, 7, 8):   # a jump in t re-seeds the device iteration number
+            I.icd2s_step(st, lp, t, s.cuda_stream)
+        s.synchronize()
+        out.append(I.icd2s_get_state(st, z, n))
+        I.icd2s_state_destroy(st)
+    I.icd2s_qubo_destroy(q)
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
