@@ -70,7 +70,10 @@ typedef struct icd2s_params {
                            iteration (re-captured when parameters or tuning change); the
                            iteration number and mutation rate are then read from device memory.
                            Results are identical; per-phase timing and traces are not available. */
-    int32_t reserved[7];
+    int32_t refresh_every; /* > 0: icd2s_run recomputes all gains and energies on the tensor cores
+                              every this many iterations and fails with ICD2S_ERR_INVARIANT if
+                              they differ from the tracked ones (see icd2s_refresh) */
+    int32_t reserved[6];
 } icd2s_params;
 
 /* Per-call anneal parameters (the emulated Ising machine). */
@@ -195,6 +198,16 @@ int icd2s_mutate(icd2s_state* st, const icd2s_mutate_params* mp, uint8_t* flips_
 /* Folds the current solutions into the best one (strictly lower energy,
  * lowest replica on ties). */
 int icd2s_best_update(icd2s_state* st, void* stream);
+
+/* Dense refresh: recomputes every gain g_i = (1 - 2x_i)(Q_ii + 2 sum_{j!=i} Q_ij x_j)
+ * and energy (Eq. 1) of all replicas from scratch as H = Q X^T on the tensor
+ * cores (tcgen05, BF16 operands, FP32 accumulation: exact for int8 Q and binary
+ * x, since every partial sum is an integer below 2^24), and compares them with
+ * the incrementally tracked values.  mismatches (host, may be NULL) receives
+ * the number of differing entries and synchronises `stream`; rebuild != 0
+ * replaces the tracked values with the recomputed ones.  ICD2S_ERR_TIMEOUT if
+ * a bounded device-side wait gave up. */
+int icd2s_refresh(icd2s_state* st, int32_t rebuild, int32_t* mismatches, void* stream);
 
 /* Call_IM_Solution_Set (Algorithm 2): for each replica, floor(n / m_init)
  * disjoint blocks of m_init consecutive variables are annealed and written

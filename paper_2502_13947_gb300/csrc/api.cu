@@ -102,6 +102,7 @@ struct icd2s_qubo {
     int cap = 0;
     uint8_t* xpad = nullptr;
     int32_t* hpad = nullptr;
+    void* Qb = nullptr;  // bf16 copy of Q for the tensor-core refresh (made on first use)
 };
 
 struct icd2s_state {
@@ -137,6 +138,8 @@ struct icd2s_state {
     int dev_t = -1;              // value of ctx[0] after the last replay (-1: unknown)
     cudaStream_t own_stream = nullptr;  // captures cannot use the legacy default stream
     cudaEvent_t join_ev = nullptr;
+    // dense refresh buffers (made on first use)
+    void* Xb = nullptr; int32_t* G2 = nullptr; int64_t* E2 = nullptr; int* rflags = nullptr;  // [0] timeout, [1] mismatches
     // phase timing of icd2s_step: events [2 * phase] / [2 * phase + 1]
     bool timing = false, timed_step = false;
     cudaEvent_t ev[2 * ICD2S_PHASES] = {};
@@ -153,7 +156,7 @@ static void free_state(icd2s_state* st)
     void* ptrs[] = {st->X, st->G, st->E, st->T, st->C, st->gamma, st->A, st->delta, st->order, st->sel,
                     st->FL, st->FCNT, st->DEACC, st->DONE, st->best_x, st->best_E, st->flags, st->idx,
                     st->off, st->scratch, st->counters, st->nlog, st->beta, st->limtab,
-                    st->lpt, st->queue, st->ctx, st->rates};
+                    st->lpt, st->queue, st->ctx, st->rates, st->Xb, st->G2, st->E2, st->rflags};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (st->graph) cudaGraphExecDestroy(st->graph);
@@ -311,7 +314,7 @@ int icd2s_qubo_create(const int8_t* Q_host, int32_t n, icd2s_qubo** out)
 int icd2s_qubo_destroy(icd2s_qubo* q)
 {
     if (!q) return ICD2S_OK;
-    void* ptrs[] = {q->Q, q->diag, q->eta, q->etahat, q->xpad, q->hpad};
+    void* ptrs[] = {q->Q, q->diag, q->eta, q->etahat, q->xpad, q->hpad, q->Qb};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete q;
@@ -572,6 +575,44 @@ int icd2s_mutate(icd2s_state* st, const icd2s_mutate_params* mp, uint8_t* flips_
 {
     REQ(st && mp, ICD2S_ERR_ARG, "NULL argument");
     return mutate_impl(st, mp->mut_mode, mp->mut_rate, mp->iter, flips_dev, S(stream));
+}
+
+int icd2s_refresh(icd2s_state* st, int32_t rebuild, int32_t* mismatches, void* stream)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    cudaStream_t s = S(stream);
+    icd2s_qubo* q = st->q;
+    const int n = q->n, ld = q->ld, R = st->R;
+    const size_t RL = (size_t)R * ld;
+    if (!q->Qb) {
+        CK(cudaStreamSynchronize(s));
+        CK(cudaMalloc(&q->Qb, (size_t)n * ld * 2));
+        CK(launch_to_bf16(q->Q, true, (size_t)n * ld, q->Qb, s));
+    }
+    if (!st->Xb) {
+        CK(cudaStreamSynchronize(s));
+        CK(cudaMalloc(&st->Xb, RL * 2));
+        CK(dalloc(&st->G2, RL));
+        CK(dalloc(&st->E2, (size_t)R));
+        CK(dalloc(&st->rflags, 4));
+    }
+    CK(cudaMemsetAsync(st->rflags, 0, 16, s));
+    CK(launch_to_bf16(st->X, false, RL, st->Xb, s));
+    CK(launch_refresh_mma(q->Qb, st->Xb, n, R, ld, st->G2, st->rflags, s));   // H into G2
+    CK(launch_finish_gains(q->diag, n, ld, st->X, st->G2, st->E2, R, s));     // H -> g, E
+    CK(launch_compare(st->G, st->E, st->G2, st->E2, n, ld, R, st->rflags + 1, s));
+    if (rebuild) {
+        CK(cudaMemcpyAsync(st->G, st->G2, RL * 4, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(st->E, st->E2, (size_t)R * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    if (mismatches) {
+        int f[2] = {0, 0};
+        CK(cudaMemcpyAsync(f, st->rflags, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        REQ(f[0] == 0, ICD2S_ERR_TIMEOUT, "refresh: a tensor-core pipeline wait timed out");
+        *mismatches = f[1];
+    }
+    return ICD2S_OK;
 }
 
 int icd2s_best_update(icd2s_state* st, void* stream)
@@ -887,6 +928,12 @@ int icd2s_run(icd2s_qubo* q, const icd2s_params* p, uint64_t seed, uint8_t* x_ou
         if (p->patience > 0) {  // the termination test needs this iteration's stale count
             CK(cudaMemcpyAsync(flags, st->flags, 8, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
+        }
+        if (p->refresh_every > 0 && (t + 1) % p->refresh_every == 0) {  // drift check on the tensor cores
+            int32_t bad = 0;
+            rc = icd2s_refresh(st, 0, &bad, s);
+            if (rc) return rc;
+            REQ(bad == 0, ICD2S_ERR_INVARIANT, "tracked gains/energies differ from the refresh in %d entries", bad);
         }
         ++t;
     }

@@ -1,0 +1,374 @@
+// kernels_refresh.cu -- exact dense refresh of all gains on the tensor cores.
+//
+// H = Q X^T for every replica at once (H[p][j] = sum_k Q_jk x_pk), then
+// g = (1 - 2x)(Q_jj + 2 (H - Q_jj x)) and E = sum_j x_j (Q_jj + H_j - Q_jj x_j):
+// a from-scratch recompute of the state the other kernels update
+// incrementally, used to check that the tracked gains and energies never
+// drift (and to rebuild them).
+//
+// tcgen05 (5th-generation tensor cores) with BF16 operands and FP32
+// accumulators in tensor memory.  Exact: |Q_ij| <= 100 and x in {0, 1} are
+// BF16 integers, every product is exact, and every partial sum is an integer
+// of magnitude <= 100 n < 2^24, which FP32 represents exactly whatever the
+// summation order.  (The int8 MMA kind is not available for sm_103a.)
+//
+// Tiles: 128 rows of Q (M) x BN replicas (N), K in chunks of 64 (128 bytes,
+// one 128-byte-swizzled row per operand row), STAGES-deep TMA pipeline.
+// Warp 0 lane 0 issues the TMA loads, warp 1 lane 0 issues the MMAs
+// (M = 128, N = BN, K = 16 per instruction, 4 per chunk) and commits each
+// stage back to the producer; after the last chunk all four warps read their
+// 32 accumulator lanes (rows) from tensor memory and add them, as exact
+// int32, into H (split-K CTAs over the same tile add into the same entries).
+// Every mbarrier wait is bounded: on timeout the kernel raises an error flag,
+// skips its output, releases its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace icd2s {
+
+namespace {
+
+constexpr int kBM = 128, kBK = 64;
+constexpr int kWaitLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait (iterations and about 2 s of wall time); false, with the error
+// flag raised, if the phase never completes
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err)
+{
+    const uint64_t t0 = global_ns();
+    for (int i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255) == 255 && global_ns() - t0 > 2000000000ull) break;
+    }
+    atomicExch(err, 1);
+    return false;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile stored with the
+// 128-byte swizzle (8-row groups of 1024 bytes): start address, stride
+// between 8-row groups (1024 B), descriptor version 1, layout "128B swizzle".
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);        // start address
+    d |= (uint64_t)1u << 16;                        // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;              // stride byte offset
+    d |= (uint64_t)1u << 46;                        // version
+    d |= (uint64_t)2u << 61;                        // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+}  // namespace
+
+template <int BN, int STAGES>
+__global__ __launch_bounds__(128, 1) void k_refresh_mma(const __grid_constant__ CUtensorMap tA,
+                                                       const __grid_constant__ CUtensorMap tB, int n, int R,
+                                                       int kc_total, int kc_per_split, int32_t* __restrict__ H,
+                                                       int ldh, int* err)
+{
+    constexpr uint32_t kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
+    constexpr uint32_t kIdesc = idesc_bf16_f32(kBM, BN);
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + STAGES * kABytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * kBBytes);  // full[S], empty[S], done
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int kc0 = blockIdx.z * kc_per_split;
+    const int kc1 = min(kc0 + kc_per_split, kc_total);
+    const int nk = kc1 > kc0 ? kc1 - kc0 : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0 && lane == 0 && nk > 0) {
+        // producer: TMA loads of A = Q[m0 .. m0+127][k] and B = X[n0 .. n0+BN-1][k]
+        int issued = 0;
+        for (int i = 0; i < nk && ok; ++i) {
+            const int s = i % STAGES, u = i / STAGES;
+            if (u > 0) ok = mbar_wait(empty0 + 8 * s, (uint32_t)((u - 1) & 1), err);
+            if (!ok) break;
+            const uint32_t fb = full0 + 8 * s;
+            mbar_expect_tx(fb, kABytes + kBBytes);
+            const int kx = (kc0 + i) * kBK;  // element column, a multiple of 64
+            tma_load_2d(smem_u32(sA + s * kABytes), &tA, kx, m0, fb);
+            tma_load_2d(smem_u32(sB + s * kBBytes), &tB, kx, n0, fb);
+            ++issued;
+        }
+        // every load this thread issued has landed before the CTA can leave
+        for (int i = issued - STAGES > 0 ? issued - STAGES : 0; i < issued; ++i)
+            mbar_wait(full0 + 8 * (i % STAGES), (uint32_t)((i / STAGES) & 1), err);
+    } else if (warp == 1 && lane == 0 && nk > 0) {
+        // MMA issuer
+        for (int i = 0; i < nk && ok; ++i) {
+            const int s = i % STAGES, u = i / STAGES;
+            ok = mbar_wait(full0 + 8 * s, (uint32_t)(u & 1), err);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a = smem_u32(sA + s * kABytes), b = smem_u32(sB + s * kBBytes);
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk)  // K = 16 per instruction: 32 bytes along the row
+                mma_bf16(tmem, smem_desc_sw128(a + 32 * kk), smem_desc_sw128(b + 32 * kk), kIdesc,
+                         (i > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
+        }
+        mma_commit(done);
+    }
+    __syncwarp();
+
+    // epilogue: warp w owns accumulator lanes (rows) 32 w .. 32 w + 31
+    if (nk > 0 && mbar_wait(done, 0u, err)) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int row = m0 + warp * 32 + lane;
+        const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 16) {
+            uint32_t v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(tw + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < n) {
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int p = n0 + c + t;
+                    if (p < R) {
+                        const int h = __float2int_rn(__uint_as_float(v[t]));
+                        if (h != 0) atomicAdd(H + (size_t)p * ldh + row, h);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+}
+
+// int8 Q [n][ld] -> bf16 [n][ld]; uint8 X [R][ld] -> bf16 [R][ld]
+__global__ void k_to_bf16_i8(const int8_t* __restrict__ src, size_t count, __nv_bfloat16_raw* __restrict__ dst)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        // integers in [-128, 127] are exact in bfloat16: the float's top 16 bits
+        const float f = (float)src[i];
+        __nv_bfloat16_raw r;
+        r.x = (unsigned short)(__float_as_uint(f) >> 16);
+        dst[i] = r;
+    }
+}
+
+__global__ void k_to_bf16_u8(const uint8_t* __restrict__ src, size_t count, __nv_bfloat16_raw* __restrict__ dst)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        __nv_bfloat16_raw r;
+        r.x = src[i] ? (unsigned short)0x3F80u : (unsigned short)0u;  // 1.0 or 0.0
+        dst[i] = r;
+    }
+}
+
+cudaError_t launch_to_bf16(const void* src, bool is_signed, size_t count, void* dst, cudaStream_t s)
+{
+    int blocks = (int)((count + 255) / 256);
+    if (blocks > device_sm_count() * 8) blocks = device_sm_count() * 8;
+    if (blocks < 1) blocks = 1;
+    if (is_signed)
+        k_to_bf16_i8<<<blocks, 256, 0, s>>>(static_cast<const int8_t*>(src), count,
+                                             static_cast<__nv_bfloat16_raw*>(dst));
+    else
+        k_to_bf16_u8<<<blocks, 256, 0, s>>>(static_cast<const uint8_t*>(src), count,
+                                             static_cast<__nv_bfloat16_raw*>(dst));
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder()
+{
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+// 2-D bf16 tensor [rows][ld] (ld elements per row), box = 64 columns x box_rows, 128-byte swizzle
+bool make_map(CUtensorMap* m, const void* base, int rows, int ld, int box_rows)
+{
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES>
+cudaError_t launch_mma(const CUtensorMap& tA, const CUtensorMap& tB, int n, int R, int ld, int splits, int32_t* H,
+                       int* err, cudaStream_t s)
+{
+    const size_t sm = 1024 + (size_t)STAGES * (kBM + BN) * kBK * 2 + (2 * STAGES + 1) * 8 + 16;
+    cudaError_t e = cudaFuncSetAttribute(k_refresh_mma<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    const int kc_total = ld / kBK;
+    const int kcps = (kc_total + splits - 1) / splits;
+    dim3 grid((n + kBM - 1) / kBM, (R + BN - 1) / BN, (kc_total + kcps - 1) / kcps);
+    k_refresh_mma<BN, STAGES><<<grid, 128, sm, s>>>(tA, tB, n, R, kc_total, kcps, H, ld, err);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// H[R][ld] (int32, zeroed here) = Q X^T on the tensor cores.  Qb: bf16 [n][ld];
+// Xb: bf16 [R][ld]; ld a multiple of 128.  err: device flag raised on a
+// timed-out wait.
+cudaError_t launch_refresh_mma(const void* Qb, const void* Xb, int n, int R, int ld, int32_t* H, int* err,
+                               cudaStream_t s)
+{
+    CUtensorMap tA, tB;
+    const int BN = R > 128 ? 256 : 128;
+    if (!make_map(&tA, Qb, n, ld, kBM) || !make_map(&tB, Xb, R, ld, BN)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(H, 0, sizeof(int32_t) * (size_t)R * ld, s);
+    if (e != cudaSuccess) return e;
+    const int tiles = ((n + kBM - 1) / kBM) * ((R + BN - 1) / BN);
+    const int kc_total = ld / kBK;
+    int splits = (device_sm_count() + tiles - 1) / tiles;  // about one CTA per SM
+    if (splits < 1) splits = 1;
+    if (splits > kc_total) splits = kc_total;
+    if (BN == 256) return launch_mma<256, 4>(tA, tB, n, R, ld, splits, H, err, s);
+    return launch_mma<128, 6>(tA, tB, n, R, ld, splits, H, err, s);
+}
+
+// Counts entries where two gain/energy sets differ (the drift check).
+__global__ void k_compare(const int32_t* __restrict__ G1, const int64_t* __restrict__ E1,
+                          const int32_t* __restrict__ G2, const int64_t* __restrict__ E2, int n, int ld, int R,
+                          int* mismatches)
+{
+    int bad = 0;
+    const size_t total = (size_t)R * ld;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+        if ((int)(i % ld) < n && G1[i] != G2[i]) ++bad;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < R; p += gridDim.x * blockDim.x)
+        if (E1[p] != E2[p]) ++bad;
+    bad = (int)__reduce_add_sync(0xffffffffu, (unsigned)bad);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(mismatches, bad);
+}
+
+cudaError_t launch_compare(const int32_t* G1, const int64_t* E1, const int32_t* G2, const int64_t* E2, int n, int ld,
+                           int R, int* mismatches, cudaStream_t s)
+{
+    int blocks = (int)(((size_t)R * ld + 255) / 256);
+    if (blocks > device_sm_count() * 8) blocks = device_sm_count() * 8;
+    k_compare<<<blocks, 256, 0, s>>>(G1, E1, G2, E2, n, ld, R, mismatches);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+}  // namespace icd2s

@@ -147,6 +147,14 @@ cudaError_t launch_recompute(const Dev& d, const uint8_t* X, int ldx, int R, int
     return cudaGetLastError();
 }
 
+cudaError_t launch_finish_gains(const int32_t* diag, int n, int ld, const uint8_t* X, int32_t* G, int64_t* E, int R,
+                                cudaStream_t s)
+{
+    k_finish_gains<<<R, 256, 0, s>>>(diag, n, ld, X, ld, G, E);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
 // dense [rows][n] -> padded [rows][ld] (zero padding)
 __global__ void k_pad_rows(const uint8_t* __restrict__ src, int n, int rows, uint8_t* __restrict__ dst, int ld)
 {

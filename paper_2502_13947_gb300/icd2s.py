@@ -31,7 +31,7 @@ EXPORTS = (
     "icd2s_get_control", "icd2s_anneal_subqubos_batch", "icd2s_apply_flips_update_gains", "icd2s_mutate",
     "icd2s_best_update", "icd2s_initial_pass", "icd2s_step", "icd2s_step_host", "icd2s_run", "icd2s_tables",
     "icd2s_set_timing", "icd2s_get_phase_ms", "icd2s_kernel_launches", "icd2s_apply_flips_static",
-    "icd2s_set_tuning", "icd2s_get_tuning", "icd2s_autotune",
+    "icd2s_set_tuning", "icd2s_get_tuning", "icd2s_autotune", "icd2s_refresh",
 )
 PHASES = ("tabu", "select", "anneal", "apply_anneal", "mutate", "apply_mutate", "best")
 
@@ -47,7 +47,8 @@ class Params(C.Structure):
         ("z", C.c_int32), ("K", C.c_int32), ("m_min", C.c_int32), ("m_max", C.c_int32), ("m_init", C.c_int32),
         ("alpha", C.c_int32), ("c", C.c_int32), ("sweeps", C.c_int32), ("T_max", C.c_double), ("T_min", C.c_double),
         ("w1", C.c_int64), ("w2", C.c_int64), ("w3", C.c_int64), ("mut_mode", C.c_int32), ("mut_rate", C.c_double),
-        ("patience", C.c_int32), ("max_iters", C.c_int32), ("use_graph", C.c_int32), ("reserved", C.c_int32 * 7),
+        ("patience", C.c_int32), ("max_iters", C.c_int32), ("use_graph", C.c_int32), ("refresh_every", C.c_int32),
+        ("reserved", C.c_int32 * 6),
     ]
 
 
@@ -118,6 +119,7 @@ def lib():
                 "icd2s_set_tuning": (C.c_int, [vp, vp]),
                 "icd2s_get_tuning": (C.c_int, [vp, vp]),
                 "icd2s_autotune": (C.c_int, [vp, P(Params), vp, vp]),
+                "icd2s_refresh": (C.c_int, [vp, i32, P(i32), vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -325,6 +327,14 @@ def icd2s_get_tuning(st) -> dict:
     t = Tuning()
     _check(lib().icd2s_get_tuning(st, C.byref(t)))
     return dict(tabu_variant=t.tabu_variant, anneal_warps_per_cta=t.anneal_warps_per_cta)
+
+
+def icd2s_refresh(st, rebuild: bool = False, stream=0) -> int:
+    """Tensor-core recompute of all gains/energies; returns the number of
+    entries that differ from the tracked ones (synchronises)."""
+    bad = C.c_int32(0)
+    _check(lib().icd2s_refresh(st, 1 if rebuild else 0, C.byref(bad), _s(stream)))
+    return int(bad.value)
 
 
 def icd2s_autotune(st, p: Params, stream=0) -> dict:
