@@ -165,6 +165,51 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- dense refresh
+REFRESH_WORKLOAD = dict(name="palubeckis-like-n7000-d1.0-R256", n=7000, density=1.0, qseed=7, z=256)
+
+
+def measure_refresh(I, torch, peaks, stream, flush, reps=10):
+    """The exact tensor-core refresh H = Q X^T on the dense n = 7000 instance
+    with 256 replicas: kernel time (CUDA events on the launching stream, L2
+    flushed before each call) against the measured BF16 peak."""
+    w = REFRESH_WORKLOAD
+    n, R = w["n"], w["z"]
+    Q = make_qubo(n, w["density"], w["qseed"])
+    q = I.icd2s_qubo_create(Q)
+    st = I.icd2s_state_create(q, R, 11)
+    sp = stream.cuda_stream
+    try:
+        I.icd2s_set_timing(st, True)
+        bad = I.icd2s_refresh(st, False, sp)          # warm-up (builds the BF16 copies)
+        mma, whole = [], []
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            bad += I.icd2s_refresh(st, False, sp)
+            with torch.cuda.stream(stream):
+                e1.record(stream)
+            e1.synchronize()
+            whole.append(e0.elapsed_time(e1))
+            mma.append(I.icd2s_get_refresh_ms(st))
+    finally:
+        I.icd2s_state_destroy(st)
+        I.icd2s_qubo_destroy(q)
+    ms = sum(mma) / len(mma)
+    flops = 2.0 * n * n * R
+    tf = flops / (ms / 1000.0) / 1e12
+    ld = (n + 127) // 128 * 128
+    return {"kernel": "k_refresh_mma", "workload": w["name"], "bound": "tensor", "achieved": tf,
+            "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": tf / peaks["bf16_tflops"],
+            "traffic": ncu_traffic("kernels_refresh.cu", "k_refresh_mma"),
+            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": 2 * n * ld + 2 * R * ld + 4 * R * ld,
+            "launch_ms": ms, "refresh_call_ms": sum(whole) / len(whole), "mismatches": bad,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst: the kernel is timed alone)"}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_gpu(args, w):
     import torch
@@ -273,6 +318,7 @@ def run_gpu(args, w):
         return
 
     peaks, peak_src = measured_peaks()
+    refresh = None if args.no_refresh else measure_refresh(I, torch, peaks, stream, flush)
     K = args.steps
     phase_avg = {k: v / K for k, v in phase_tot.items()}
     ld = (n + 127) // 128 * 128
@@ -304,6 +350,7 @@ def run_gpu(args, w):
                    "attempts_per_step": att, "parallelism": "independent instance per GPU" if world > 1 else "1 GPU",
                    "l2": "flushed before every timed step (256 MiB write outside the step events)"},
         "roofline": roofline,
+        "roofline_refresh": refresh,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": z * n, "d2h_bytes_per_step": z * n + 8 * z,
                 "steps": e2e_steps, "api": "icd2s_step_host"},
@@ -325,6 +372,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-refresh", action="store_true", help="skip the dense tensor-core refresh measurement")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":

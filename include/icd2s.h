@@ -242,6 +242,9 @@ int icd2s_run(icd2s_qubo* q, const icd2s_params* p, uint64_t seed, uint8_t* x_ou
 #define ICD2S_PHASES 7
 int icd2s_set_timing(icd2s_state* st, int32_t enable);
 int icd2s_get_phase_ms(icd2s_state* st, double* ms);
+/* With timing enabled: duration (ms) of the tensor-core kernel of the last
+ * icd2s_refresh. */
+int icd2s_get_refresh_ms(icd2s_state* st, double* ms);
 
 /* Kernel variants used by a state (launch configuration only: every variant
  * computes the same results bit for bit).  tabu_variant indexes the Tabu
@@ -251,7 +254,9 @@ int icd2s_get_phase_ms(icd2s_state* st, double* ms);
 typedef struct icd2s_tuning {
     int32_t tabu_variant;
     int32_t anneal_warps_per_cta;
-    int32_t reserved[6];
+    int32_t refresh_bn;       /* tensor-core refresh: replicas per tile (128 or 256; 0 = default) */
+    int32_t refresh_splits;   /* tensor-core refresh: K splits (0 = about one CTA per SM) */
+    int32_t reserved[4];
 } icd2s_tuning;
 int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t);
 int icd2s_get_tuning(icd2s_state* st, icd2s_tuning* t);

@@ -125,7 +125,7 @@ struct icd2s_state {
     int* limtab = nullptr;  // [beta_cap][4096] acceptance limits of the schedule
     int beta_sweeps = -1; double beta_tmax = 0, beta_tmin = 0;
     bool have_select = false; int sel_K = 0;
-    icd2s_tuning tune{-1, 0, {0}};  // kernel variants (see icd2s_set_tuning)
+    icd2s_tuning tune{-1, 0, 0, 0, {0}};  // kernel variants (see icd2s_set_tuning)
     // persistent anneal queue (uneven subQUBOs) and the iteration context of a captured step
     int32_t* lpt = nullptr;      // [R * 64] subQUBOs in largest-first order
     int32_t* queue = nullptr;    // [1] queue counter
@@ -140,6 +140,8 @@ struct icd2s_state {
     cudaEvent_t join_ev = nullptr;
     // dense refresh buffers (made on first use)
     void* Xb = nullptr; int32_t* G2 = nullptr; int64_t* E2 = nullptr; int* rflags = nullptr;  // [0] timeout, [1] mismatches
+    cudaEvent_t rev[2] = {};  // around the tensor-core kernel of the last refresh (when timing)
+    bool timed_refresh = false;
     // phase timing of icd2s_step: events [2 * phase] / [2 * phase + 1]
     bool timing = false, timed_step = false;
     cudaEvent_t ev[2 * ICD2S_PHASES] = {};
@@ -163,6 +165,8 @@ static void free_state(icd2s_state* st)
     if (st->own_stream) cudaStreamDestroy(st->own_stream);
     if (st->join_ev) cudaEventDestroy(st->join_ev);
     for (cudaEvent_t e : st->ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : st->rev)
         if (e) cudaEventDestroy(e);
     delete st;
 }
@@ -598,7 +602,16 @@ int icd2s_refresh(icd2s_state* st, int32_t rebuild, int32_t* mismatches, void* s
     }
     CK(cudaMemsetAsync(st->rflags, 0, 16, s));
     CK(launch_to_bf16(st->X, false, RL, st->Xb, s));
-    CK(launch_refresh_mma(q->Qb, st->Xb, n, R, ld, st->G2, st->rflags, s));   // H into G2
+    if (st->timing) {
+        if (!st->rev[0]) for (cudaEvent_t& e : st->rev) CK(cudaEventCreate(&e));
+        CK(cudaEventRecord(st->rev[0], s));
+    }
+    CK(launch_refresh_mma(q->Qb, st->Xb, n, R, ld, st->G2, st->rflags, st->tune.refresh_bn,
+                          st->tune.refresh_splits, s));                        // H into G2
+    if (st->timing) {
+        CK(cudaEventRecord(st->rev[1], s));
+        st->timed_refresh = true;
+    }
     CK(launch_finish_gains(q->diag, n, ld, st->X, st->G2, st->E2, R, s));     // H -> g, E
     CK(launch_compare(st->G, st->E, st->G2, st->E2, n, ld, R, st->rflags + 1, s));
     if (rebuild) {
@@ -749,11 +762,26 @@ int icd2s_get_phase_ms(icd2s_state* st, double* ms)
     return ICD2S_OK;
 }
 
+int icd2s_get_refresh_ms(icd2s_state* st, double* ms)
+{
+    REQ(st && ms, ICD2S_ERR_ARG, "NULL argument");
+    REQ(st->timed_refresh, ICD2S_ERR_STATE, "no timed refresh: enable icd2s_set_timing, then run icd2s_refresh");
+    CK(cudaEventSynchronize(st->rev[1]));
+    float f = 0.f;
+    CK(cudaEventElapsedTime(&f, st->rev[0], st->rev[1]));
+    *ms = f;
+    return ICD2S_OK;
+}
+
 int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t)
 {
     REQ(st && t, ICD2S_ERR_ARG, "NULL argument");
     REQ(t->tabu_variant < 0 || tabu_variant_fits(t->tabu_variant, st->q->n), ICD2S_ERR_ARG,
         "Tabu variant %d does not cover n=%d", t->tabu_variant, st->q->n);
+    REQ(t->refresh_bn == 0 || t->refresh_bn == 128 || t->refresh_bn == 256, ICD2S_ERR_ARG,
+        "refresh_bn=%d must be 0, 128 or 256", t->refresh_bn);
+    REQ(t->refresh_splits >= 0 && t->refresh_splits <= 256, ICD2S_ERR_ARG, "refresh_splits=%d outside 0..256",
+        t->refresh_splits);
     REQ(t->anneal_warps_per_cta >= 0 && t->anneal_warps_per_cta <= 4, ICD2S_ERR_ARG,
         "anneal_warps_per_cta=%d outside 0..4", t->anneal_warps_per_cta);
     st->tune = *t;

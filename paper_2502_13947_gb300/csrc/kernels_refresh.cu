@@ -328,18 +328,19 @@ cudaError_t launch_mma(const CUtensorMap& tA, const CUtensorMap& tB, int n, int 
 
 // H[R][ld] (int32, zeroed here) = Q X^T on the tensor cores.  Qb: bf16 [n][ld];
 // Xb: bf16 [R][ld]; ld a multiple of 128.  err: device flag raised on a
-// timed-out wait.
-cudaError_t launch_refresh_mma(const void* Qb, const void* Xb, int n, int R, int ld, int32_t* H, int* err,
-                               cudaStream_t s)
+// timed-out wait.  bn: replicas per tile (128 / 256; 0 picks by R);
+// splits: K splits (0: as many as keep every tile's CTAs in one wave).
+cudaError_t launch_refresh_mma(const void* Qb, const void* Xb, int n, int R, int ld, int32_t* H, int* err, int bn,
+                               int splits, cudaStream_t s)
 {
     CUtensorMap tA, tB;
-    const int BN = R > 128 ? 256 : 128;
+    const int BN = bn == 128 || bn == 256 ? bn : (R > 128 ? 256 : 128);
     if (!make_map(&tA, Qb, n, ld, kBM) || !make_map(&tB, Xb, R, ld, BN)) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(H, 0, sizeof(int32_t) * (size_t)R * ld, s);
     if (e != cudaSuccess) return e;
     const int tiles = ((n + kBM - 1) / kBM) * ((R + BN - 1) / BN);
     const int kc_total = ld / kBK;
-    int splits = (device_sm_count() + tiles - 1) / tiles;  // about one CTA per SM
+    if (splits <= 0) splits = device_sm_count() / tiles;  // one CTA per SM, a single wave
     if (splits < 1) splits = 1;
     if (splits > kc_total) splits = kc_total;
     if (BN == 256) return launch_mma<256, 4>(tA, tB, n, R, ld, splits, H, err, s);

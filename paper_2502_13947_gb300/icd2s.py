@@ -31,7 +31,7 @@ EXPORTS = (
     "icd2s_get_control", "icd2s_anneal_subqubos_batch", "icd2s_apply_flips_update_gains", "icd2s_mutate",
     "icd2s_best_update", "icd2s_initial_pass", "icd2s_step", "icd2s_step_host", "icd2s_run", "icd2s_tables",
     "icd2s_set_timing", "icd2s_get_phase_ms", "icd2s_kernel_launches", "icd2s_apply_flips_static",
-    "icd2s_set_tuning", "icd2s_get_tuning", "icd2s_autotune", "icd2s_refresh",
+    "icd2s_set_tuning", "icd2s_get_tuning", "icd2s_autotune", "icd2s_refresh", "icd2s_get_refresh_ms",
 )
 PHASES = ("tabu", "select", "anneal", "apply_anneal", "mutate", "apply_mutate", "best")
 
@@ -120,6 +120,7 @@ def lib():
                 "icd2s_get_tuning": (C.c_int, [vp, vp]),
                 "icd2s_autotune": (C.c_int, [vp, P(Params), vp, vp]),
                 "icd2s_refresh": (C.c_int, [vp, i32, P(i32), vp]),
+                "icd2s_get_refresh_ms": (C.c_int, [vp, P(f64)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -315,18 +316,26 @@ def icd2s_apply_flips_static(Q_dev: int, n: int, ld: int, replicas: int, flips_d
 
 
 class Tuning(C.Structure):
-    _fields_ = [("tabu_variant", C.c_int32), ("anneal_warps_per_cta", C.c_int32), ("reserved", C.c_int32 * 6)]
+    _fields_ = [("tabu_variant", C.c_int32), ("anneal_warps_per_cta", C.c_int32), ("refresh_bn", C.c_int32),
+                ("refresh_splits", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
-def icd2s_set_tuning(st, tabu_variant: int = -1, anneal_warps_per_cta: int = 0) -> None:
-    t = Tuning(tabu_variant=tabu_variant, anneal_warps_per_cta=anneal_warps_per_cta)
+def _tuning_dict(t):
+    return dict(tabu_variant=t.tabu_variant, anneal_warps_per_cta=t.anneal_warps_per_cta,
+                refresh_bn=t.refresh_bn, refresh_splits=t.refresh_splits)
+
+
+def icd2s_set_tuning(st, tabu_variant: int = -1, anneal_warps_per_cta: int = 0, refresh_bn: int = 0,
+                     refresh_splits: int = 0) -> None:
+    t = Tuning(tabu_variant=tabu_variant, anneal_warps_per_cta=anneal_warps_per_cta, refresh_bn=refresh_bn,
+               refresh_splits=refresh_splits)
     _check(lib().icd2s_set_tuning(st, C.byref(t)))
 
 
 def icd2s_get_tuning(st) -> dict:
     t = Tuning()
     _check(lib().icd2s_get_tuning(st, C.byref(t)))
-    return dict(tabu_variant=t.tabu_variant, anneal_warps_per_cta=t.anneal_warps_per_cta)
+    return _tuning_dict(t)
 
 
 def icd2s_refresh(st, rebuild: bool = False, stream=0) -> int:
@@ -337,7 +346,13 @@ def icd2s_refresh(st, rebuild: bool = False, stream=0) -> int:
     return int(bad.value)
 
 
+def icd2s_get_refresh_ms(st) -> float:
+    ms = C.c_double(0.0)
+    _check(lib().icd2s_get_refresh_ms(st, C.byref(ms)))
+    return float(ms.value)
+
+
 def icd2s_autotune(st, p: Params, stream=0) -> dict:
     t = Tuning()
     _check(lib().icd2s_autotune(st, C.byref(p), C.byref(t), _s(stream)))
-    return dict(tabu_variant=t.tabu_variant, anneal_warps_per_cta=t.anneal_warps_per_cta)
+    return _tuning_dict(t)
