@@ -492,16 +492,18 @@ static void orc_best_update(const uint8_t* S, const int64_t* E, int32_t z, int32
  * (Algorithm 4) and the mutation with rate r_t (Eq. 5) or a constant rate.
  * E[z] receives the energies after the iteration; trace3[3 z] (optional) the
  * energies after the Tabu search, the Ising-machine step and the mutation;
- * the best solution is folded in after each of the three phases.  T_out and
- * A_out (optional, z * n) receive the toggle counts and A.  Returns 1 if the
- * best energy improved. */
+ * the best solution is folded in after each of the three phases.  T_out,
+ * A_out and C_out (optional, z * n) receive the toggle counts, A and the
+ * tabu memory at the end of each search; H_io (optional, z * n) counts, per
+ * solution and variable, the Ising-machine calls that included it (each
+ * selection adds 1).  Returns 1 if the best energy improved. */
 int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t seed, int32_t t,
                  const int32_t* eta_hat, uint8_t* S, int64_t* E, int64_t* trace3, int64_t* best_E,
-                 uint8_t* best_x, int32_t* T_out, int32_t* A_out)
+                 uint8_t* best_x, int32_t* T_out, int32_t* A_out, int32_t* C_out, int32_t* H_io)
 {
     const int32_t z = prm->z, K = prm->K;
     int32_t* T = (int32_t*)malloc(sizeof(int32_t) * (size_t)z * n);
-    int32_t* C = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t* C = (int32_t*)malloc(sizeof(int32_t) * (size_t)z * n);
     int32_t* A = (int32_t*)malloc(sizeof(int32_t) * (size_t)z * n);
     int32_t* gam = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
     int32_t* del = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
@@ -520,7 +522,7 @@ int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t see
 
     /* Tabu search on every solution (Algorithm 1) */
     for (int32_t p = 0; p < z; ++p)
-        E[p] = orc_tabu(Q, n, S + (int64_t)p * n, prm->alpha, prm->c, T + (int64_t)p * n, C);
+        E[p] = orc_tabu(Q, n, S + (int64_t)p * n, prm->alpha, prm->c, T + (int64_t)p * n, C + (int64_t)p * n);
     orc_best_update(S, E, z, n, best_E, best_x, &improved);
     if (trace3) memcpy(trace3, E, sizeof(int64_t) * (size_t)z);
     /* Deviation_Extraction (Eq. 8), Control_Parameters_Aggregation (Algorithm 3) */
@@ -549,6 +551,7 @@ int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t see
             for (int32_t a = 0; a < m; ++a) {
                 x[idx[off + a]] = xs[a];
                 in_sel[(int64_t)p * n + idx[off + a]] = 1;
+                if (H_io) H_io[(int64_t)p * n + idx[off + a]] += 1;
             }
             off += m;
             msel[p] += m;
@@ -569,6 +572,7 @@ int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t see
     if (trace3) memcpy(trace3 + 2 * z, E, sizeof(int64_t) * (size_t)z);
     if (T_out) memcpy(T_out, T, sizeof(int32_t) * (size_t)z * n);
     if (A_out) memcpy(A_out, A, sizeof(int32_t) * (size_t)z * n);
+    if (C_out) memcpy(C_out, C, sizeof(int32_t) * (size_t)z * n);
     free(T); free(C); free(A); free(gam); free(del); free(Qs); free(xs); free(sizes); free(idx);
     free(S_pre); free(in_sel); free(msel); free(beta);
     return improved;
@@ -630,7 +634,7 @@ int32_t orc_run(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t seed
     int32_t t = 0, stale = 0;
     while (t < prm->max_iters && (prm->patience <= 0 || stale < prm->patience)) {
         int64_t* tr = trace ? trace + (int64_t)t * (3 * z + 1) : NULL;
-        improved = orc_step(Q, n, prm, seed, t, eta_hat, S, E, tr, &best_E, best_x, NULL, NULL);
+        improved = orc_step(Q, n, prm, seed, t, eta_hat, S, E, tr, &best_E, best_x, NULL, NULL, NULL, NULL);
         if (tr) tr[3 * z] = best_E;
         /* MRAnnealer.NextRate is r_{t+1}; termination rule (Section 3, end) */
         stale = improved ? 0 : stale + 1;

@@ -89,7 +89,7 @@ def lib():
                 "orc_anneal": (i64, [vp, i32, vp, i32, vp, vp, u64, u32, u32, vp]),
                 "orc_mutate": (i32, [vp, i32, vp, i32, u64, u32, u32, vp]),
                 "orc_run": (i32, [vp, i32, C.POINTER(Params), u64, vp, vp, vp, vp, C.POINTER(Result)]),
-                "orc_step": (i32, [vp, i32, C.POINTER(Params), u64, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
+                "orc_step": (i32, [vp, i32, C.POINTER(Params), u64, i32] + [vp] * 10),
                 "orc_initial_pass": (None, [vp, i32, C.POINTER(Params), u64, vp, vp]),
             }
             for name, (res, args) in sig.items():
@@ -305,9 +305,12 @@ def run(Q, prm: Params, seed: int, trace: bool = True):
                 init_best_E=int(res.init_best_E), iters=int(it))
 
 
-def step(Q, prm: Params, seed: int, t: int, S, best_E=None, best_x=None):
+def step(Q, prm: Params, seed: int, t: int, S, best_E=None, best_x=None, H=None):
     """One outer iteration of Algorithm 2 from the solution set S (not
-    modified).  Returns dict(S, E, trace3, best_E, best_x, T, A, improved)."""
+    modified).  Returns dict(S, E, trace3, best_E, best_x, T, A, C, H,
+    improved): T/C the Tabu toggle counts and final tabu memory of each
+    replica, H the per-replica selection hit counts (H input + 1 for every
+    variable placed in a subQUBO this iteration)."""
     Q, n = _q(Q)
     S = _u8(S).copy()
     z = prm.z
@@ -319,9 +322,12 @@ def step(Q, prm: Params, seed: int, t: int, S, best_E=None, best_x=None):
     bx = np.zeros(n, np.uint8) if best_x is None else _u8(best_x).copy()
     T = np.zeros((z, n), np.int32)
     A = np.zeros((z, n), np.int32)
+    Cm = np.zeros((z, n), np.int32)
+    Hm = np.zeros((z, n), np.int32) if H is None else np.ascontiguousarray(H, np.int32).copy()
+    assert Hm.shape == (z, n)
     imp = lib().orc_step(_p(Q), n, C.byref(prm), seed, t, _p(eh), _p(S), _p(E), _p(tr), _p(bE), _p(bx),
-                         _p(T), _p(A))
-    return dict(S=S, E=E, trace3=tr, best_E=int(bE[0]), best_x=bx, T=T, A=A, improved=int(imp))
+                         _p(T), _p(A), _p(Cm), _p(Hm))
+    return dict(S=S, E=E, trace3=tr, best_E=int(bE[0]), best_x=bx, T=T, A=A, C=Cm, H=Hm, improved=int(imp))
 
 
 def initial_pass(Q, prm: Params, seed: int, S):
