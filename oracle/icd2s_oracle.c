@@ -467,7 +467,88 @@ typedef struct {
     double mut_rate;
     int32_t patience;   /* stop after this many iterations without a new best (<= 0: off) */
     int32_t max_iters;
+    int32_t select_mode; /* 0: rank by A (Algorithm 4); 1: rank by the learned score;
+                            2: learned on even solutions, A on odd ones */
 } orc_params;
+
+/* ------------------------------------------------------------------------ */
+/* Learned selection (the added proposal network; readings S21, S22).        */
+/* ------------------------------------------------------------------------ */
+
+/* Per-variable features of one solution at selection time, as floats:
+ *   f0 = x_i, f1 = g_i / (max_j |g_j| + 1), f2 = T_i / alpha, f3 = C_i / c,
+ *   f4 = H_i / (t + 1), f5 = eta_hat_i / 2^16,
+ * with g the 1-flip gains, T and C the toggle counts and tabu memory of the
+ * last Tabu search, H the number of earlier Ising-machine calls that included
+ * the variable and t the outer iteration.  Every quotient is of two integers
+ * below 2^24 (exact in float); it is formed in double and rounded once to
+ * float, which gives the correctly rounded float quotient because double
+ * has more than 2 * 24 + 2 significand bits.  alpha = 0 gives f2 = 0. */
+void orc_features(int32_t n, const uint8_t* x, const int32_t* g, const int32_t* T, const int32_t* C,
+                  const int32_t* H, const int32_t* eta_hat, int32_t t, int32_t alpha, int32_t c, float* F)
+{
+    int64_t gmax = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int64_t a = g[i] < 0 ? -(int64_t)g[i] : g[i];
+        if (a > gmax) gmax = a;
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        float* f = F + (int64_t)i * 6;
+        f[0] = (float)x[i];
+        f[1] = (float)((double)g[i] / (double)(gmax + 1));
+        f[2] = alpha > 0 ? (float)((double)T[i] / (double)alpha) : 0.0f;
+        f[3] = (float)((double)C[i] / (double)c);
+        f[4] = (float)((double)H[i] / (double)(t + 1));
+        f[5] = (float)((double)eta_hat[i] / 65536.0);
+    }
+}
+
+/* Parameter layout of the 6-64-64-1 network (4673 values): W1[64][6], b1[64],
+ * W2[64][64], b2[64], w3[64], b3.  Row o of W1/W2 holds the weights into
+ * hidden unit o. */
+#define ORC_W1 0
+#define ORC_B1 384
+#define ORC_W2 448
+#define ORC_B2 4544
+#define ORC_W3 4608
+#define ORC_B3 4672
+#define ORC_NPAR 4673
+
+/* Score of one feature row in float arithmetic, the precision in which the
+ * selection decision is taken: ReLU hidden layers, every product added by
+ * one fused multiply-add (fmaf), units and inputs in increasing order:
+ *   a1_o = b1_o (+ W1_o0 f_0) ... (+ W1_o5 f_5),        h1_o = max(a1_o, 0)
+ *   a2_o = b2_o (+ W2_o0 h1_0) ... (+ W2_o63 h1_63),    h2_o = max(a2_o, 0)
+ *   s    = b3 (+ w3_0 h2_0) ... (+ w3_63 h2_63).
+ * W holds BF16 values widened to float. */
+float orc_mlp_score_f32(const float* W, const float* f)
+{
+    float h1[64];
+    for (int o = 0; o < 64; ++o) {
+        float a = W[ORC_B1 + o];
+        for (int k = 0; k < 6; ++k) a = fmaf(W[ORC_W1 + o * 6 + k], f[k], a);
+        h1[o] = a > 0.0f ? a : 0.0f;
+    }
+    float s = W[ORC_B3];
+    for (int o = 0; o < 64; ++o) {
+        float a = W[ORC_B2 + o];
+        for (int k = 0; k < 64; ++k) a = fmaf(W[ORC_W2 + o * 64 + k], h1[k], a);
+        float h2 = a > 0.0f ? a : 0.0f;
+        s = fmaf(W[ORC_W3 + o], h2, s);
+    }
+    return s;
+}
+
+/* A signed integer with the order of the float s (a total order on the bit
+ * patterns: -0 ranks just below +0), so that ranking by (score desc, index
+ * asc) is the same integer ranking as for A. */
+int32_t orc_score_key(float s)
+{
+    uint32_t b;
+    memcpy(&b, &s, 4);
+    if (b < 0x80000000u) return (int32_t)b;
+    return -(int32_t)(b & 0x7FFFFFFFu) - 1;
+}
 
 typedef struct {
     int32_t iters;            /* outer iterations run */
@@ -476,13 +557,14 @@ typedef struct {
 } orc_result;
 
 static void orc_best_update(const uint8_t* S, const int64_t* E, int32_t z, int32_t n,
-                            int64_t* best_E, uint8_t* best_x, int* improved)
+                            int64_t* best_E, uint8_t* best_x, int* improved, int32_t* winner)
 {
     for (int32_t p = 0; p < z; ++p)
         if (E[p] < *best_E) {
             *best_E = E[p];
             memcpy(best_x, S + (int64_t)p * n, (size_t)n);
             *improved = 1;
+            if (winner) *winner = p;
         }
 }
 
@@ -496,12 +578,24 @@ static void orc_best_update(const uint8_t* S, const int64_t* E, int32_t z, int32
  * A_out and C_out (optional, z * n) receive the toggle counts, A and the
  * tabu memory at the end of each search; H_io (optional, z * n) counts, per
  * solution and variable, the Ising-machine calls that included it (each
- * selection adds 1).  Returns 1 if the best energy improved. */
+ * selection adds 1).
+ * Learned selection (select_mode 1, or 2 on even solutions): the subset S' is
+ * ranked by (score desc, index asc) instead of (A desc, index asc), the score
+ * being orc_mlp_score_f32 with the network W of the features at selection
+ * time (after the Tabu search; H before this iteration's increments); A still
+ * ranks the mutation candidates.  H_io is required in that mode.  F_out
+ * (z * n * 6) and score_out (z * n, needs W) receive the features and scores
+ * of every solution at selection time; *winner (optional) the solution whose
+ * row was last copied into best_x in this iteration (-1 if none).
+ * Returns 1 if the best energy improved. */
 int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t seed, int32_t t,
                  const int32_t* eta_hat, uint8_t* S, int64_t* E, int64_t* trace3, int64_t* best_E,
-                 uint8_t* best_x, int32_t* T_out, int32_t* A_out, int32_t* C_out, int32_t* H_io)
+                 uint8_t* best_x, int32_t* T_out, int32_t* A_out, int32_t* C_out, int32_t* H_io,
+                 const float* W, float* F_out, float* score_out, int32_t* winner)
 {
     const int32_t z = prm->z, K = prm->K;
+    if (winner) *winner = -1;
+    if (prm->select_mode != 0 && (W == NULL || H_io == NULL)) return -1;
     int32_t* T = (int32_t*)malloc(sizeof(int32_t) * (size_t)z * n);
     int32_t* C = (int32_t*)malloc(sizeof(int32_t) * (size_t)z * n);
     int32_t* A = (int32_t*)malloc(sizeof(int32_t) * (size_t)z * n);
@@ -516,6 +610,9 @@ int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t see
     int32_t* msel = (int32_t*)malloc(sizeof(int32_t) * (size_t)z);
     uint32_t* beta = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(prm->sweeps > 0 ? prm->sweeps : 1));
     uint32_t nlog[4096];
+    int32_t* g = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    float* F = (float*)malloc(sizeof(float) * (size_t)n * 6);
+    int32_t* skey = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
     int improved = 0;
     orc_beta_table(prm->sweeps, prm->T_max, prm->T_min, beta);
     orc_nlog_table(nlog);
@@ -523,7 +620,7 @@ int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t see
     /* Tabu search on every solution (Algorithm 1) */
     for (int32_t p = 0; p < z; ++p)
         E[p] = orc_tabu(Q, n, S + (int64_t)p * n, prm->alpha, prm->c, T + (int64_t)p * n, C + (int64_t)p * n);
-    orc_best_update(S, E, z, n, best_E, best_x, &improved);
+    orc_best_update(S, E, z, n, best_E, best_x, &improved, winner);
     if (trace3) memcpy(trace3, E, sizeof(int64_t) * (size_t)z);
     /* Deviation_Extraction (Eq. 8), Control_Parameters_Aggregation (Algorithm 3) */
     orc_gamma(S, z, n, gam);
@@ -536,7 +633,23 @@ int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t see
         uint8_t* x = S + (int64_t)p * n;
         const int32_t* Ap = A + (int64_t)p * n;
         orc_subqubo_sizes(K, prm->m_min, prm->m_max, seed, (uint32_t)p, (uint32_t)t, sizes);
-        orc_select(Ap, n, sizes, K, idx);
+        const int learned = prm->select_mode == 1 || (prm->select_mode == 2 && p % 2 == 0);
+        if (learned || F_out || score_out) {
+            orc_gains(Q, n, x, g);
+            int32_t* Hp = H_io ? H_io + (int64_t)p * n : NULL;
+            if (!Hp) { Hp = skey; memset(Hp, 0, sizeof(int32_t) * (size_t)n); }
+            orc_features(n, x, g, T + (int64_t)p * n, C + (int64_t)p * n, Hp, eta_hat, t, prm->alpha,
+                         prm->c, F);
+            if (F_out) memcpy(F_out + (int64_t)p * n * 6, F, sizeof(float) * (size_t)n * 6);
+        }
+        if (learned || (score_out && W)) {
+            for (int32_t i = 0; i < n; ++i) {
+                float s = orc_mlp_score_f32(W, F + (int64_t)i * 6);
+                if (score_out) score_out[(int64_t)p * n + i] = s;
+                skey[i] = orc_score_key(s);
+            }
+        }
+        orc_select(learned ? skey : Ap, n, sizes, K, idx);
         memcpy(S_pre, x, (size_t)n);
         memset(in_sel + (int64_t)p * n, 0, (size_t)n);
         int32_t off = 0;
@@ -558,7 +671,7 @@ int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t see
         }
         E[p] = orc_energy(Q, n, x);
     }
-    orc_best_update(S, E, z, n, best_E, best_x, &improved);
+    orc_best_update(S, E, z, n, best_E, best_x, &improved, winner);
     if (trace3) memcpy(trace3 + z, E, sizeof(int64_t) * (size_t)z);
     /* Mutation with the MRAnnealer rate (Eq. 5) */
     double r = prm->mut_mode == 0 ? orc_mutation_rate(t) : prm->mut_rate;
@@ -568,13 +681,14 @@ int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t see
         orc_mutate(A + (int64_t)p * n, n, in_sel + (int64_t)p * n, L, seed, (uint32_t)p, (uint32_t)t, x);
         E[p] = orc_energy(Q, n, x);
     }
-    orc_best_update(S, E, z, n, best_E, best_x, &improved);
+    orc_best_update(S, E, z, n, best_E, best_x, &improved, winner);
     if (trace3) memcpy(trace3 + 2 * z, E, sizeof(int64_t) * (size_t)z);
     if (T_out) memcpy(T_out, T, sizeof(int32_t) * (size_t)z * n);
     if (A_out) memcpy(A_out, A, sizeof(int32_t) * (size_t)z * n);
     if (C_out) memcpy(C_out, C, sizeof(int32_t) * (size_t)z * n);
     free(T); free(C); free(A); free(gam); free(del); free(Qs); free(xs); free(sizes); free(idx);
     free(S_pre); free(in_sel); free(msel); free(beta);
+    free(g); free(F); free(skey);
     return improved;
 }
 
@@ -610,12 +724,14 @@ void orc_initial_pass(const int8_t* Q, int32_t n, const orc_params* prm, uint64_
  * S_out[z][n] (final solutions), trace[max_iters][3 z + 1] (int64,
  * optional): per iteration the energies of all solutions after the Tabu
  * search, after the IM step, after the mutation, then the best energy;
- * init_E[z] (optional): energies after Call_IM_Solution_Set. */
+ * init_E[z] (optional): energies after Call_IM_Solution_Set.  Plain
+ * selection only (select_mode 0; otherwise returns -1). */
 int32_t orc_run(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t seed,
                 uint8_t* best_x, uint8_t* S_out, int64_t* trace, int64_t* init_E,
                 orc_result* res)
 {
     const int32_t z = prm->z;
+    if (prm->select_mode != 0) return -1;
     uint8_t* S = (uint8_t*)malloc((size_t)z * n);
     int64_t* E = (int64_t*)malloc(sizeof(int64_t) * (size_t)z);
     int64_t* eta = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
@@ -625,7 +741,7 @@ int32_t orc_run(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t seed
 
     orc_init_solutions(n, z, seed, S);                 /* Generate_Initial_Solution_Set */
     orc_initial_pass(Q, n, prm, seed, S, E);           /* Call_IM_Solution_Set */
-    orc_best_update(S, E, z, n, &best_E, best_x, &improved);
+    orc_best_update(S, E, z, n, &best_E, best_x, &improved, NULL);
     if (init_E) memcpy(init_E, E, sizeof(int64_t) * (size_t)z);
     if (res) res->init_best_E = best_E;
     orc_eta(Q, n, eta);                                /* Weight_Effect_Extraction (Eq. 6) */
@@ -634,7 +750,8 @@ int32_t orc_run(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t seed
     int32_t t = 0, stale = 0;
     while (t < prm->max_iters && (prm->patience <= 0 || stale < prm->patience)) {
         int64_t* tr = trace ? trace + (int64_t)t * (3 * z + 1) : NULL;
-        improved = orc_step(Q, n, prm, seed, t, eta_hat, S, E, tr, &best_E, best_x, NULL, NULL, NULL, NULL);
+        improved = orc_step(Q, n, prm, seed, t, eta_hat, S, E, tr, &best_E, best_x, NULL, NULL, NULL, NULL,
+                            NULL, NULL, NULL, NULL);
         if (tr) tr[3 * z] = best_E;
         /* MRAnnealer.NextRate is r_{t+1}; termination rule (Section 3, end) */
         stale = improved ? 0 : stale + 1;

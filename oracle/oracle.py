@@ -47,7 +47,7 @@ class Params(C.Structure):
         ("T_max", C.c_double), ("T_min", C.c_double),
         ("w1", C.c_int64), ("w2", C.c_int64), ("w3", C.c_int64),
         ("mut_mode", C.c_int32), ("mut_rate", C.c_double),
-        ("patience", C.c_int32), ("max_iters", C.c_int32),
+        ("patience", C.c_int32), ("max_iters", C.c_int32), ("select_mode", C.c_int32),
     ]
 
 
@@ -89,7 +89,10 @@ def lib():
                 "orc_anneal": (i64, [vp, i32, vp, i32, vp, vp, u64, u32, u32, vp]),
                 "orc_mutate": (i32, [vp, i32, vp, i32, u64, u32, u32, vp]),
                 "orc_run": (i32, [vp, i32, C.POINTER(Params), u64, vp, vp, vp, vp, C.POINTER(Result)]),
-                "orc_step": (i32, [vp, i32, C.POINTER(Params), u64, i32] + [vp] * 10),
+                "orc_step": (i32, [vp, i32, C.POINTER(Params), u64, i32] + [vp] * 14),
+                "orc_features": (None, [i32, vp, vp, vp, vp, vp, vp, i32, i32, i32, vp]),
+                "orc_mlp_score_f32": (C.c_float, [vp, vp]),
+                "orc_score_key": (i32, [C.c_float]),
                 "orc_initial_pass": (None, [vp, i32, C.POINTER(Params), u64, vp, vp]),
             }
             for name, (res, args) in sig.items():
@@ -305,12 +308,16 @@ def run(Q, prm: Params, seed: int, trace: bool = True):
                 init_best_E=int(res.init_best_E), iters=int(it))
 
 
-def step(Q, prm: Params, seed: int, t: int, S, best_E=None, best_x=None, H=None):
+def step(Q, prm: Params, seed: int, t: int, S, best_E=None, best_x=None, H=None, W=None, want_features=False):
     """One outer iteration of Algorithm 2 from the solution set S (not
     modified).  Returns dict(S, E, trace3, best_E, best_x, T, A, C, H,
-    improved): T/C the Tabu toggle counts and final tabu memory of each
-    replica, H the per-replica selection hit counts (H input + 1 for every
-    variable placed in a subQUBO this iteration)."""
+    improved, winner, F, score): T/C the Tabu toggle counts and final tabu
+    memory of each replica, H the per-replica selection hit counts (H input
+    + 1 for every variable placed in a subQUBO this iteration), winner the
+    replica last copied into best_x (-1: none).  W (4673 BF16-valued floats)
+    is the proposal network, required when prm.select_mode != 0; with
+    want_features, F [z][n][6] and (when W is given) score [z][n] are the
+    features and scores at selection time."""
     Q, n = _q(Q)
     S = _u8(S).copy()
     z = prm.z
@@ -325,9 +332,46 @@ def step(Q, prm: Params, seed: int, t: int, S, best_E=None, best_x=None, H=None)
     Cm = np.zeros((z, n), np.int32)
     Hm = np.zeros((z, n), np.int32) if H is None else np.ascontiguousarray(H, np.int32).copy()
     assert Hm.shape == (z, n)
+    Wf = None if W is None else np.ascontiguousarray(W, np.float32)
+    assert Wf is None or Wf.shape == (NPAR,)
+    assert prm.select_mode == 0 or Wf is not None
+    F = np.zeros((z, n, 6), np.float32) if want_features else None
+    sc = np.zeros((z, n), np.float32) if (want_features and Wf is not None) else None
+    win = np.zeros(1, np.int32)
+    nul = C.c_void_p(None)
     imp = lib().orc_step(_p(Q), n, C.byref(prm), seed, t, _p(eh), _p(S), _p(E), _p(tr), _p(bE), _p(bx),
-                         _p(T), _p(A), _p(Cm), _p(Hm))
-    return dict(S=S, E=E, trace3=tr, best_E=int(bE[0]), best_x=bx, T=T, A=A, C=Cm, H=Hm, improved=int(imp))
+                         _p(T), _p(A), _p(Cm), _p(Hm), nul if Wf is None else _p(Wf),
+                         nul if F is None else _p(F), nul if sc is None else _p(sc), _p(win))
+    assert imp >= 0
+    return dict(S=S, E=E, trace3=tr, best_E=int(bE[0]), best_x=bx, T=T, A=A, C=Cm, H=Hm, improved=int(imp),
+                winner=int(win[0]), F=F, score=sc)
+
+
+# --------------------------------------------------------------------------- learned selection
+NPAR = 4673  # 6-64-64-1 network: W1[64][6], b1[64], W2[64][64], b2[64], w3[64], b3
+
+
+def features(x, g, T, Cm, H, eta_hat_v, t, alpha, c):
+    """Per-variable features of one solution at selection time, float32 [n][6]."""
+    x, g, T, Cm, H, eh = _u8(x), _i32(g), _i32(T), _i32(Cm), _i32(H), _i32(eta_hat_v)
+    n = x.shape[0]
+    F = np.zeros((n, 6), np.float32)
+    lib().orc_features(n, _p(x), _p(g), _p(T), _p(Cm), _p(H), _p(eh), int(t), int(alpha), int(c), _p(F))
+    return F
+
+
+def mlp_score_f32(W, F):
+    """Float scores of the rows of F [rows][6] (fused multiply-adds in a fixed order)."""
+    Wf = np.ascontiguousarray(W, np.float32)
+    F = np.ascontiguousarray(F, np.float32).reshape(-1, 6)
+    out = np.zeros(F.shape[0], np.float32)
+    for r in range(F.shape[0]):
+        out[r] = lib().orc_mlp_score_f32(_p(Wf), _p(F[r]))
+    return out
+
+
+def score_key(s) -> int:
+    return int(lib().orc_score_key(float(np.float32(s))))
 
 
 def initial_pass(Q, prm: Params, seed: int, S):
