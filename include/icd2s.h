@@ -48,6 +48,7 @@ extern "C" {
 
 typedef struct icd2s_qubo icd2s_qubo;   /* device copy of Q and its per-instance data */
 typedef struct icd2s_state icd2s_state; /* z solutions (replicas) with gains and energies */
+typedef struct icd2s_mlp icd2s_mlp;     /* proposal network of the learned selection */
 
 /* Solver parameters (Algorithm 2; defaults from Table 1 via icd2s_default_params). */
 typedef struct icd2s_params {
@@ -73,7 +74,15 @@ typedef struct icd2s_params {
     int32_t refresh_every; /* > 0: icd2s_run recomputes all gains and energies on the tensor cores
                               every this many iterations and fails with ICD2S_ERR_INVARIANT if
                               they differ from the tracked ones (see icd2s_refresh) */
-    int32_t reserved[6];
+    int32_t select_mode;   /* subset S' of Algorithm 4: 0 = the highest A (the paper's rule);
+                              1 = the highest score of the proposal network attached with
+                              icd2s_state_set_mlp (learned selection); 2 = learned on even
+                              replicas, the paper's rule on odd ones.  A always ranks the
+                              mutation candidates. */
+    int32_t stop_at_target;/* 1: icd2s_run / icd2s_state_run stop as soon as the best energy is
+                              <= target_E and report the device time to reach it */
+    int64_t target_E;
+    int32_t reserved[2];
 } icd2s_params;
 
 /* Per-call anneal parameters (the emulated Ising machine). */
@@ -105,7 +114,21 @@ typedef struct icd2s_stats {
     int64_t anneal_attempts; /* single-flip attempts made by the emulated Ising machine */
     int64_t tabu_moves;      /* Tabu iterations summed over solutions */
     double device_ms;        /* device time of the loop (CUDA events) */
+    double ttt_ms;           /* stop_at_target: device time from the start of the run (initial
+                                pass included) to the end of the iteration that reached the
+                                target; -1 if it was not reached */
+    int32_t hit_iter;        /* iterations completed when the target was reached (0: by the
+                                initial pass; -1: not reached) */
 } icd2s_stats;
+
+/* Training parameters of the proposal network (icd2s_mlp_train). */
+typedef struct icd2s_train_params {
+    int32_t steps;       /* Adam steps */
+    int32_t batch;       /* rows per step; >= rows: every row, in order (full batch) */
+    float lr, beta1, beta2, eps;   /* Adam (Kingma & Ba, ICLR'15) */
+    float pos_weight;    /* weight of the y = 1 term of the loss */
+    int32_t reserved[3];
+} icd2s_train_params;
 
 /* Message of the last failure on this thread ("" if none).  Never NULL. */
 const char* icd2s_last_error(void);
@@ -232,6 +255,83 @@ int icd2s_step_host(icd2s_state* st, const icd2s_params* p, int32_t t, const uin
  * energy.  S_out (optional, z * n): the final solutions. */
 int icd2s_run(icd2s_qubo* q, const icd2s_params* p, uint64_t seed, uint8_t* x_out, int64_t* E_out,
               icd2s_stats* stats, int64_t* trace, uint8_t* S_out);
+
+/* icd2s_run on an existing state (its current solutions, its attached
+ * proposal network and improvement log, its tuning): Call_IM_Solution_Set,
+ * then outer iterations t = 0, 1, ... until max_iters, patience or the
+ * target.  The state's best solution is reset to its current solutions
+ * first.  Outputs as for icd2s_run. */
+int icd2s_state_run(icd2s_state* st, const icd2s_params* p, uint8_t* x_out, int64_t* E_out,
+                    icd2s_stats* stats, int64_t* trace, uint8_t* S_out);
+
+/* --- Learned selection (an addition to the paper's method) -------------------
+ * A proposal network scores every variable of every replica at selection
+ * time from six features (reading of the method's data-driven choice of S'):
+ *   f0 = x_i, f1 = g_i / (max_j |g_j| + 1), f2 = T_i / alpha, f3 = C_i / c,
+ *   f4 = H_i / (t + 1), f5 = eta_hat_i / 2^16,
+ * with g the gains after the Tabu search, T/C its toggle counts and final
+ * tabu memory, H the selection hit counts (Ising-machine calls that included
+ * variable i before iteration t) and eta_hat Eq. 6 normalised (Q16).  Each
+ * quotient is the correctly rounded float quotient.  Network: 6 -> 64 ReLU ->
+ * 64 ReLU -> 1, parameters flat as W1[64][6], b1[64], W2[64][64], b2[64],
+ * w3[64], b3 (4673 floats; row o = weights into unit o).  It computes with the
+ * BF16 roundings (nearest even) of float32 master weights, in float, one
+ * fused multiply-add per product, units and inputs in increasing order.
+ * S' = the highest scores (index ascending on ties; the score's IEEE bit
+ * pattern orders -0 below +0). */
+#define ICD2S_MLP_PARAMS 4673
+
+/* New network with weights uniform in +-sqrt(6 / (fan_in + fan_out))
+ * (Philox with `seed`), zero biases, Adam moments zero. */
+int icd2s_mlp_create(uint64_t seed, icd2s_mlp** out);
+int icd2s_mlp_destroy(icd2s_mlp* m);
+/* Replaces the master weights (host, 4673 floats; must be finite) and
+ * resets Adam. */
+int icd2s_mlp_set_weights(icd2s_mlp* m, const float* W_host);
+/* Host copies of the master weights and of the BF16 weights widened to
+ * float (either may be NULL).  Synchronises. */
+int icd2s_mlp_get_weights(icd2s_mlp* m, float* master_host, float* bf16_host);
+/* Scores of the rows F_dev[rows][6] into score_dev[rows]. */
+int icd2s_mlp_score(icd2s_mlp* m, const float* F_dev, int64_t rows, float* score_dev, void* stream);
+/* Mean loss over all rows, l = pos_weight y softplus(-s) + (1 - y) softplus(s),
+ * into loss_dev[1] and its gradient with respect to the (BF16) weights into
+ * grad_dev[4673] (either may be NULL).  y_dev[rows] holds 0/1 labels.  The
+ * sums are taken in a fixed order: the result does not depend on scheduling. */
+int icd2s_mlp_grad(icd2s_mlp* m, const float* F_dev, const uint8_t* y_dev, int64_t rows, float pos_weight,
+                   float* grad_dev, float* loss_dev, void* stream);
+/* tp->steps Adam steps on mini-batches of the rows (see icd2s_train_params;
+ * a batch smaller than rows draws its rows with Philox from the network's
+ * seed and its running step count).  loss_host[tp->steps] (may be NULL)
+ * receives each step's mean batch loss; synchronises `stream` then. */
+int icd2s_mlp_train(icd2s_mlp* m, const float* F_dev, const uint8_t* y_dev, int64_t rows,
+                    const icd2s_train_params* tp, float* loss_host, void* stream);
+
+/* Attaches a network to a state for select_mode 1/2 (NULL detaches).  The
+ * state borrows it: it must outlive the state's use of it. */
+int icd2s_state_set_mlp(icd2s_state* st, icd2s_mlp* m);
+/* Features F_host[replicas][n][6] and scores score_host[replicas][n] of the
+ * last step that computed them (learned mode or logging on); either may be
+ * NULL.  Synchronises. */
+int icd2s_get_features(icd2s_state* st, float* F_host, float* score_host);
+/* Selection hit counts H_host[replicas][n] (reset by state_create/load). */
+int icd2s_get_hits(icd2s_state* st, int32_t* H_host);
+
+/* Improvement log (training data for the network, reading S22): with a
+ * capacity > 0, every outer iteration that lowers the best energy appends one
+ * entry: the features (at that iteration's selection time) of the replica
+ * whose solution became the best, and labels y_i = 1 where the new best
+ * solution differs from the best solution at the previous entry (at the
+ * start of logging for the first one).  A ring buffer of `capacity` entries
+ * of n rows; capacity 0 turns logging off and frees it. */
+int icd2s_log_enable(icd2s_state* st, int32_t capacity);
+/* entries: appended since enabling (may exceed capacity); capacity. */
+int icd2s_log_info(icd2s_state* st, int32_t* entries, int32_t* capacity);
+/* Copies the min(entries, capacity) stored entries in slot order (entry e is
+ * in slot e mod capacity): F_out[count][n][6], y_out[count][n],
+ * replica_out[count] (any may be NULL), to host memory or, with
+ * out_is_device, to device memory.  Synchronises `stream`. */
+int icd2s_log_copy(icd2s_state* st, float* F_out, uint8_t* y_out, int32_t* replica_out, int32_t out_is_device,
+                   void* stream);
 
 /* Per-phase device timing of icd2s_step.  When enabled, each step records
  * CUDA events on its stream around its phases; icd2s_get_phase_ms waits for

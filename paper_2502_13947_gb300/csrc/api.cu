@@ -105,6 +105,17 @@ struct icd2s_qubo {
     void* Qb = nullptr;  // bf16 copy of Q for the tensor-core refresh (made on first use)
 };
 
+// Proposal network: float32 master weights with Adam moments, the BF16 copy
+// the kernels compute with, and the training scratch.
+struct icd2s_mlp {
+    uint64_t seed = 0;
+    float* master = nullptr; float* mom = nullptr; float* vel = nullptr;
+    void* Wb = nullptr;                       // bf16 [kNPar]
+    float* partial = nullptr; size_t partial_cap = 0;
+    float* losses = nullptr; int loss_cap = 0;
+    int64_t adam_t = 0;                       // Adam steps taken
+};
+
 struct icd2s_state {
     icd2s_qubo* q = nullptr;
     int R = 0;
@@ -145,6 +156,16 @@ struct icd2s_state {
     // phase timing of icd2s_step: events [2 * phase] / [2 * phase + 1]
     bool timing = false, timed_step = false;
     cudaEvent_t ev[2 * ICD2S_PHASES] = {};
+    unsigned long long graph_kernels = 0;  // kernels in one replay of the captured step
+    // learned selection
+    int32_t* H = nullptr;                    // [R][ld] hit counts
+    float* F = nullptr; float* score = nullptr; int32_t* gmax = nullptr;  // made on first use
+    bool have_features = false, have_scores = false;
+    icd2s_mlp* mlp = nullptr;                // borrowed
+    // improvement log (ring buffer)
+    int log_cap = 0;
+    float* LF = nullptr; uint8_t* LY = nullptr; int32_t* lrep = nullptr; uint8_t* prev_x = nullptr;
+    int32_t* log_ctl = nullptr;              // {entries, capacity}
 };
 
 // Records the start (which == 0) or end (which == 1) event of a phase.
@@ -158,7 +179,8 @@ static void free_state(icd2s_state* st)
     void* ptrs[] = {st->X, st->G, st->E, st->T, st->C, st->gamma, st->A, st->delta, st->order, st->sel,
                     st->FL, st->FCNT, st->DEACC, st->DONE, st->best_x, st->best_E, st->flags, st->idx,
                     st->off, st->scratch, st->counters, st->nlog, st->beta, st->limtab,
-                    st->lpt, st->queue, st->ctx, st->rates, st->Xb, st->G2, st->E2, st->rflags};
+                    st->lpt, st->queue, st->ctx, st->rates, st->Xb, st->G2, st->E2, st->rflags,
+                    st->H, st->F, st->score, st->gmax, st->LF, st->LY, st->lrep, st->prev_x, st->log_ctl};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (st->graph) cudaGraphExecDestroy(st->graph);
@@ -244,6 +266,10 @@ static int check_params(const icd2s_state* st, const icd2s_params* p)
     REQ(p->mut_mode == 0 || (p->mut_mode == 1 && p->mut_rate >= 0 && p->mut_rate <= 1), ICD2S_ERR_ARG,
         "mut_mode must be 0 or 1 with 0 <= mut_rate <= 1");
     REQ(p->max_iters >= 0, ICD2S_ERR_ARG, "max_iters < 0");
+    REQ(p->select_mode >= 0 && p->select_mode <= 2, ICD2S_ERR_ARG, "select_mode=%d outside 0..2", p->select_mode);
+    REQ(p->select_mode == 0 || st->mlp, ICD2S_ERR_STATE, "select_mode %d needs a network (icd2s_state_set_mlp)",
+        p->select_mode);
+    REQ(p->stop_at_target == 0 || p->stop_at_target == 1, ICD2S_ERR_ARG, "stop_at_target must be 0 or 1");
     return ICD2S_OK;
 }
 
@@ -368,9 +394,9 @@ int icd2s_state_create(icd2s_qubo* q, int32_t replicas, uint64_t seed, icd2s_sta
 #define ALLOC(ptr, cnt) if (e == cudaSuccess) e = dalloc(&st->ptr, (cnt))
     ALLOC(X, RL); ALLOC(G, RL); ALLOC(E, replicas); ALLOC(T, RL); ALLOC(C, RL); ALLOC(gamma, q->ld);
     ALLOC(A, RL); ALLOC(delta, RL); ALLOC(order, RL); ALLOC(sel, RL); ALLOC(FL, RL); ALLOC(FCNT, replicas);
-    ALLOC(DEACC, replicas); ALLOC(DONE, replicas); ALLOC(best_x, q->ld); ALLOC(best_E, 1); ALLOC(flags, 4);
+    ALLOC(DEACC, replicas); ALLOC(DONE, replicas); ALLOC(best_x, q->ld); ALLOC(best_E, 1); ALLOC(flags, 8);
     ALLOC(idx, RL); ALLOC(off, (size_t)replicas * 64 + 1); ALLOC(scratch, RL); ALLOC(counters, 4);
-    ALLOC(nlog, 4096); ALLOC(lpt, (size_t)replicas * 64); ALLOC(queue, 4); ALLOC(ctx, 4);
+    ALLOC(nlog, 4096); ALLOC(lpt, (size_t)replicas * 64); ALLOC(queue, 4); ALLOC(ctx, 4); ALLOC(H, RL);
 #undef ALLOC
     if (e != cudaSuccess) {
         free_state(st);
@@ -381,6 +407,7 @@ int icd2s_state_create(icd2s_qubo* q, int32_t replicas, uint64_t seed, icd2s_sta
     d.X = st->X; d.G = st->G; d.E = st->E; d.T = st->T; d.C = st->C; d.gamma = st->gamma; d.A = st->A;
     d.delta = st->delta; d.order = st->order; d.sel = st->sel; d.FL = st->FL; d.FCNT = st->FCNT;
     d.DEACC = st->DEACC; d.DONE = st->DONE; d.best_x = st->best_x; d.best_E = st->best_E; d.flags = st->flags;
+    d.H = st->H;
     d.k0 = (uint32_t)(seed & 0xffffffffu); d.k1 = (uint32_t)(seed >> 32);
     uint32_t nl[4096];
     make_nlog(nl);
@@ -389,7 +416,8 @@ int icd2s_state_create(icd2s_qubo* q, int32_t replicas, uint64_t seed, icd2s_sta
     if ((e = cudaMemset(st->T, 0, RL * 4)) != cudaSuccess || (e = cudaMemset(st->C, 0, RL * 4)) != cudaSuccess ||
         (e = cudaMemset(st->FCNT, 0, replicas * 4)) != cudaSuccess ||
         (e = cudaMemset(st->DEACC, 0, replicas * 8)) != cudaSuccess ||
-        (e = cudaMemset(st->DONE, 0, replicas * 4)) != cudaSuccess || (e = cudaMemset(st->flags, 0, 16)) != cudaSuccess ||
+        (e = cudaMemset(st->DONE, 0, replicas * 4)) != cudaSuccess || (e = cudaMemset(st->flags, 0, 32)) != cudaSuccess ||
+        (e = cudaMemset(st->H, 0, RL * 4)) != cudaSuccess ||
         (e = cudaMemset(st->counters, 0, 32)) != cudaSuccess || (e = cudaMemset(st->best_x, 0, q->ld)) != cudaSuccess ||
         (e = cudaMemcpy(st->best_E, &big, 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(st->nlog, nl, sizeof nl, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -419,6 +447,7 @@ int icd2s_state_load(icd2s_state* st, const uint8_t* x, int32_t x_is_device, voi
     }
     CK(launch_pad_rows(src, n, R, st->X, st->q->ld, s));
     CK(launch_recompute(st->d, st->X, st->q->ld, R, st->G, st->E, s));
+    CK(cudaMemsetAsync(st->H, 0, (size_t)R * st->q->ld * 4, s));
     return ICD2S_OK;
 }
 
@@ -479,7 +508,8 @@ int icd2s_tabu(icd2s_state* st, int32_t alpha, int32_t c, void* stream)
 
 // iter_dev: non-null when the iteration number comes from device memory (a replayed step).
 static int select_impl(icd2s_state* st, int64_t w1, int64_t w2, int64_t w3, int K, int m_min, int m_max,
-                       uint32_t iter, cudaStream_t s, const int32_t* iter_dev = nullptr)
+                       uint32_t iter, cudaStream_t s, const int32_t* iter_dev = nullptr, int mode = 0,
+                       bool count_hits = true)
 {
     const int n = st->q->n;
     REQ(K >= 1 && K <= 64, ICD2S_ERR_RANGE, "K=%d outside 1..64", K);
@@ -489,7 +519,7 @@ static int select_impl(icd2s_state* st, int64_t w1, int64_t w2, int64_t w3, int 
     REQ(w1 >= -wl && w1 <= wl && w2 >= -wl && w2 <= wl && w3 >= -wl && w3 <= wl, ICD2S_ERR_RANGE, "|w| > 2^24");
     CK(launch_gamma(st->d, s));
     CK(launch_sizes(st->R, K, m_min, m_max, st->d.k0, st->d.k1, iter, iter_dev, st->off, st->lpt, st->queue, s));
-    CK(launch_select(st->d, w1, w2, w3, K, st->off, st->idx, s));
+    CK(launch_select(st->d, w1, w2, w3, K, st->off, st->idx, mode, count_hits, s));
     st->have_select = true;
     st->sel_K = K;
     return ICD2S_OK;
@@ -651,6 +681,27 @@ int icd2s_initial_pass(icd2s_state* st, const icd2s_params* p, void* stream)
     return ICD2S_OK;
 }
 
+// Feature, score and hit-count buffers of the learned selection (made on
+// first use; a captured step holds the pointers, so a new buffer bumps gen).
+static int ensure_features(icd2s_state* st, cudaStream_t s)
+{
+    if (st->F) return ICD2S_OK;
+    const size_t RL = (size_t)st->R * st->q->ld;
+    CK(cudaStreamSynchronize(s));
+    CK(dalloc(&st->F, RL * 6));
+    CK(dalloc(&st->score, RL));
+    CK(dalloc(&st->gmax, (size_t)st->R));
+    st->d.F = st->F;
+    st->d.score = st->score;
+    ++st->gen;
+    return ICD2S_OK;
+}
+
+static bool wants_features(const icd2s_state* st, const icd2s_params* p)
+{
+    return p->select_mode != 0 || st->log_cap > 0;
+}
+
 // One outer iteration.  dev_iter: the kernels read t (and the mutation rate)
 // from st->ctx / st->rates, and the last one advances st->ctx[0] -- the form
 // that is captured once and replayed as a CUDA graph.
@@ -662,12 +713,23 @@ static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* tra
     const bool queued = p->K > 1 || p->m_min != p->m_max;  // uneven batch: persistent queue kernel
     int rc = ensure_beta(st, p->sweeps, p->T_max, p->T_min, s);
     if (rc) return rc;
+    const bool feats = wants_features(st, p);
+    if (feats && (rc = ensure_features(st, s))) return rc;
     mark(st, 0, 0, s);
     CK(launch_tabu(st->d, p->alpha, p->c, st->tune.tabu_variant, s));                     // Algorithm 1
     mark(st, 0, 1, s);
     CK(launch_best(st->d, trace_it, 0, nullptr, s));
     mark(st, 1, 0, s);
-    rc = select_impl(st, p->w1, p->w2, p->w3, p->K, p->m_min, p->m_max, (uint32_t)t, s, it_dev);  // Eq. 6-8, Alg. 3
+    if (feats) {                                                   // learned selection: features, scores
+        CK(launch_features(st->d, t, it_dev, p->alpha, p->c, st->gmax, s));
+        st->have_features = true;
+        if (st->mlp) {
+            CK(launch_score(st->F, (long long)R * st->q->ld, st->mlp->Wb, st->score, s));
+            st->have_scores = true;
+        }
+    }
+    rc = select_impl(st, p->w1, p->w2, p->w3, p->K, p->m_min, p->m_max, (uint32_t)t, s, it_dev,
+                     p->select_mode);                                                       // Eq. 6-8, Alg. 3-4
     if (rc) return rc;
     mark(st, 1, 1, s);
     mark(st, 2, 0, s);
@@ -687,7 +749,9 @@ static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* tra
     CK(launch_apply(st->d, s));
     mark(st, 5, 1, s);
     mark(st, 6, 0, s);
-    CK(launch_best(st->d, trace_it ? trace_it + 2 * R : nullptr, 1, dev_iter ? st->ctx : nullptr, s));
+    CK(launch_best(st->d, trace_it ? trace_it + 2 * R : nullptr, 1, dev_iter ? st->ctx : nullptr, s,
+                   st->log_cap > 0 ? st->log_ctl : nullptr));
+    if (st->log_cap > 0) CK(launch_log(st->d, st->prev_x, st->LF, st->LY, st->lrep, s));
     mark(st, 6, 1, s);
     st->timed_step = st->timing;
     return ICD2S_OK;
@@ -709,13 +773,17 @@ static int graph_step(icd2s_state* st, const icd2s_params* p, int t, cudaStream_
         CK(cudaEventRecord(st->join_ev, caller));
         CK(cudaStreamWaitEvent(s, st->join_ev, 0));
     }
+    if (wants_features(st, p) && (rc = ensure_features(st, caller))) return rc;
     if (!st->graph || st->graph_gen != st->gen || std::memcmp(&st->graph_p, p, sizeof *p) != 0) {
         if (st->graph) { cudaGraphExecDestroy(st->graph); st->graph = nullptr; }
         const bool timing = st->timing;
         st->timing = false;  // no event records inside the graph
+        const unsigned long long before = g_launches.load();
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
         rc = step_impl(st, p, 0, nullptr, s, true);
         st->timing = timing;
+        st->graph_kernels = g_launches.load() - before;  // captured, not run: counted per replay
+        g_launches.fetch_sub(st->graph_kernels);
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(s, &g);
         if (rc) { if (g) cudaGraphDestroy(g); return rc; }
@@ -729,7 +797,7 @@ static int graph_step(icd2s_state* st, const icd2s_params* p, int t, cudaStream_
     }
     if (st->dev_t != t) CK(launch_set_iter(st->ctx, t, s));
     CK(cudaGraphLaunch(st->graph, s));
-    note_launch(11);  // the kernels of one outer iteration
+    note_launch((int)st->graph_kernels);
     st->dev_t = t + 1;
     st->timed_step = false;
     if (!caller) {
@@ -851,7 +919,7 @@ int icd2s_autotune(icd2s_state* st, const icd2s_params* p, icd2s_tuning* chosen,
         if (vbest < best_ms) { best_ms = vbest; best.tabu_variant = v; }
     }
     if ((rc = restore())) return rc;
-    rc = select_impl(st, p->w1, p->w2, p->w3, p->K, p->m_min, p->m_max, 0u, s);
+    rc = select_impl(st, p->w1, p->w2, p->w3, p->K, p->m_min, p->m_max, 0u, s, nullptr, 0, false);
     if (rc) return rc;
     AnnealArgs a{};
     a.idx = st->idx; a.off = st->off; a.count = R * p->K; a.per_replica = p->K; a.limtab = st->limtab;
@@ -918,45 +986,52 @@ int icd2s_step_host(icd2s_state* st, const icd2s_params* p, int32_t t, const uin
     return ICD2S_OK;
 }
 
-int icd2s_run(icd2s_qubo* q, const icd2s_params* p, uint64_t seed, uint8_t* x_out, int64_t* E_out,
-              icd2s_stats* stats, int64_t* trace, uint8_t* S_out)
+// Algorithm 2 on a state: Call_IM_Solution_Set, then outer iterations until
+// max_iters, patience or the target.  Per-iteration host synchronisation only
+// when patience or the target needs this iteration's flags / best energy.
+static int run_impl(icd2s_state* st, const icd2s_params* p, uint8_t* x_out, int64_t* E_out, icd2s_stats* stats,
+                    int64_t* trace, uint8_t* S_out)
 {
-    REQ(q && p, ICD2S_ERR_ARG, "NULL argument");
-    icd2s_state* st = nullptr;
-    REQ(p->z >= 1 && p->z <= kMaxReplicas, ICD2S_ERR_RANGE, "z=%d outside 1..%d", p->z, kMaxReplicas);
-    int rc = icd2s_state_create(q, p->z, seed, &st);
+    int rc = check_params(st, p);
     if (rc) return rc;
-    struct Guard { icd2s_state* s; int64_t* tr; cudaEvent_t e0, e1; ~Guard() {
+    icd2s_qubo* q = st->q;
+    const int R = st->R;
+    struct Guard { int64_t* tr = nullptr; cudaEvent_t e0 = nullptr, e1 = nullptr, eh = nullptr; ~Guard() {
         if (tr) cudaFree(tr);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
-        icd2s_state_destroy(s); } } guard{st, nullptr, nullptr, nullptr};
-    rc = check_params(st, p);
-    if (rc) return rc;
-    const int R = st->R;
+        if (eh) cudaEventDestroy(eh); } } guard;
     const size_t tr_len = (size_t)(p->max_iters > 0 ? p->max_iters : 1) * (3 * R + 1);
     if (trace) CK(dalloc(&guard.tr, tr_len));
     CK(cudaEventCreate(&guard.e0));
     CK(cudaEventCreate(&guard.e1));
+    CK(cudaEventCreate(&guard.eh));
     cudaStream_t s = 0;
+    const int64_t big = INT64_MAX;
+    CK(cudaMemcpyAsync(st->best_E, &big, 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(st->flags, 0, 32, s));
     CK(cudaEventRecord(guard.e0, s));
     rc = icd2s_initial_pass(st, p, s);
     if (rc) return rc;
     CK(launch_best(st->d, nullptr, 0, nullptr, s));
     CK(cudaMemsetAsync(st->flags, 0, 8, s));
+    if (st->log_cap > 0) CK(cudaMemcpyAsync(st->prev_x, st->best_x, q->ld, cudaMemcpyDeviceToDevice, s));
     int64_t init_best = 0;
     CK(cudaMemcpyAsync(&init_best, st->best_E, 8, cudaMemcpyDeviceToHost, s));
-    int t = 0;
+    CK(cudaStreamSynchronize(s));  // init_best is read below (and the host value must stay alive)
+    int t = 0, hit_iter = -1;
+    if (p->stop_at_target && init_best <= p->target_E) {
+        hit_iter = 0;
+        CK(cudaEventRecord(guard.eh, s));
+    }
     int32_t flags[2] = {0, 0};
+    int64_t cur_best = init_best;
     const bool graph = p->use_graph && !trace;
-    while (t < p->max_iters && (p->patience <= 0 || flags[1] < p->patience)) {
+    const bool sync_each = p->patience > 0 || p->stop_at_target;
+    while (hit_iter < 0 && t < p->max_iters && (p->patience <= 0 || flags[1] < p->patience)) {
         if (graph) rc = graph_step(st, p, t, s);
         else rc = step_impl(st, p, t, guard.tr ? guard.tr + (size_t)t * (3 * R + 1) : nullptr, s);
         if (rc) return rc;
-        if (p->patience > 0) {  // the termination test needs this iteration's stale count
-            CK(cudaMemcpyAsync(flags, st->flags, 8, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-        }
         if (p->refresh_every > 0 && (t + 1) % p->refresh_every == 0) {  // drift check on the tensor cores
             int32_t bad = 0;
             rc = icd2s_refresh(st, 0, &bad, s);
@@ -964,6 +1039,13 @@ int icd2s_run(icd2s_qubo* q, const icd2s_params* p, uint64_t seed, uint8_t* x_ou
             REQ(bad == 0, ICD2S_ERR_INVARIANT, "tracked gains/energies differ from the refresh in %d entries", bad);
         }
         ++t;
+        if (sync_each) {  // the termination tests need this iteration's stale count / best energy
+            CK(cudaEventRecord(guard.eh, s));
+            CK(cudaMemcpyAsync(flags, st->flags, 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(&cur_best, st->best_E, 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (p->stop_at_target && cur_best <= p->target_E) hit_iter = t;
+        }
     }
     CK(cudaEventRecord(guard.e1, s));
     CK(cudaStreamSynchronize(s));
@@ -980,7 +1062,281 @@ int icd2s_run(icd2s_qubo* q, const icd2s_params* p, uint64_t seed, uint8_t* x_ou
         CK(cudaEventElapsedTime(&ms, guard.e0, guard.e1));
         stats->iters = t; stats->best_E = bestE; stats->init_best_E = init_best; stats->anneal_attempts = att;
         stats->tabu_moves = (int64_t)t * R * p->alpha; stats->device_ms = ms;
+        stats->hit_iter = hit_iter;
+        stats->ttt_ms = -1.0;
+        if (hit_iter >= 0) {
+            float mh = 0;
+            CK(cudaEventElapsedTime(&mh, guard.e0, guard.eh));
+            stats->ttt_ms = mh;
+        }
     }
+    return ICD2S_OK;
+}
+
+int icd2s_run(icd2s_qubo* q, const icd2s_params* p, uint64_t seed, uint8_t* x_out, int64_t* E_out,
+              icd2s_stats* stats, int64_t* trace, uint8_t* S_out)
+{
+    REQ(q && p, ICD2S_ERR_ARG, "NULL argument");
+    REQ(p->z >= 1 && p->z <= kMaxReplicas, ICD2S_ERR_RANGE, "z=%d outside 1..%d", p->z, kMaxReplicas);
+    REQ(p->select_mode == 0, ICD2S_ERR_STATE, "learned selection needs a state with a network: icd2s_state_run");
+    icd2s_state* st = nullptr;
+    int rc = icd2s_state_create(q, p->z, seed, &st);
+    if (rc) return rc;
+    rc = run_impl(st, p, x_out, E_out, stats, trace, S_out);
+    icd2s_state_destroy(st);
+    return rc;
+}
+
+int icd2s_state_run(icd2s_state* st, const icd2s_params* p, uint8_t* x_out, int64_t* E_out, icd2s_stats* stats,
+                    int64_t* trace, uint8_t* S_out)
+{
+    REQ(st && p, ICD2S_ERR_ARG, "NULL argument");
+    return run_impl(st, p, x_out, E_out, stats, trace, S_out);
+}
+
+// ----------------------------------------------------------------------------- learned selection
+static int mlp_upload(icd2s_mlp* m, const float* W)
+{
+    CK(cudaMemcpy(m->master, W, sizeof(float) * kNPar, cudaMemcpyHostToDevice));
+    CK(cudaMemset(m->mom, 0, sizeof(float) * kNPar));
+    CK(cudaMemset(m->vel, 0, sizeof(float) * kNPar));
+    CK(launch_round_bf16(m->master, m->Wb, 0));
+    CK(cudaDeviceSynchronize());
+    m->adam_t = 0;
+    return ICD2S_OK;
+}
+
+static void free_mlp(icd2s_mlp* m)
+{
+    void* ptrs[] = {m->master, m->mom, m->vel, m->Wb, m->partial, m->losses};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete m;
+}
+
+int icd2s_mlp_create(uint64_t seed, icd2s_mlp** out)
+{
+    REQ(out, ICD2S_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    auto* m = new icd2s_mlp();
+    m->seed = seed;
+    cudaError_t e = cudaSuccess;
+    if ((e = dalloc(&m->master, kNPar)) != cudaSuccess || (e = dalloc(&m->mom, kNPar)) != cudaSuccess ||
+        (e = dalloc(&m->vel, kNPar)) != cudaSuccess || (e = cudaMalloc(&m->Wb, 2 * kNPar)) != cudaSuccess) {
+        free_mlp(m);
+        return fail(ICD2S_ERR_OOM, "device allocation failed: %s", cudaGetErrorString(e));
+    }
+    // Glorot-uniform weights from Philox (counter (q, TAG_MLP_INIT << 24, 0, 0)), zero biases
+    std::vector<float> W(kNPar, 0.f);
+    const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+    auto fill = [&](int off, int count, int fan_in, int fan_out) {
+        const double bound = std::sqrt(6.0 / (double)(fan_in + fan_out));
+        for (int i = 0; i < count; ++i) {
+            const u32x4 v = philox10((uint32_t)(off + i), kTagMlpInit << 24, 0u, 0u, k0, k1);
+            const double u = (double)v.v[0] * (1.0 / 4294967296.0);
+            W[off + i] = (float)((2.0 * u - 1.0) * bound);
+        }
+    };
+    fill(kOffW1, 384, 6, 64);
+    fill(kOffW2, 4096, 64, 64);
+    fill(kOffW3, 64, 64, 1);
+    const int rc = mlp_upload(m, W.data());
+    if (rc) { free_mlp(m); return rc; }
+    *out = m;
+    return ICD2S_OK;
+}
+
+int icd2s_mlp_destroy(icd2s_mlp* m)
+{
+    if (m) free_mlp(m);
+    return ICD2S_OK;
+}
+
+int icd2s_mlp_set_weights(icd2s_mlp* m, const float* W_host)
+{
+    REQ(m && W_host, ICD2S_ERR_ARG, "NULL argument");
+    for (int q = 0; q < kNPar; ++q) REQ(std::isfinite(W_host[q]), ICD2S_ERR_ARG, "weight %d is not finite", q);
+    return mlp_upload(m, W_host);
+}
+
+int icd2s_mlp_get_weights(icd2s_mlp* m, float* master_host, float* bf16_host)
+{
+    REQ(m, ICD2S_ERR_ARG, "NULL network");
+    CK(cudaDeviceSynchronize());
+    if (master_host) CK(cudaMemcpy(master_host, m->master, sizeof(float) * kNPar, cudaMemcpyDeviceToHost));
+    if (bf16_host) {
+        std::vector<uint16_t> b(kNPar);
+        CK(cudaMemcpy(b.data(), m->Wb, 2 * kNPar, cudaMemcpyDeviceToHost));
+        for (int q = 0; q < kNPar; ++q) {
+            const uint32_t bits = (uint32_t)b[q] << 16;
+            std::memcpy(&bf16_host[q], &bits, 4);
+        }
+    }
+    return ICD2S_OK;
+}
+
+int icd2s_mlp_score(icd2s_mlp* m, const float* F_dev, int64_t rows, float* score_dev, void* stream)
+{
+    REQ(m && (rows == 0 || (F_dev && score_dev)), ICD2S_ERR_ARG, "NULL argument");
+    REQ(rows >= 0, ICD2S_ERR_ARG, "rows < 0");
+    CK(launch_score(F_dev, rows, m->Wb, score_dev, S(stream)));
+    return ICD2S_OK;
+}
+
+static int ensure_partial(icd2s_mlp* m, long long batch, cudaStream_t s)
+{
+    const size_t need = mlp_partial_floats(batch);
+    if (need <= m->partial_cap) return ICD2S_OK;
+    CK(cudaStreamSynchronize(s));
+    if (m->partial) CK(cudaFree(m->partial));
+    m->partial = nullptr;
+    m->partial_cap = 0;
+    CK(dalloc(&m->partial, need));
+    m->partial_cap = need;
+    return ICD2S_OK;
+}
+
+int icd2s_mlp_grad(icd2s_mlp* m, const float* F_dev, const uint8_t* y_dev, int64_t rows, float pos_weight,
+                   float* grad_dev, float* loss_dev, void* stream)
+{
+    REQ(m && F_dev && y_dev, ICD2S_ERR_ARG, "NULL argument");
+    REQ(rows >= 1 && rows <= ((int64_t)1 << 31) * 64, ICD2S_ERR_RANGE, "rows=%lld out of range", (long long)rows);
+    REQ(std::isfinite(pos_weight) && pos_weight >= 0.f, ICD2S_ERR_ARG, "pos_weight must be finite and >= 0");
+    cudaStream_t s = S(stream);
+    int rc = ensure_partial(m, rows, s);
+    if (rc) return rc;
+    CK(launch_mlp_grad(F_dev, y_dev, rows, rows, 0u, 0u, 0u, m->Wb, pos_weight, m->partial, grad_dev, loss_dev,
+                       nullptr, nullptr, nullptr, nullptr, 0, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f, s));
+    return ICD2S_OK;
+}
+
+int icd2s_mlp_train(icd2s_mlp* m, const float* F_dev, const uint8_t* y_dev, int64_t rows,
+                    const icd2s_train_params* tp, float* loss_host, void* stream)
+{
+    REQ(m && F_dev && y_dev && tp, ICD2S_ERR_ARG, "NULL argument");
+    REQ(rows >= 1 && rows <= ((int64_t)1 << 31) * 64, ICD2S_ERR_RANGE, "rows=%lld out of range", (long long)rows);
+    REQ(tp->steps >= 0 && tp->batch >= 1, ICD2S_ERR_ARG, "steps >= 0 and batch >= 1 required");
+    REQ(std::isfinite(tp->lr) && tp->lr >= 0.f && tp->beta1 >= 0.f && tp->beta1 < 1.f && tp->beta2 >= 0.f &&
+        tp->beta2 < 1.f && tp->eps > 0.f && std::isfinite(tp->pos_weight) && tp->pos_weight >= 0.f,
+        ICD2S_ERR_ARG, "bad training parameters");
+    if (tp->steps == 0) return ICD2S_OK;
+    cudaStream_t s = S(stream);
+    const long long batch = tp->batch < rows ? tp->batch : rows;
+    int rc = ensure_partial(m, batch, s);
+    if (rc) return rc;
+    if (tp->steps > m->loss_cap) {
+        CK(cudaStreamSynchronize(s));
+        if (m->losses) CK(cudaFree(m->losses));
+        m->losses = nullptr;
+        m->loss_cap = 0;
+        CK(dalloc(&m->losses, (size_t)tp->steps));
+        m->loss_cap = tp->steps;
+    }
+    const uint32_t k0 = (uint32_t)(m->seed & 0xffffffffu), k1 = (uint32_t)(m->seed >> 32);
+    for (int i = 0; i < tp->steps; ++i) {
+        const int64_t t = m->adam_t + 1;
+        const float bc1 = (float)(1.0 - std::pow((double)tp->beta1, (double)t));
+        const float bc2 = (float)(1.0 - std::pow((double)tp->beta2, (double)t));
+        CK(launch_mlp_grad(F_dev, y_dev, rows, tp->batch, (uint32_t)m->adam_t, k0, k1, m->Wb, tp->pos_weight,
+                           m->partial, nullptr, m->losses + i, m->master, m->mom, m->vel, m->Wb, 1, tp->lr,
+                           tp->beta1, tp->beta2, tp->eps, bc1, bc2, s));
+        m->adam_t = t;
+    }
+    if (loss_host) {
+        CK(cudaMemcpyAsync(loss_host, m->losses, sizeof(float) * tp->steps, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return ICD2S_OK;
+}
+
+int icd2s_state_set_mlp(icd2s_state* st, icd2s_mlp* m)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    st->mlp = m;
+    ++st->gen;  // the captured step holds the network's weights pointer
+    return ICD2S_OK;
+}
+
+int icd2s_get_features(icd2s_state* st, float* F_host, float* score_host)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    REQ(st->have_features && (score_host == nullptr || st->have_scores), ICD2S_ERR_STATE,
+        "no step has computed features%s yet", score_host ? " and scores" : "");
+    const int n = st->q->n, ld = st->q->ld, R = st->R;
+    CK(cudaDeviceSynchronize());
+    if (F_host)
+        CK(cudaMemcpy2D(F_host, (size_t)n * 24, st->F, (size_t)ld * 24, (size_t)n * 24, R, cudaMemcpyDeviceToHost));
+    if (score_host)
+        CK(cudaMemcpy2D(score_host, (size_t)n * 4, st->score, (size_t)ld * 4, (size_t)n * 4, R,
+                        cudaMemcpyDeviceToHost));
+    return ICD2S_OK;
+}
+
+int icd2s_get_hits(icd2s_state* st, int32_t* H_host)
+{
+    REQ(st && H_host, ICD2S_ERR_ARG, "NULL argument");
+    const int n = st->q->n, ld = st->q->ld, R = st->R;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy2D(H_host, (size_t)n * 4, st->H, (size_t)ld * 4, (size_t)n * 4, R, cudaMemcpyDeviceToHost));
+    return ICD2S_OK;
+}
+
+int icd2s_log_enable(icd2s_state* st, int32_t capacity)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    REQ(capacity >= 0, ICD2S_ERR_ARG, "capacity < 0");
+    const int n = st->q->n;
+    REQ((int64_t)capacity * n <= ((int64_t)1 << 31), ICD2S_ERR_RANGE, "capacity * n above 2^31 rows");
+    CK(cudaDeviceSynchronize());
+    void* ptrs[] = {st->LF, st->LY, st->lrep, st->prev_x, st->log_ctl};
+    for (void* p : ptrs)
+        if (p) CK(cudaFree(p));
+    st->LF = nullptr; st->LY = nullptr; st->lrep = nullptr; st->prev_x = nullptr; st->log_ctl = nullptr;
+    st->log_cap = 0;
+    ++st->gen;
+    if (capacity == 0) return ICD2S_OK;
+    CK(dalloc(&st->LF, (size_t)capacity * n * 6));
+    CK(dalloc(&st->LY, (size_t)capacity * n));
+    CK(dalloc(&st->lrep, (size_t)capacity));
+    CK(dalloc(&st->prev_x, (size_t)st->q->ld));
+    CK(dalloc(&st->log_ctl, 2));
+    const int32_t ctl[2] = {0, capacity};
+    CK(cudaMemcpy(st->log_ctl, ctl, 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(st->prev_x, st->best_x, (size_t)st->q->ld, cudaMemcpyDeviceToDevice));
+    st->log_cap = capacity;
+    return ICD2S_OK;
+}
+
+int icd2s_log_info(icd2s_state* st, int32_t* entries, int32_t* capacity)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    int32_t ctl[2] = {0, 0};
+    if (st->log_cap > 0) {
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpy(ctl, st->log_ctl, 8, cudaMemcpyDeviceToHost));
+    }
+    if (entries) *entries = ctl[0];
+    if (capacity) *capacity = st->log_cap;
+    return ICD2S_OK;
+}
+
+int icd2s_log_copy(icd2s_state* st, float* F_out, uint8_t* y_out, int32_t* replica_out, int32_t out_is_device,
+                   void* stream)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    REQ(st->log_cap > 0, ICD2S_ERR_STATE, "logging is off (icd2s_log_enable)");
+    cudaStream_t s = S(stream);
+    int32_t ctl[2] = {0, 0};
+    CK(cudaMemcpyAsync(ctl, st->log_ctl, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const size_t cnt = (size_t)(ctl[0] < st->log_cap ? ctl[0] : st->log_cap), n = (size_t)st->q->n;
+    const cudaMemcpyKind k = out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (cnt > 0) {
+        if (F_out) CK(cudaMemcpyAsync(F_out, st->LF, cnt * n * 24, k, s));
+        if (y_out) CK(cudaMemcpyAsync(y_out, st->LY, cnt * n, k, s));
+        if (replica_out) CK(cudaMemcpyAsync(replica_out, st->lrep, cnt * 4, k, s));
+    }
+    CK(cudaStreamSynchronize(s));
     return ICD2S_OK;
 }
 

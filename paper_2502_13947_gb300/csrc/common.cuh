@@ -14,6 +14,9 @@
 //   order  int32 [R][LD]       variables ranked by (A desc, index asc)
 //   sel    uint8 [R][LD]       1 where the variable is in S' (last selection)
 //   FL     int32 [R][LD]       flip lists: index | (old x << 31), FCNT[R] entries
+//   H      int32 [R][LD]       selection hit counts (Ising-machine calls that included j)
+//   F      float [R][LD][6]    features of the learned selection at selection time
+//   score  float [R][LD]       proposal-network scores
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -26,7 +29,14 @@ constexpr int kMaxM = 256;
 constexpr int kMaxReplicas = 4096;
 constexpr int kMaxSweeps = 16384;   // the acceptance-limit table is sweeps x 4096 int32
 
-constexpr uint32_t kTagInit = 1u, kTagAnneal = 2u, kTagMut = 3u, kTagSize = 4u;
+constexpr uint32_t kTagInit = 1u, kTagAnneal = 2u, kTagMut = 3u, kTagSize = 4u, kTagMlpInit = 5u, kTagTrain = 6u;
+
+// Proposal network 6-64-64-1: flat parameters W1[64][6], b1[64], W2[64][64],
+// b2[64], w3[64], b3 (row o of W1/W2 = weights into hidden unit o).
+constexpr int kOffW1 = 0, kOffB1 = 384, kOffW2 = 448, kOffB2 = 4544, kOffW3 = 4608, kOffB3 = 4672;
+constexpr int kNPar = 4673;
+constexpr int kNParPad = 4676;     // float4-aligned shared copy
+constexpr int kPartStride = 4680;  // per-CTA partial gradient + loss
 
 inline int round_up(int v, int a) { return (v + a - 1) / a * a; }
 
@@ -66,7 +76,10 @@ struct Dev {
     int32_t* T; int32_t* C;
     int32_t* gamma; int32_t* A; int32_t* delta; int32_t* order; uint8_t* sel;
     int32_t* FL; int32_t* FCNT; unsigned long long* DEACC; unsigned int* DONE;
-    uint8_t* best_x; int64_t* best_E; int32_t* flags; // flags[0] improved, [1] stale, [2] error
+    uint8_t* best_x; int64_t* best_E; int32_t* flags; // flags[0] improved, [1] stale, [2] error,
+                                                       // [3] last best replica, [4] improved in the
+                                                       // finished iteration, [5] its log slot
+    int32_t* H; float* F; float* score;
     uint32_t k0, k1; // Philox key = seed halves
 };
 
@@ -92,8 +105,10 @@ cudaError_t launch_gamma(const Dev& d, cudaStream_t s);
 // iter_dev is null the kernels use their `iter` / `rate` arguments.
 cudaError_t launch_sizes(int R, int K, int m_min, int m_max, uint32_t k0, uint32_t k1, uint32_t iter,
                          const int32_t* iter_dev, int32_t* off, int32_t* order, int32_t* queue, cudaStream_t s);
+// mode: 0 rank S' by A; 1 by d.score; 2 by d.score on even replicas.  Hit
+// counts d.H are incremented for S' when count_hits.
 cudaError_t launch_select(const Dev& d, int64_t w1, int64_t w2, int64_t w3, int K, const int32_t* off,
-                          int32_t* idx, cudaStream_t s);
+                          int32_t* idx, int mode, bool count_hits, cudaStream_t s);
 cudaError_t launch_mutate(const Dev& d, int K, const int32_t* off, double rate, uint32_t iter,
                           const int32_t* iter_dev, const double* rates, uint8_t* mask, int ldm, cudaStream_t s);
 struct AnnealArgs {
@@ -116,7 +131,9 @@ cudaError_t launch_anneal(const Dev& d, const AnnealArgs& a, cudaStream_t s);
 cudaError_t launch_limtab(const uint32_t* beta, int sweeps, const uint32_t* nlog, int* lim, cudaStream_t s);
 cudaError_t launch_compact_mask(const Dev& d, const uint8_t* mask, int ldm, cudaStream_t s);
 cudaError_t launch_apply(const Dev& d, cudaStream_t s);
-cudaError_t launch_best(const Dev& d, int64_t* trace_slot, int iter_end, int32_t* iter_dev, cudaStream_t s);
+// log_ctl (iteration end only, may be null): {entries written, capacity} of the improvement log.
+cudaError_t launch_best(const Dev& d, int64_t* trace_slot, int iter_end, int32_t* iter_dev, cudaStream_t s,
+                        int32_t* log_ctl = nullptr);
 cudaError_t launch_set_iter(int32_t* iter_dev, int t, cudaStream_t s);
 // dense refresh on the tensor cores (kernels_refresh.cu)
 cudaError_t launch_to_bf16(const void* src, bool is_signed, size_t count, void* dst, cudaStream_t s);
@@ -124,6 +141,17 @@ cudaError_t launch_refresh_mma(const void* Qb, const void* Xb, int n, int R, int
                                int splits, cudaStream_t s);
 cudaError_t launch_finish_gains(const int32_t* diag, int n, int ld, const uint8_t* X, int32_t* G, int64_t* E, int R,
                                 cudaStream_t s);
+// learned selection (kernels_mlp.cu)
+cudaError_t launch_features(const Dev& d, int t, const int32_t* iter_dev, int alpha, int c, int32_t* gmax,
+                            cudaStream_t s);
+cudaError_t launch_score(const float* F, long long rows, const void* Wb, float* out, cudaStream_t s);
+size_t mlp_partial_floats(long long batch);
+cudaError_t launch_mlp_grad(const float* F, const uint8_t* y, long long rows, long long batch, uint32_t step,
+                            uint32_t k0, uint32_t k1, const void* Wb, float pos_weight, float* partial,
+                            float* grad_out, float* loss_out, float* master, float* mom, float* vel, void* Wb_out,
+                            int adam, float lr, float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
+cudaError_t launch_round_bf16(const float* master, void* Wb, cudaStream_t s);
+cudaError_t launch_log(const Dev& d, uint8_t* prev_x, float* LF, uint8_t* LY, int32_t* lrep, cudaStream_t s);
 cudaError_t launch_compare(const int32_t* G1, const int64_t* E1, const int32_t* G2, const int64_t* E2, int n, int ld,
                            int R, int* mismatches, cudaStream_t s);
 

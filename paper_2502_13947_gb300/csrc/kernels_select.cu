@@ -8,7 +8,9 @@
 //            bitonic sort of the 64-bit keys (A desc, index asc) in shared
 //            memory, the S' mask, and a second bitonic sort of the first
 //            sum(m_k) ranks by (group, index) so that every group comes out
-//            in ascending index order (Algorithm 4's subset choice).
+//            in ascending index order (Algorithm 4's subset choice).  In the
+//            learned mode S' comes from a third sort by the network's score;
+//            the selection hit counts H are incremented for S'.
 //  k_mutate  one CTA per replica: the first L = floor((n - |S'|) r) ranked
 //            variables outside S' are candidates; candidate i flips iff its
 //            Philox word is below floor((A_i - A_min)(2^32 - 1)/(A_max - A_min)).
@@ -132,7 +134,8 @@ cudaError_t launch_sizes(int R, int K, int m_min, int m_max, uint32_t k0, uint32
 
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(1024) void k_select(Dev d, int64_t w1, int64_t w2, int64_t w3, int K,
-                                                 const int32_t* __restrict__ off, int32_t* __restrict__ idx)
+                                                 const int32_t* __restrict__ off, int32_t* __restrict__ idx, int mode,
+                                                 int32_t* __restrict__ H)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int red[33];
@@ -174,11 +177,33 @@ __global__ __launch_bounds__(1024) void k_select(Dev d, int64_t w1, int64_t w2, 
         orow[r] = r < n ? (int32_t)(keys[r] & 0xffffffffu) : 0;
         srow[r] = 0;
     }
+    // Learned selection: S' ranked by (score desc, index asc) instead; the A
+    // ranking above still orders the mutation candidates.  The score's bit
+    // pattern maps to a signed integer with the float's order (-0 below +0).
+    if (mode == 1 || (mode == 2 && (p & 1) == 0)) {
+        __syncthreads();
+        const float* sc = d.score + (size_t)p * ld;
+        for (int j = tid; j < NP; j += NT) {
+            unsigned long long key = ~0ull;
+            if (j < n) {
+                const unsigned b = __float_as_uint(sc[j]);
+                const int a = b < 0x80000000u ? (int)b : -(int)(b & 0x7fffffffu) - 1;
+                key = ((unsigned long long)(~((unsigned)a ^ 0x80000000u)) << 32) | (unsigned)j;
+            }
+            keys[j] = key;
+        }
+        __syncthreads();
+        bitonic_sort(keys, NP);
+    }
     const int base = off[p * K];
     if (tid <= K) goff[tid] = off[p * K + tid] - base;
     __syncthreads();
     const int M = goff[K];
-    for (int r = tid; r < M; r += NT) srow[(int)(keys[r] & 0xffffffffu)] = 1;
+    for (int r = tid; r < M; r += NT) {
+        const int i = (int)(keys[r] & 0xffffffffu);
+        srow[i] = 1;
+        if (H) H[(size_t)p * ld + i] += 1;
+    }
     const int NP2 = next_pow2(M > 0 ? M : 1);
     for (int r = tid; r < NP2; r += NT) {
         unsigned long long k2 = ~0ull;
@@ -195,12 +220,12 @@ __global__ __launch_bounds__(1024) void k_select(Dev d, int64_t w1, int64_t w2, 
 }
 
 cudaError_t launch_select(const Dev& d, int64_t w1, int64_t w2, int64_t w3, int K, const int32_t* off,
-                          int32_t* idx, cudaStream_t s)
+                          int32_t* idx, int mode, bool count_hits, cudaStream_t s)
 {
     const size_t sm = 8 * (size_t)next_pow2(d.n);
     cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_select<<<d.R, 1024, sm, s>>>(d, w1, w2, w3, K, off, idx);
+    k_select<<<d.R, 1024, sm, s>>>(d, w1, w2, w3, K, off, idx, mode, count_hits ? d.H : nullptr);
     note_launch(1);
     return cudaGetLastError();
 }

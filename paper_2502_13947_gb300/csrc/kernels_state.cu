@@ -203,11 +203,14 @@ cudaError_t launch_gamma(const Dev& d, cudaStream_t s)
 // ties), optional trace of all energies, and the per-iteration stale counter
 // used by the termination rule (Section 3: stop after a number of
 // consecutive iterations without a new best).
-// flags[0] = improved during this iteration, flags[1] = stale iterations.
+// flags[0] = improved during this iteration, flags[1] = stale iterations,
+// flags[3] = replica last copied into best_x, flags[4] = flags[0] of the
+// iteration just ended, flags[5] = its improvement-log slot.
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(256) void k_best(const uint8_t* __restrict__ X, int ld, const int64_t* __restrict__ E,
                                               int R, uint8_t* best_x, int64_t* best_E, int32_t* flags,
-                                              int64_t* trace_slot, int iter_end, int32_t* iter_dev)
+                                              int64_t* trace_slot, int iter_end, int32_t* iter_dev,
+                                              int32_t* log_ctl)
 {
     __shared__ long long sE[8];
     __shared__ int sP[8];
@@ -232,7 +235,7 @@ __global__ __launch_bounds__(256) void k_best(const uint8_t* __restrict__ X, int
             if (sE[w] < me || (sE[w] == me && sP[w] < mp)) { me = sE[w]; mp = sP[w]; }
         const long long cur = *best_E;
         s_win = (me < cur) ? mp : -1;
-        if (s_win >= 0) { *best_E = me; flags[0] = 1; }
+        if (s_win >= 0) { *best_E = me; flags[0] = 1; flags[3] = mp; }
     }
     __syncthreads();
     const int win = s_win;
@@ -242,14 +245,21 @@ __global__ __launch_bounds__(256) void k_best(const uint8_t* __restrict__ X, int
     if (threadIdx.x == 0 && iter_end) {
         if (trace_slot) trace_slot[R] = *best_E;
         flags[1] = flags[0] ? 0 : flags[1] + 1;
+        flags[4] = flags[0];
+        if (log_ctl && flags[0]) {  // slot of the improvement-log entry (ring buffer)
+            flags[5] = log_ctl[0] % log_ctl[1];
+            log_ctl[0] += 1;
+        }
         flags[0] = 0;
         if (iter_dev) *iter_dev += 1;  // the next replay of a captured iteration is t + 1
     }
 }
 
-cudaError_t launch_best(const Dev& d, int64_t* trace_slot, int iter_end, int32_t* iter_dev, cudaStream_t s)
+cudaError_t launch_best(const Dev& d, int64_t* trace_slot, int iter_end, int32_t* iter_dev, cudaStream_t s,
+                        int32_t* log_ctl)
 {
-    k_best<<<1, 256, 0, s>>>(d.X, d.ld, d.E, d.R, d.best_x, d.best_E, d.flags, trace_slot, iter_end, iter_dev);
+    k_best<<<1, 256, 0, s>>>(d.X, d.ld, d.E, d.R, d.best_x, d.best_E, d.flags, trace_slot, iter_end, iter_dev,
+                             log_ctl);
     note_launch(1);
     return cudaGetLastError();
 }

@@ -32,7 +32,11 @@ EXPORTS = (
     "icd2s_best_update", "icd2s_initial_pass", "icd2s_step", "icd2s_step_host", "icd2s_run", "icd2s_tables",
     "icd2s_set_timing", "icd2s_get_phase_ms", "icd2s_kernel_launches", "icd2s_apply_flips_static",
     "icd2s_set_tuning", "icd2s_get_tuning", "icd2s_autotune", "icd2s_refresh", "icd2s_get_refresh_ms",
+    "icd2s_state_run", "icd2s_mlp_create", "icd2s_mlp_destroy", "icd2s_mlp_set_weights", "icd2s_mlp_get_weights",
+    "icd2s_mlp_score", "icd2s_mlp_grad", "icd2s_mlp_train", "icd2s_state_set_mlp", "icd2s_get_features",
+    "icd2s_get_hits", "icd2s_log_enable", "icd2s_log_info", "icd2s_log_copy",
 )
+MLP_PARAMS = 4673
 PHASES = ("tabu", "select", "anneal", "apply_anneal", "mutate", "apply_mutate", "best")
 
 
@@ -48,7 +52,8 @@ class Params(C.Structure):
         ("alpha", C.c_int32), ("c", C.c_int32), ("sweeps", C.c_int32), ("T_max", C.c_double), ("T_min", C.c_double),
         ("w1", C.c_int64), ("w2", C.c_int64), ("w3", C.c_int64), ("mut_mode", C.c_int32), ("mut_rate", C.c_double),
         ("patience", C.c_int32), ("max_iters", C.c_int32), ("use_graph", C.c_int32), ("refresh_every", C.c_int32),
-        ("reserved", C.c_int32 * 6),
+        ("select_mode", C.c_int32), ("stop_at_target", C.c_int32), ("target_E", C.c_int64),
+        ("reserved", C.c_int32 * 2),
     ]
 
 
@@ -68,7 +73,13 @@ class MutateParams(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("best_E", C.c_int64), ("init_best_E", C.c_int64),
-                ("anneal_attempts", C.c_int64), ("tabu_moves", C.c_int64), ("device_ms", C.c_double)]
+                ("anneal_attempts", C.c_int64), ("tabu_moves", C.c_int64), ("device_ms", C.c_double),
+                ("ttt_ms", C.c_double), ("hit_iter", C.c_int32)]
+
+
+class TrainParams(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("pos_weight", C.c_float), ("reserved", C.c_int32 * 3)]
 
 
 _lock = threading.Lock()
@@ -121,6 +132,20 @@ def lib():
                 "icd2s_autotune": (C.c_int, [vp, P(Params), vp, vp]),
                 "icd2s_refresh": (C.c_int, [vp, i32, P(i32), vp]),
                 "icd2s_get_refresh_ms": (C.c_int, [vp, P(f64)]),
+                "icd2s_state_run": (C.c_int, [vp, P(Params), vp, vp, P(Stats), vp, vp]),
+                "icd2s_mlp_create": (C.c_int, [u64, P(vp)]),
+                "icd2s_mlp_destroy": (C.c_int, [vp]),
+                "icd2s_mlp_set_weights": (C.c_int, [vp, vp]),
+                "icd2s_mlp_get_weights": (C.c_int, [vp, vp, vp]),
+                "icd2s_mlp_score": (C.c_int, [vp, vp, i64, vp, vp]),
+                "icd2s_mlp_grad": (C.c_int, [vp, vp, vp, i64, C.c_float, vp, vp, vp]),
+                "icd2s_mlp_train": (C.c_int, [vp, vp, vp, i64, P(TrainParams), vp, vp]),
+                "icd2s_state_set_mlp": (C.c_int, [vp, vp]),
+                "icd2s_get_features": (C.c_int, [vp, vp, vp]),
+                "icd2s_get_hits": (C.c_int, [vp, vp]),
+                "icd2s_log_enable": (C.c_int, [vp, i32]),
+                "icd2s_log_info": (C.c_int, [vp, P(i32), P(i32)]),
+                "icd2s_log_copy": (C.c_int, [vp, vp, vp, vp, i32, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -267,6 +292,17 @@ def icd2s_step_host(st, p: Params, t: int, x_in=None, x_out=None, E_out=None, st
     _check(lib().icd2s_step_host(st, C.byref(p), t, _np(x_in), _np(x_out), _np(E_out), _s(stream)))
 
 
+def _run_out(st, x, E, tr, S, trace, want_S):
+    out = dict(best_x=x, best_E=int(E[0]), iters=st.iters, init_best_E=st.init_best_E,
+               anneal_attempts=st.anneal_attempts, tabu_moves=st.tabu_moves, device_ms=st.device_ms,
+               ttt_ms=st.ttt_ms, hit_iter=st.hit_iter)
+    if trace:
+        out["trace"] = tr[:st.iters]
+    if want_S:
+        out["S"] = S
+    return out
+
+
 def icd2s_run(q, p: Params, seed: int, trace: bool = False, want_S: bool = False):
     n = icd2s_qubo_size(q)
     x = np.zeros(n, np.uint8)
@@ -275,13 +311,102 @@ def icd2s_run(q, p: Params, seed: int, trace: bool = False, want_S: bool = False
     tr = np.zeros((max(p.max_iters, 1), 3 * p.z + 1), np.int64) if trace else None
     S = np.zeros((p.z, n), np.uint8) if want_S else None
     _check(lib().icd2s_run(q, C.byref(p), C.c_uint64(seed), _np(x), _np(E), C.byref(st), _np(tr), _np(S)))
-    out = dict(best_x=x, best_E=int(E[0]), iters=st.iters, init_best_E=st.init_best_E,
-               anneal_attempts=st.anneal_attempts, tabu_moves=st.tabu_moves, device_ms=st.device_ms)
-    if trace:
-        out["trace"] = tr[:st.iters]
-    if want_S:
-        out["S"] = S
-    return out
+    return _run_out(st, x, E, tr, S, trace, want_S)
+
+
+def icd2s_state_run(state, n: int, p: Params, trace: bool = False, want_S: bool = False):
+    x = np.zeros(n, np.uint8)
+    E = np.zeros(1, np.int64)
+    st = Stats()
+    tr = np.zeros((max(p.max_iters, 1), 3 * p.z + 1), np.int64) if trace else None
+    S = np.zeros((p.z, n), np.uint8) if want_S else None
+    _check(lib().icd2s_state_run(state, C.byref(p), _np(x), _np(E), C.byref(st), _np(tr), _np(S)))
+    return _run_out(st, x, E, tr, S, trace, want_S)
+
+
+# ----------------------------------------------------------------------------- learned selection
+def icd2s_mlp_create(seed: int) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().icd2s_mlp_create(C.c_uint64(seed), C.byref(h)))
+    return h
+
+
+def icd2s_mlp_destroy(m) -> None:
+    _check(lib().icd2s_mlp_destroy(m))
+
+
+def icd2s_mlp_set_weights(m, W) -> None:
+    W = np.ascontiguousarray(W, np.float32)
+    assert W.shape == (MLP_PARAMS,)
+    _check(lib().icd2s_mlp_set_weights(m, _np(W)))
+
+
+def icd2s_mlp_get_weights(m):
+    """Returns (master float32 [4673], bf16 values as float32 [4673])."""
+    a = np.zeros(MLP_PARAMS, np.float32)
+    b = np.zeros(MLP_PARAMS, np.float32)
+    _check(lib().icd2s_mlp_get_weights(m, _np(a), _np(b)))
+    return a, b
+
+
+def icd2s_mlp_score(m, F_dev: int, rows: int, score_dev: int, stream=0) -> None:
+    _check(lib().icd2s_mlp_score(m, F_dev, rows, score_dev, _s(stream)))
+
+
+def icd2s_mlp_grad(m, F_dev: int, y_dev: int, rows: int, pos_weight: float, grad_dev: int, loss_dev: int,
+                   stream=0) -> None:
+    _check(lib().icd2s_mlp_grad(m, F_dev, y_dev, rows, pos_weight, grad_dev or None, loss_dev or None, _s(stream)))
+
+
+def icd2s_mlp_train(m, F_dev: int, y_dev: int, rows: int, steps: int, batch: int, lr: float = 1e-3,
+                    beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, pos_weight: float = 1.0, stream=0):
+    """Returns the per-step mean batch losses (numpy float32 [steps])."""
+    tp = TrainParams(steps=steps, batch=batch, lr=lr, beta1=beta1, beta2=beta2, eps=eps, pos_weight=pos_weight)
+    loss = np.zeros(max(steps, 1), np.float32)
+    _check(lib().icd2s_mlp_train(m, F_dev, y_dev, rows, C.byref(tp), _np(loss), _s(stream)))
+    return loss[:steps]
+
+
+def icd2s_state_set_mlp(st, m) -> None:
+    _check(lib().icd2s_state_set_mlp(st, m))
+
+
+def icd2s_get_features(st, R: int, n: int, scores: bool = True):
+    F = np.zeros((R, n, 6), np.float32)
+    sc = np.zeros((R, n), np.float32) if scores else None
+    _check(lib().icd2s_get_features(st, _np(F), _np(sc)))
+    return F, sc
+
+
+def icd2s_get_hits(st, R: int, n: int):
+    H = np.zeros((R, n), np.int32)
+    _check(lib().icd2s_get_hits(st, _np(H)))
+    return H
+
+
+def icd2s_log_enable(st, capacity: int) -> None:
+    _check(lib().icd2s_log_enable(st, capacity))
+
+
+def icd2s_log_info(st):
+    e, c = C.c_int32(0), C.c_int32(0)
+    _check(lib().icd2s_log_info(st, C.byref(e), C.byref(c)))
+    return int(e.value), int(c.value)
+
+
+def icd2s_log_copy(st, n: int):
+    """Host copies of the stored log entries: (F [cnt][n][6], y [cnt][n], replica [cnt])."""
+    e, c = icd2s_log_info(st)
+    cnt = min(e, c)
+    F = np.zeros((max(cnt, 1), n, 6), np.float32)
+    y = np.zeros((max(cnt, 1), n), np.uint8)
+    r = np.zeros(max(cnt, 1), np.int32)
+    _check(lib().icd2s_log_copy(st, _np(F), _np(y), _np(r), 0, None))
+    return F[:cnt], y[:cnt], r[:cnt]
+
+
+def icd2s_log_copy_device(st, F_dev: int, y_dev: int, replica_dev: int = 0, stream=0) -> None:
+    _check(lib().icd2s_log_copy(st, F_dev, y_dev, replica_dev or None, 1, _s(stream)))
 
 
 def icd2s_tables(sweeps: int, T_max: float, T_min: float):

@@ -84,3 +84,28 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     with pytest.raises(I.ICD2SError) as e:
         I.icd2s_version()
     assert "missing" in str(e.value)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """sizeof/offsetof of every parameter struct, from a C probe compiled
+    against the header, equal the ctypes mirrors of the binding."""
+    structs = {"icd2s_params": I.Params, "icd2s_anneal_params": I.AnnealParams,
+               "icd2s_select_params": I.SelectParams, "icd2s_mutate_params": I.MutateParams,
+               "icd2s_stats": I.Stats, "icd2s_tuning": I.Tuning, "icd2s_train_params": I.TrainParams}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "icd2s.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got["%s size" % cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got["%s %s" % (cname, f)]) == getattr(py, f).offset, (cname, f)
