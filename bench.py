@@ -8,6 +8,7 @@ metric is spin-flip attempts of the emulated Ising machine per second of
 step time (sweeps x subQUBO size x subQUBOs per step / step time).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--workload NAME]
+  python bench.py --ttt [--ttt-seeds S] [--ttt-budget ITERS] [--ttt-instances a,b]
 
 The default workload is the Beasley-shaped instance (n = 2500, 10 % density,
 int8 entries in [-100, 100]) with 128 replicas, subQUBOs of 64, 1024 sweeps,
@@ -364,6 +365,121 @@ def run_gpu(args, w):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- time to target
+# Second metric: device-timed time to a target energy, learned / batched
+# selection against the plain method, on one GPU.  Instances are the
+# generator's dense-ish synthetic stand-ins (n = 5000 and 10 000, 50 %
+# density); the target E* of an instance is the best energy of three plain
+# runs ten times as long as the measured ones (run seeds 100-102); every
+# method then runs from seeds 0..S-1 until its best energy is <= E* or the
+# iteration budget is spent (a miss, censored at the budget).
+TTT_INSTANCES = {"n5000-d0.5": dict(n=5000, density=0.5, qseed=0),
+                 "n10000-d0.5": dict(n=10000, density=0.5, qseed=0)}
+TTT_METHODS = {  # (K, m_min, m_max, select_mode)
+    "plain": (1, 64, 64, 0),
+    "batched": (16, 32, 256, 0),
+    "learned": (1, 64, 64, 1),
+    "learned+batched": (16, 32, 256, 1),
+    "hybrid+batched": (16, 32, 256, 2),
+}
+# improvement logs of the plain method for training: shapes of the n = 64
+# dense, n = 2500 sparse and n = 5000 batched workloads, instance seeds 200+
+TTT_LOG_SHAPES = ((64, 1.0, 8, 1, 16, 16, 200), (2500, 0.1, 128, 1, 64, 64, 40), (5000, 0.5, 32, 16, 32, 256, 40))
+
+
+def ttt_params(I, n, K, m_min, m_max, mode, iters, z=32):
+    p = I.icd2s_default_params(n)
+    p.z, p.K, p.m_min, p.m_max, p.m_init = z, K, m_min, m_max, 64 if n >= 64 else n
+    p.alpha, p.c, p.sweeps, p.T_max, p.T_min = 5 * n, max(2, n // 150), 256, 2000.0, 1.0
+    p.mut_mode, p.patience, p.max_iters, p.select_mode, p.use_graph = 0, 0, iters, mode, 1
+    return p
+
+
+def ttt_train(I, torch, steps=3000, batch=8192, runs=4):
+    """Collects improvement logs of plain runs and trains the network on the GPU."""
+    Fs, ys, entries = [], [], 0
+    for (n, rho, z, K, m_min, m_max, iters) in TTT_LOG_SHAPES:
+        for r in range(runs):
+            q = I.icd2s_qubo_create(make_qubo(n, rho, 200 + r))
+            p = ttt_params(I, n, K, m_min, m_max, 0, iters, z=z)
+            p.m_init = min(m_max, 64)
+            st = I.icd2s_state_create(q, z, 200 + r)
+            I.icd2s_log_enable(st, 512)
+            I.icd2s_state_run(st, n, p)
+            e, cap = I.icd2s_log_info(st)
+            cnt = min(e, cap)
+            if cnt:
+                F = torch.empty((cnt, n, 6), dtype=torch.float32, device="cuda")
+                y = torch.empty((cnt, n), dtype=torch.uint8, device="cuda")
+                I.icd2s_log_copy_device(st, F.data_ptr(), y.data_ptr())
+                Fs.append(F.reshape(-1, 6))
+                ys.append(y.reshape(-1))
+                entries += cnt
+            I.icd2s_state_destroy(st)
+            I.icd2s_qubo_destroy(q)
+    F = torch.cat(Fs).contiguous()
+    y = torch.cat(ys).contiguous()
+    pos = float(y.float().mean())
+    pw = (1.0 - pos) / max(pos, 1e-9)
+    m = I.icd2s_mlp_create(1)
+    losses = I.icd2s_mlp_train(m, F.data_ptr(), y.data_ptr(), F.shape[0], steps=steps, batch=batch, lr=2e-3,
+                               pos_weight=pw)
+    info = dict(entries=entries, rows=int(F.shape[0]), positive_rate=round(pos, 5), pos_weight=round(pw, 3),
+                steps=steps, batch=batch, loss_first=round(float(losses[:20].mean()), 4),
+                loss_last=round(float(losses[-20:].mean()), 4))
+    return m, info
+
+
+def run_ttt(args):
+    import torch
+    from paper_2502_13947_gb300 import icd2s as I
+    if not torch.cuda.is_available():
+        raise SystemExit("time-to-target needs a CUDA GPU")
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    mlp, train_info = ttt_train(I, torch)
+    results = {}
+    for name in args.ttt_instances.split(","):
+        spec = TTT_INSTANCES[name]
+        n = spec["n"]
+        q = I.icd2s_qubo_create(make_qubo(n, spec["density"], spec["qseed"]))
+        longs = []
+        for s in (100, 101, 102):
+            r = I.icd2s_run(q, ttt_params(I, n, 1, 64, 64, 0, 10 * args.ttt_budget), s)
+            longs.append(r["best_E"])
+        E_star = min(longs)
+        res = dict(target_E=E_star, target_runs=longs, budget_iters=args.ttt_budget)
+        for meth, (K, m_min, m_max, mode) in TTT_METHODS.items():
+            per = []
+            for seed in range(args.ttt_seeds):
+                p = ttt_params(I, n, K, m_min, m_max, mode, args.ttt_budget)
+                p.stop_at_target, p.target_E = 1, E_star
+                st = I.icd2s_state_create(q, p.z, seed)
+                if mode:
+                    I.icd2s_state_set_mlp(st, mlp)
+                r = I.icd2s_state_run(st, n, p)
+                I.icd2s_state_destroy(st)
+                per.append(dict(seed=seed, hit_iter=r["hit_iter"], ttt_ms=round(r["ttt_ms"], 2), best_E=r["best_E"],
+                                ms_per_iter=round(r["device_ms"] / max(r["iters"], 1), 2)))
+            hits = [x["ttt_ms"] for x in per if x["hit_iter"] >= 0]
+            cens = sorted(hits + [float("inf")] * (len(per) - len(hits)))
+            med = cens[len(cens) // 2] if len(cens) % 2 else 0.5 * (cens[len(cens) // 2 - 1] + cens[len(cens) // 2])
+            res[meth] = dict(median_ttt_ms=None if med == float("inf") else round(med, 2),
+                             success=len(hits), runs=len(per),
+                             mean_ms_per_iter=round(statistics.mean(x["ms_per_iter"] for x in per), 2),
+                             per_seed=per)
+        I.icd2s_qubo_destroy(q)
+        results[name] = res
+    I.icd2s_mlp_destroy(mlp)
+    line = {"metric": "time-to-target energy", "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+            "data": "synthetic", "dtype": "int32/int64 (network: bf16 weights, f32)",
+            "config": {"workload": "time-to-target, z=32, alpha=5n, c=n/150, 256 sweeps, T 2000->1, Eq. 5 mutation",
+                       "methods": {k: dict(K=v[0], m_min=v[1], m_max=v[2], select_mode=v[3])
+                                   for k, v in TTT_METHODS.items()}},
+            "train": train_info, "results": results, "wall_s": round(time.time() - t0, 1)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,9 +489,15 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-refresh", action="store_true", help="skip the dense tensor-core refresh measurement")
+    ap.add_argument("--ttt", action="store_true", help="time to target: learned / batched vs plain selection")
+    ap.add_argument("--ttt-seeds", type=int, default=10)
+    ap.add_argument("--ttt-budget", type=int, default=30, help="outer iterations per measured run")
+    ap.add_argument("--ttt-instances", default="n5000-d0.5,n10000-d0.5")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
-    if args.impl == "reference":
+    if args.ttt:
+        run_ttt(args)
+    elif args.impl == "reference":
         run_reference(args, w)
     else:
         run_gpu(args, w)
