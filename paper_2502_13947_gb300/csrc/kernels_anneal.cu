@@ -21,17 +21,25 @@
 // gains this is l_b <= LIM[k][u >> 20] with LIM[k][j] = floor((NLOG[j] - 1) /
 // BETA[k]) (0 when NLOG[j] = 0, unbounded when BETA[k] = 0): a per-schedule
 // table built once on the device (k_limtab), so an attempt costs one
-// L1-resident load and one compare.  A sweep runs as "first accept"
-// rounds: every lane tests its positions at or after the current one
-// against the current gains, P ballots (masked by warp-uniform "not yet
-// visited" lane masks) locate the first accepted position,
-// that flip is applied (each lane updates its gains from one P-byte row
-// segment of Q'), and the scan resumes just after it.  Positions before the
-// first accept would have been tested with exactly these gains by a
-// one-at-a-time sweep, so the trajectory is identical to the sequential one;
-// a sweep costs (accepts + 1) rounds instead of m dependent steps.  Each
-// lane draws one Philox block per owned position every 4 sweeps, so no
-// random words are wasted or exchanged.
+// L1-resident load and one compare.  Each lane draws one Philox block per
+// owned position every 4 sweeps, so no random words are wasted or exchanged.
+//
+// A sweep runs as rounds.  In a round every lane tests its unvisited
+// positions against the current gains (P ballots).  For m <= 128 the warp
+// also knows which positions are coupled (Q'_ab != 0; one bit mask per owned
+// position, built from ballots during the gather): a tentative decision is
+// final unless the position is coupled to an earlier tentatively accepted
+// one, so the round ends at the first such position and every accept before
+// it is applied -- those accepts are pairwise uncoupled, hence the gains each
+// of them and every rejected position saw are exactly the gains of a
+// one-at-a-time sweep.  For m > 128 a round ends at the first accept.  A
+// sweep of a sparse subQUBO thus costs far fewer rounds than accepts; the
+// trajectory is the sequential one bit for bit either way.
+//
+// Lanes keep the sign-free field h_b = (1 - 2 x_b) l_b: a flip of a adds
+// 2 Q'_ab (1 - 2 x_a) to every h_b (one multiply-add with a warp-uniform
+// factor, two rows per step so the shared-memory loads overlap) and only
+// negates the sign of a itself.
 //
 // Output: the changed positions, either as a 0/1 mask [R][ldm] or appended
 // to the replica's flip list (index | old x << 31) for k_apply; and the
@@ -86,7 +94,16 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
         valid[q] = b < m;
         col[q] = valid[q] ? (S ? __ldg(S + b) : a.block_base + b) : 0;
     }
-    // gather Q[S, S] into the permuted layout, diagonal as 0
+    // gather Q[S, S] into the permuted layout, diagonal as 0; for P <= 4 also
+    // the coupling masks of the owned positions: bit L of nz[q][q2] is set
+    // iff Q'[lane + 32 q][L + 32 q2] != 0 (ballots over the row's columns,
+    // kept by the row's owner)
+    constexpr bool kSparse = P <= 4;
+    unsigned nz[kSparse ? P : 1][kSparse ? P : 1];
+#pragma unroll
+    for (int q = 0; q < (kSparse ? P : 1); ++q)
+#pragma unroll
+        for (int q2 = 0; q2 < (kSparse ? P : 1); ++q2) nz[q][q2] = 0u;
 #pragma unroll 4
     for (int r = 0; r < m; ++r) {
         const int ir = S ? __ldg(S + r) : a.block_base + r;
@@ -99,10 +116,25 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
             packed |= (Seg)v << (8 * q);
         }
         *reinterpret_cast<Seg*>(Qs + (size_t)r * MC + lane * P) = packed;
+        if constexpr (kSparse) {
+            const bool owner = lane == (r & 31);
+#pragma unroll
+            for (int q2 = 0; q2 < P; ++q2) {
+                const unsigned bm = __ballot_sync(0xffffffffu, ((packed >> (8 * q2)) & 0xff) != 0);
+#pragma unroll
+                for (int q = 0; q < P; ++q) nz[q][q2] = (owner && (r >> 5) == q) ? bm : nz[q][q2];
+            }
+        }
     }
     __syncwarp();
 
-    int l[P], sg[P];       // gains and signs 1 - 2 x of the owned positions
+    // Owned positions keep the sign-free field h = (1 - 2x) l (l the gain) and
+    // the sign sg = 1 - 2x, so l = sg h.  A flip of position a changes the
+    // field of every other position b by 2 Q'_ab (1 - 2 x_a) -- one
+    // multiply-add per owned position with a warp-uniform factor -- and leaves
+    // its own field alone (Q'_aa is stored as 0); the flipped position only
+    // changes its sign.
+    int h[P], sg[P];
     unsigned X[P];         // warp-uniform: bit lane of X[q] = x at position lane + 32 q
     const int32_t* grow = d.G + (size_t)p * ld;
     const uint8_t* xrow = d.X + (size_t)p * ld;
@@ -110,8 +142,8 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
 #pragma unroll
     for (int q = 0; q < P; ++q) {
         const int xv = valid[q] ? (int)xrow[col[q]] : 0;
-        l[q] = valid[q] ? grow[col[q]] : 0;
         sg[q] = 1 - 2 * xv;
+        h[q] = valid[q] ? sg[q] * grow[col[q]] : 0;
         x0 |= (unsigned)xv << q;
         X[q] = __ballot_sync(0xffffffffu, xv != 0);
     }
@@ -133,6 +165,35 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
             }
         }
     };
+    // field updates of the flips of the positions in the warp-uniform mask A
+    // of column block qf (all before their sign changes), two rows at a time
+    // so that the shared-memory loads overlap
+    auto apply_fields = [&](unsigned A, int qf) {
+        while (A) {
+            const int L1 = __ffs(A) - 1;
+            A &= A - 1u;
+            const bool two = A != 0u;
+            const int L2 = two ? __ffs(A) - 1 : L1;
+            A = two ? (A & (A - 1u)) : A;
+            const Seg s1 = *reinterpret_cast<const Seg*>(Qs + (size_t)(L1 + 32 * qf) * MC + lane * P);
+            const Seg s2 = *reinterpret_cast<const Seg*>(Qs + (size_t)(L2 + 32 * qf) * MC + lane * P);
+            const int f1 = ((X[qf] >> L1) & 1u) ? -2 : 2;
+            const int f2 = two ? (((X[qf] >> L2) & 1u) ? -2 : 2) : 0;
+#pragma unroll
+            for (int q = 0; q < P; ++q)
+                h[q] += f1 * (int)(int8_t)(uint8_t)(s1 >> (8 * q)) + f2 * (int)(int8_t)(uint8_t)(s2 >> (8 * q));
+        }
+    };
+    // sign changes (and accepted gains) of the flipped positions in A[q]
+    auto flip_signs = [&](const unsigned (&A)[P]) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const bool f = (A[q] >> lane) & 1u;
+            dE += f ? sg[q] * h[q] : 0;
+            sg[q] = f ? -sg[q] : sg[q];
+            X[q] ^= A[q];
+        }
+    };
     int limA[4][P];
     load_limits(0, limA);
     for (int k4 = 0; k4 < a.sweeps; k4 += 4) {
@@ -149,33 +210,71 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
                 lim[q] = limA[r][q];
                 M[q] = 0xffffffffu;
             }
-            while (true) {
-                unsigned B[P];
+            if constexpr (kSparse) {
+                // Rounds of several accepts: the tentative decisions of all
+                // unvisited positions are taken against the current gains; a
+                // position's decision is final unless it is coupled to an
+                // earlier tentatively accepted position (whose flip would
+                // change its gain).  The first such position ends the round:
+                // the accepts before it are pairwise uncoupled, so applying
+                // them in any order gives exactly the gains a one-at-a-time
+                // sweep sees.
+                const unsigned below = (1u << lane) - 1u;
+                while (true) {
+                    unsigned B[P], any = 0u;
 #pragma unroll
-                for (int q = 0; q < P; ++q) B[q] = __ballot_sync(0xffffffffu, l[q] <= lim[q]) & M[q];
-                int qs = -1;
-                unsigned bq = 0u, xq = 0u;
+                    for (int q = 0; q < P; ++q) {
+                        B[q] = __ballot_sync(0xffffffffu, sg[q] * h[q] <= lim[q]) & M[q];
+                        any |= B[q];
+                    }
+                    if (!any) break;
+                    unsigned Cf[P];
 #pragma unroll
-                for (int q = P - 1; q >= 0; --q)
-                    if (B[q]) { qs = q; bq = B[q]; xq = X[q]; }
-                if (qs < 0) break;
-                const int L = __ffs(bq) - 1;
-                const int si2 = ((xq >> L) & 1u) ? -2 : 2;
-                const Seg seg = *reinterpret_cast<const Seg*>(Qs + (size_t)(L + 32 * qs) * MC + lane * P);
-                const bool own = lane == L;  // selects, not a branch: no reconvergence per round
+                    for (int q = 0; q < P; ++q) {
+                        unsigned c = nz[q][q] & B[q] & below;
 #pragma unroll
-                for (int q = 0; q < P; ++q) {
-                    const bool me = own && q == qs;
-                    const int qv = (int)(int8_t)(uint8_t)(seg >> (8 * q));
-                    const int upd = l[q] + qv * (si2 * sg[q]);  // the flipped position adds Q'_ii = 0
-                    dE += me ? l[q] : 0;
-                    l[q] = me ? -l[q] : upd;
-                    sg[q] = me ? -sg[q] : sg[q];
+                        for (int q2 = 0; q2 < q; ++q2) c |= nz[q][q2] & B[q2];
+                        Cf[q] = __ballot_sync(0xffffffffu, c != 0u) & M[q];
+                    }
+                    int qc = P, Lc = 0;
+#pragma unroll
+                    for (int q = P - 1; q >= 0; --q)
+                        if (Cf[q]) { qc = q; Lc = __ffs(Cf[q]) - 1; }
+                    unsigned A[P];
+#pragma unroll
+                    for (int q = 0; q < P; ++q) {
+                        A[q] = q < qc ? B[q] : (q == qc ? (B[q] & ((1u << Lc) - 1u)) : 0u);
+                        apply_fields(A[q], q);
+                    }
+                    flip_signs(A);
+                    if (qc == P) break;  // every remaining decision was final
+#pragma unroll
+                    for (int q = 0; q < P; ++q)
+                        M[q] = q < qc ? 0u : (q == qc ? (M[q] & (0xffffffffu << Lc)) : M[q]);
                 }
+            } else {
+                // one accept per round: the first accepted unvisited position
+                while (true) {
+                    unsigned B[P];
 #pragma unroll
-                for (int q = 0; q < P; ++q) {
-                    if (q == qs) X[q] ^= 1u << L;
-                    M[q] = q < qs ? 0u : (q == qs ? (M[q] & (0xfffffffeu << L)) : M[q]);
+                    for (int q = 0; q < P; ++q) B[q] = __ballot_sync(0xffffffffu, sg[q] * h[q] <= lim[q]) & M[q];
+                    int qs = -1;
+                    unsigned bq = 0u;
+#pragma unroll
+                    for (int q = P - 1; q >= 0; --q)
+                        if (B[q]) { qs = q; bq = B[q]; }
+                    if (qs < 0) break;
+                    const int L = __ffs(bq) - 1;
+                    unsigned A[P];
+#pragma unroll
+                    for (int q = 0; q < P; ++q) {
+                        A[q] = q == qs ? (1u << L) : 0u;
+                        if (q == qs) apply_fields(A[q], q);
+                    }
+                    flip_signs(A);
+#pragma unroll
+                    for (int q = 0; q < P; ++q)
+                        M[q] = q < qs ? 0u : (q == qs ? (M[q] & (0xfffffffeu << L)) : M[q]);
                 }
             }
         }
