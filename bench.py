@@ -13,8 +13,8 @@ step time (sweeps x subQUBO size x subQUBOs per step / step time).
 The default workload is the Beasley-shaped instance (n = 2500, 10 % density,
 int8 entries in [-100, 100]) with 128 replicas, subQUBOs of 64, 1024 sweeps,
 alpha = 5n, c = 16 and a 1 % mutation rate.  Inputs are resident in HBM when
-the timed region starts; L2 is flushed (256 MiB write) before every timed
-step, outside the step's events.  `--impl reference` times the CPU oracle
+the timed region starts; L2 is flushed (a 256 MiB write, then a 256 MiB
+read) before every timed step, outside the step's events.  `--impl reference` times the CPU oracle
 (single thread, as it stands) on a bounded sample of the same workload.
 Under torchrun every rank solves its own instance (independent problems,
 weak scaling, no collective on the data path); rank 0 prints one JSON line.
@@ -46,6 +46,21 @@ DEFAULT_WORKLOAD = "beasley-like-n2500-d0.1-m64-z128"
 METRIC = "spin-flip attempts/s"
 UNIT = "attempts/s"
 L2_FLUSH_BYTES = 256 << 20
+
+
+class L2Flush:
+    """Flushes the L2 between timed iterations: writes a buffer larger than L2,
+    then reads another one, so the timed work starts with clean lines (the
+    write alone would leave ~L2-size dirty lines whose write-back the next
+    kernel would pay for)."""
+
+    def __init__(self, torch):
+        self.w = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        self.r = torch.zeros(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def __call__(self):
+        self.w.zero_()
+        self.r.max()
 
 
 def attempts_per_step(w):
@@ -186,7 +201,7 @@ def measure_refresh(I, torch, peaks, stream, flush, reps=10):
         mma, whole = [], []
         for _ in range(reps):
             with torch.cuda.stream(stream):
-                flush.zero_()
+                flush()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -211,7 +226,79 @@ def measure_refresh(I, torch, peaks, stream, flush, reps=10):
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst: the kernel is timed alone)"}
 
 
+APPLY_WORKLOAD = dict(name="gain-update-n16384-R16-disjoint1024", n=16384, density=1.0, qseed=5, R=16)
+
+
+def measure_apply(I, torch, peaks, stream, flush, reps=10):
+    """The exact gain write-back (icd2s_apply_flips_update_gains) streaming
+    every row of Q once: n = 16 384, 16 replicas, replica p flips the 1024
+    variables i = p (mod 16), so the flip sets are disjoint and no row is
+    reused (Q is 268 MB, twice the L2).  The kernel time comes from CUDA
+    events the library records around the write-back kernel on the launching
+    stream; call_ms adds the mask compaction (events around the call); L2 is
+    flushed before each call."""
+    w = APPLY_WORKLOAD
+    n, R = w["n"], w["R"]
+    Q = make_qubo(n, w["density"], w["qseed"])
+    q = I.icd2s_qubo_create(Q)
+    del Q
+    st = I.icd2s_state_create(q, R, 3)
+    sp = stream.cuda_stream
+    mask = np.zeros((R, n), np.uint8)
+    for p in range(R):
+        mask[p, p::R] = 1
+    mask_d = torch.from_numpy(mask).cuda()
+    ms, kms = [], []
+    try:
+        I.icd2s_set_timing(st, True)
+        with torch.cuda.stream(stream):
+            I.icd2s_apply_flips_update_gains(st, mask_d.data_ptr(), sp)   # warm-up
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                I.icd2s_apply_flips_update_gains(st, mask_d.data_ptr(), sp)
+                e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            kms.append(I.icd2s_get_apply_ms(st))
+    finally:
+        I.icd2s_state_destroy(st)
+        I.icd2s_qubo_destroy(q)
+    ld = (n + 127) // 128 * 128
+    flips = int(mask.sum())
+    # per (replica, flip): the flipped row of Q (ld bytes streamed); per
+    # replica: the mask row, g read + written, x read + written
+    nbytes = flips * ld + R * (n + 8 * ld + 2 * ld)
+    t = sum(kms) / len(kms)
+    tc = sum(ms) / len(ms)
+    gbs = nbytes / (t / 1000.0) / 1e9
+    return {"kernel": "k_apply", "workload": w["name"], "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "traffic": ncu_traffic("kernels_update.cu", "k_apply"),
+            "algorithmic_bytes_per_launch": nbytes, "launch_ms": t, "call_ms": tc,
+            "call_frac": nbytes / (tc / 1000.0) / 1e9 / peaks["hbm_gbs"],
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst: the call is timed alone)"}
+
+
 # ----------------------------------------------------------------------------- GPU arm
+def run_only(args):
+    """One measurement alone (for profiling commands): --only apply|refresh."""
+    import torch
+
+    from paper_2502_13947_gb300 import build as B
+    from paper_2502_13947_gb300 import icd2s as I
+    torch.cuda.set_device(0)
+    if not B.up_to_date():
+        B.build()
+    peaks, _ = measured_peaks()
+    stream = torch.cuda.Stream()
+    flush = L2Flush(torch)
+    fn = measure_apply if args.only == "apply" else measure_refresh
+    print(json.dumps(fn(I, torch, peaks, stream, flush, reps=args.steps)), flush=True)
+
+
 def run_gpu(args, w):
     import torch
     import torch.distributed as dist
@@ -243,7 +330,7 @@ def run_gpu(args, w):
     st = I.icd2s_state_create(q, z, 7 + rank)
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = L2Flush(torch)
     with torch.cuda.stream(stream):
         I.icd2s_initial_pass(st, p, sp)
         I.icd2s_best_update(st, sp)
@@ -265,7 +352,7 @@ def run_gpu(args, w):
     launches0 = I.icd2s_kernel_launches()
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
-            flush.zero_()                       # L2 flush, outside the step's events
+            flush()                             # L2 flush, outside the step's events
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -320,6 +407,7 @@ def run_gpu(args, w):
 
     peaks, peak_src = measured_peaks()
     refresh = None if args.no_refresh else measure_refresh(I, torch, peaks, stream, flush)
+    apply_rf = None if args.no_refresh else measure_apply(I, torch, peaks, stream, flush)
     K = args.steps
     phase_avg = {k: v / K for k, v in phase_tot.items()}
     ld = (n + 127) // 128 * 128
@@ -349,9 +437,10 @@ def run_gpu(args, w):
                    "m_min": w["m_min"], "m_max": w["m_max"], "sweeps": w["sweeps"], "alpha": w["alpha"],
                    "c": w["c"], "mutation_rate": w["mut_rate"], "T_max": w["T_max"], "T_min": w["T_min"],
                    "attempts_per_step": att, "parallelism": "independent instance per GPU" if world > 1 else "1 GPU",
-                   "l2": "flushed before every timed step (256 MiB write outside the step events)"},
+                   "l2": "flushed before every timed step (256 MiB write + 256 MiB read, outside the step events)"},
         "roofline": roofline,
         "roofline_refresh": refresh,
+        "roofline_apply": apply_rf,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": z * n, "d2h_bytes_per_step": z * n + 8 * z,
                 "steps": e2e_steps, "api": "icd2s_step_host"},
@@ -488,14 +577,18 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-refresh", action="store_true", help="skip the dense tensor-core refresh measurement")
+    ap.add_argument("--no-refresh", action="store_true",
+                    help="skip the tensor-core refresh and the write-back roofline measurements")
+    ap.add_argument("--only", choices=["apply", "refresh"], help="run one kernel measurement alone (profiling)")
     ap.add_argument("--ttt", action="store_true", help="time to target: learned / batched vs plain selection")
     ap.add_argument("--ttt-seeds", type=int, default=10)
     ap.add_argument("--ttt-budget", type=int, default=30, help="outer iterations per measured run")
     ap.add_argument("--ttt-instances", default="n5000-d0.5,n10000-d0.5")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
-    if args.ttt:
+    if args.only:
+        run_only(args)
+    elif args.ttt:
         run_ttt(args)
     elif args.impl == "reference":
         run_reference(args, w)

@@ -345,6 +345,9 @@ int icd2s_get_phase_ms(icd2s_state* st, double* ms);
 /* With timing enabled: duration (ms) of the tensor-core kernel of the last
  * icd2s_refresh. */
 int icd2s_get_refresh_ms(icd2s_state* st, double* ms);
+/* With timing enabled: duration (ms) of the write-back kernel (without the
+ * mask compaction) of the last icd2s_apply_flips_update_gains. */
+int icd2s_get_apply_ms(icd2s_state* st, double* ms);
 
 /* Kernel variants used by a state (launch configuration only: every variant
  * computes the same results bit for bit).  tabu_variant indexes the Tabu

@@ -153,12 +153,15 @@ struct icd2s_state {
     void* Xb = nullptr; int32_t* G2 = nullptr; int64_t* E2 = nullptr; int* rflags = nullptr;  // [0] timeout, [1] mismatches
     cudaEvent_t rev[2] = {};  // around the tensor-core kernel of the last refresh (when timing)
     bool timed_refresh = false;
+    cudaEvent_t aev[2] = {};  // around the write-back kernel of the last apply_flips_update_gains
+    bool timed_apply = false;
     // phase timing of icd2s_step: events [2 * phase] / [2 * phase + 1]
     bool timing = false, timed_step = false;
     cudaEvent_t ev[2 * ICD2S_PHASES] = {};
     unsigned long long graph_kernels = 0;  // kernels in one replay of the captured step
     // learned selection
     int32_t* H = nullptr;                    // [R][ld] hit counts
+    int32_t* ACC = nullptr; unsigned* TT = nullptr;  // split write-back: partial-sum planes, tile tickets
     float* F = nullptr; float* score = nullptr; int32_t* gmax = nullptr;  // made on first use
     bool have_features = false, have_scores = false;
     icd2s_mlp* mlp = nullptr;                // borrowed
@@ -180,7 +183,8 @@ static void free_state(icd2s_state* st)
                     st->FL, st->FCNT, st->DEACC, st->DONE, st->best_x, st->best_E, st->flags, st->idx,
                     st->off, st->scratch, st->counters, st->nlog, st->beta, st->limtab,
                     st->lpt, st->queue, st->ctx, st->rates, st->Xb, st->G2, st->E2, st->rflags,
-                    st->H, st->F, st->score, st->gmax, st->LF, st->LY, st->lrep, st->prev_x, st->log_ctl};
+                    st->H, st->F, st->score, st->gmax, st->LF, st->LY, st->lrep, st->prev_x, st->log_ctl,
+                    st->ACC, st->TT};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (st->graph) cudaGraphExecDestroy(st->graph);
@@ -189,6 +193,8 @@ static void free_state(icd2s_state* st)
     for (cudaEvent_t e : st->ev)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : st->rev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : st->aev)
         if (e) cudaEventDestroy(e);
     delete st;
 }
@@ -397,6 +403,7 @@ int icd2s_state_create(icd2s_qubo* q, int32_t replicas, uint64_t seed, icd2s_sta
     ALLOC(DEACC, replicas); ALLOC(DONE, replicas); ALLOC(best_x, q->ld); ALLOC(best_E, 1); ALLOC(flags, 8);
     ALLOC(idx, RL); ALLOC(off, (size_t)replicas * 64 + 1); ALLOC(scratch, RL); ALLOC(counters, 4);
     ALLOC(nlog, 4096); ALLOC(lpt, (size_t)replicas * 64); ALLOC(queue, 4); ALLOC(ctx, 4); ALLOC(H, RL);
+    ALLOC(ACC, RL * apply_splits_for(q->ld, replicas)); ALLOC(TT, (size_t)replicas * apply_tiles(q->ld));
 #undef ALLOC
     if (e != cudaSuccess) {
         free_state(st);
@@ -408,6 +415,7 @@ int icd2s_state_create(icd2s_qubo* q, int32_t replicas, uint64_t seed, icd2s_sta
     d.delta = st->delta; d.order = st->order; d.sel = st->sel; d.FL = st->FL; d.FCNT = st->FCNT;
     d.DEACC = st->DEACC; d.DONE = st->DONE; d.best_x = st->best_x; d.best_E = st->best_E; d.flags = st->flags;
     d.H = st->H;
+    d.ACC = st->ACC; d.TT = st->TT; d.apply_splits = apply_splits_for(q->ld, replicas);
     d.k0 = (uint32_t)(seed & 0xffffffffu); d.k1 = (uint32_t)(seed >> 32);
     uint32_t nl[4096];
     make_nlog(nl);
@@ -417,7 +425,8 @@ int icd2s_state_create(icd2s_qubo* q, int32_t replicas, uint64_t seed, icd2s_sta
         (e = cudaMemset(st->FCNT, 0, replicas * 4)) != cudaSuccess ||
         (e = cudaMemset(st->DEACC, 0, replicas * 8)) != cudaSuccess ||
         (e = cudaMemset(st->DONE, 0, replicas * 4)) != cudaSuccess || (e = cudaMemset(st->flags, 0, 32)) != cudaSuccess ||
-        (e = cudaMemset(st->H, 0, RL * 4)) != cudaSuccess ||
+        (e = cudaMemset(st->H, 0, RL * 4)) != cudaSuccess || 
+        (e = cudaMemset(st->TT, 0, sizeof(unsigned) * replicas * apply_tiles(q->ld))) != cudaSuccess ||
         (e = cudaMemset(st->counters, 0, 32)) != cudaSuccess || (e = cudaMemset(st->best_x, 0, q->ld)) != cudaSuccess ||
         (e = cudaMemcpy(st->best_E, &big, 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(st->nlog, nl, sizeof nl, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -590,7 +599,15 @@ int icd2s_apply_flips_update_gains(icd2s_state* st, const uint8_t* flips_dev, vo
     REQ(st && flips_dev, ICD2S_ERR_ARG, "NULL argument");
     cudaStream_t s = S(stream);
     CK(launch_compact_mask(st->d, flips_dev, st->q->n, s));
+    if (st->timing) {
+        if (!st->aev[0]) for (cudaEvent_t& e : st->aev) CK(cudaEventCreate(&e));
+        CK(cudaEventRecord(st->aev[0], s));
+    }
     CK(launch_apply(st->d, s));
+    if (st->timing) {
+        CK(cudaEventRecord(st->aev[1], s));
+        st->timed_apply = true;
+    }
     return ICD2S_OK;
 }
 
@@ -837,6 +854,18 @@ int icd2s_get_refresh_ms(icd2s_state* st, double* ms)
     CK(cudaEventSynchronize(st->rev[1]));
     float f = 0.f;
     CK(cudaEventElapsedTime(&f, st->rev[0], st->rev[1]));
+    *ms = f;
+    return ICD2S_OK;
+}
+
+int icd2s_get_apply_ms(icd2s_state* st, double* ms)
+{
+    REQ(st && ms, ICD2S_ERR_ARG, "NULL argument");
+    REQ(st->timed_apply, ICD2S_ERR_STATE,
+        "no timed write-back: enable icd2s_set_timing, then call icd2s_apply_flips_update_gains");
+    CK(cudaEventSynchronize(st->aev[1]));
+    float f = 0.f;
+    CK(cudaEventElapsedTime(&f, st->aev[0], st->aev[1]));
     *ms = f;
     return ICD2S_OK;
 }

@@ -14,6 +14,7 @@
 //   order  int32 [R][LD]       variables ranked by (A desc, index asc)
 //   sel    uint8 [R][LD]       1 where the variable is in S' (last selection)
 //   FL     int32 [R][LD]       flip lists: index | (old x << 31), FCNT[R] entries
+//   ACC    int32 [S][R][LD]    partial sums of a split write-back (one plane per split)
 //   H      int32 [R][LD]       selection hit counts (Ising-machine calls that included j)
 //   F      float [R][LD][6]    features of the learned selection at selection time
 //   score  float [R][LD]       proposal-network scores
@@ -80,6 +81,7 @@ struct Dev {
                                                        // [3] last best replica, [4] improved in the
                                                        // finished iteration, [5] its log slot
     int32_t* H; float* F; float* score;
+    int32_t* ACC; unsigned* TT; int apply_splits;     // split write-back: partial sums, tile tickets
     uint32_t k0, k1; // Philox key = seed halves
 };
 
@@ -131,6 +133,8 @@ cudaError_t launch_anneal(const Dev& d, const AnnealArgs& a, cudaStream_t s);
 cudaError_t launch_limtab(const uint32_t* beta, int sweeps, const uint32_t* nlog, int* lim, cudaStream_t s);
 cudaError_t launch_compact_mask(const Dev& d, const uint8_t* mask, int ldm, cudaStream_t s);
 cudaError_t launch_apply(const Dev& d, cudaStream_t s);
+int apply_splits_for(int ld, int R);   // CTAs per column tile for long flip lists
+int apply_tiles(int ld);
 // log_ctl (iteration end only, may be null): {entries written, capacity} of the improvement log.
 cudaError_t launch_best(const Dev& d, int64_t* trace_slot, int iter_end, int32_t* iter_dev, cudaStream_t s,
                         int32_t* log_ctl = nullptr);

@@ -34,7 +34,7 @@ EXPORTS = (
     "icd2s_set_tuning", "icd2s_get_tuning", "icd2s_autotune", "icd2s_refresh", "icd2s_get_refresh_ms",
     "icd2s_state_run", "icd2s_mlp_create", "icd2s_mlp_destroy", "icd2s_mlp_set_weights", "icd2s_mlp_get_weights",
     "icd2s_mlp_score", "icd2s_mlp_grad", "icd2s_mlp_train", "icd2s_state_set_mlp", "icd2s_get_features",
-    "icd2s_get_hits", "icd2s_log_enable", "icd2s_log_info", "icd2s_log_copy",
+    "icd2s_get_hits", "icd2s_log_enable", "icd2s_log_info", "icd2s_log_copy", "icd2s_get_apply_ms",
 )
 MLP_PARAMS = 4673
 PHASES = ("tabu", "select", "anneal", "apply_anneal", "mutate", "apply_mutate", "best")
@@ -132,6 +132,7 @@ def lib():
                 "icd2s_autotune": (C.c_int, [vp, P(Params), vp, vp]),
                 "icd2s_refresh": (C.c_int, [vp, i32, P(i32), vp]),
                 "icd2s_get_refresh_ms": (C.c_int, [vp, P(f64)]),
+                "icd2s_get_apply_ms": (C.c_int, [vp, P(f64)]),
                 "icd2s_state_run": (C.c_int, [vp, P(Params), vp, vp, P(Stats), vp, vp]),
                 "icd2s_mlp_create": (C.c_int, [u64, P(vp)]),
                 "icd2s_mlp_destroy": (C.c_int, [vp]),
@@ -474,6 +475,12 @@ def icd2s_refresh(st, rebuild: bool = False, stream=0) -> int:
 def icd2s_get_refresh_ms(st) -> float:
     ms = C.c_double(0.0)
     _check(lib().icd2s_get_refresh_ms(st, C.byref(ms)))
+    return float(ms.value)
+
+
+def icd2s_get_apply_ms(st) -> float:
+    ms = C.c_double(0.0)
+    _check(lib().icd2s_get_apply_ms(st, C.byref(ms)))
     return float(ms.value)
 
 
