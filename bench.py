@@ -68,6 +68,19 @@ def attempts_per_step(w):
     return w["z"] * w["K"] * w["sweeps"] * (w["m_min"] + w["m_max"]) // 2
 
 
+def max_over_ranks(dist, torch, seconds_or_ms, device):
+    """The slowest rank's time (every rank gets it)."""
+    tt = torch.tensor([float(seconds_or_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(world, units_per_rank_step, steps, seconds):
+    """Units processed by all ranks (each rank solves its own instance:
+    weak scaling) per second of the slowest rank's time."""
+    return world * units_per_rank_step * steps / seconds
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -370,11 +383,9 @@ def run_gpu(args, w):
     clk = stop_clocks(clocks, dev_uuid) if rank == 0 else None
     total_ms = sum(step_ms)
     if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+        total_ms = max_over_ranks(dist, torch, total_ms, "cuda")
     att = attempts_per_step(w)
-    value = world * att * args.steps / (total_ms / 1000.0)
+    value = whole_job_rate(world, att, args.steps, total_ms / 1000.0)
 
     # end to end through the host-buffer entry point (pinned host memory, copies inside the timed region)
     e2e_steps = max(1, min(args.steps, 10))
@@ -393,10 +404,8 @@ def run_gpu(args, w):
         x_in[:] = x_out
         t += 1
     if world > 1:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_value = world * att * e2e_steps / e2e_s
+        e2e_s = max_over_ranks(dist, torch, e2e_s, "cuda")
+    e2e_value = whole_job_rate(world, att, e2e_steps, e2e_s)
 
     I.icd2s_state_destroy(st)
     I.icd2s_qubo_destroy(q)
