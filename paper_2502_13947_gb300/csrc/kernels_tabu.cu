@@ -24,7 +24,8 @@
 //      minima; every thread reduces those itself, so the loop has exactly one
 //      barrier.
 // Ties go to the lowest index, exactly as a scan in index order would.
-// The objective OV is tracked in int64 by every thread (uniform).  The move
+// The objective OV is tracked in int64 by thread 0, which also keeps the toggle
+// counts and the move log and publishes the best visit at the end.  The move
 // log (uint16 per iteration) stays in shared memory; after the last
 // iteration the moves made after the best visit are undone in one pass:
 // variables moved an odd number of times flip back, and their rows of Q
@@ -54,7 +55,7 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
     static_assert(4 * W <= (1 << kKeyShift), "the local index must fit the key");
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* wkeys = reinterpret_cast<unsigned long long*>(smem);         // [2][32]
-    int* nF = reinterpret_cast<int*>(smem + 512);                                     // [1]
+    int* nF = reinterpret_cast<int*>(smem + 512);                                     // [1]; +520: best visit
     int32_t* Ts = reinterpret_cast<int32_t*>(smem + 528);                             // [ld]
     uint32_t* undo = reinterpret_cast<uint32_t*>(smem + 528 + 4 * (size_t)d.ld);      // [ld / 32]
     uint16_t* mlog = reinterpret_cast<uint16_t*>(smem + 528 + 4 * (size_t)d.ld + d.ld / 8);  // [alpha]
@@ -71,6 +72,7 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
     if (tid == 0) *nF = 0;
 
     int gf[W][4], fa[W][4];
+    unsigned s32[W][4];  // 32 (1 - 2 x_j) mod 2^32: the key is gf * s32 + const, one multiply-add
     unsigned xb = 0;  // bit 4w+b = x of the owned variable
 #pragma unroll
     for (int w = 0; w < W; ++w) {
@@ -87,6 +89,7 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
             const unsigned xj = (xv >> (8 * b)) & 1u;
             xb |= xj << (4 * w + b);
             gf[w][b] = xj ? -gv[b] : gv[b];
+            s32[w][b] = xj ? (unsigned)-32 : 32u;
             fa[w][b] = (j0 + b < n) ? 0 : INT_MAX;  // padding never becomes free
         }
     }
@@ -98,9 +101,9 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
         for (int w = 0; w < W; ++w)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const int k = 4 * w + b;
-                const int g = ((xb >> k) & 1u) ? -gf[w][b] : gf[w][b];
-                const unsigned key = ((unsigned)(g + (int)kKeyBias) << kKeyShift) | (unsigned)k;
+                const unsigned k = 4 * w + b;
+                // ((g + bias) << 5) | k with g = (1 - 2x) gf, as one multiply-add modulo 2^32
+                const unsigned key = (unsigned)gf[w][b] * s32[w][b] + ((kKeyBias << kKeyShift) | k);
                 tk = itn >= fa[w][b] ? min(tk, key) : tk;
             }
         const unsigned wg = __reduce_min_sync(0xffffffffu, tk >> kKeyShift);
@@ -152,12 +155,16 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
                     if (b == bi) {
                         gf[w][b] -= (int)(int8_t)(rv[w] >> (8 * b)) * si2;
                         xb ^= 1u << (4 * w + b);
+                        s32[w][b] = 0u - s32[w][b];
                         fa[w][b] = it + c;
                     }
             }
-        OV += gi;
-        if (OV < OVmin) { OVmin = OV; best_it = it; }
-        if (tid == 0) { Ts[i] += 1; mlog[it] = (uint16_t)i; }
+        if (tid == 0) {  // the objective, best visit, toggle count and move log: one thread
+            OV += gi;
+            if (OV < OVmin) { OVmin = OV; best_it = it; }
+            Ts[i] += 1;
+            mlog[it] = (uint16_t)i;
+        }
         const int slot = (it + 1) & 1;
         warp_argmin(it + 1, slot);
         __syncthreads();
@@ -167,6 +174,10 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
     // toggle counts out; parity of the moves made after the best visit
     int32_t* Tout = d.T + (size_t)p * ld;
     for (int j = tid; j < ld; j += NT) Tout[j] = Ts[j];
+    int* s_best = reinterpret_cast<int*>(smem + 520);
+    if (tid == 0) *s_best = best_it;
+    __syncthreads();
+    best_it = *s_best;
     for (int e = best_it + 1 + tid; e < alpha; e += NT) {
         const int i = mlog[e];
         atomicXor(&undo[i >> 5], 1u << (i & 31));
