@@ -82,7 +82,9 @@ typedef struct icd2s_params {
     int32_t stop_at_target;/* 1: icd2s_run / icd2s_state_run stop as soon as the best energy is
                               <= target_E and report the device time to reach it */
     int64_t target_E;
-    int32_t reserved[2];
+    int32_t im_mode;       /* Ising machine: 0 = the cosine-schedule annealer; 1 = exact (every
+                              assignment of the subQUBO is tried; m_max, m_init <= 24) */
+    int32_t reserved[1];
 } icd2s_params;
 
 /* Per-call anneal parameters (the emulated Ising machine). */
@@ -205,6 +207,19 @@ int icd2s_get_control(icd2s_state* st, int32_t* A, int32_t* gamma, int32_t* delt
 int icd2s_anneal_subqubos_batch(icd2s_state* st, const int32_t* idx_dev, const int32_t* off_dev,
                                 int32_t count, const icd2s_anneal_params* ap, uint8_t* flips_dev,
                                 int64_t* dE_dev, void* stream);
+
+/* Exact Ising machine for small subQUBOs (the "precise solution" of a
+ * subQUBO, Section 3): for each of `count` subQUBOs (as for
+ * icd2s_anneal_subqubos_batch; sizes 1..24), the assignment of its variables
+ * that minimises the Eq. 4 objective with the other variables fixed, all 2^m
+ * assignments tried (Gray-code order, one warp per subQUBO); ties go to the
+ * smallest assignment read as sum_a y_a 2^a (position a = the a-th listed
+ * variable).  Writes the changed variables to flips_dev[replicas][n]
+ * (cleared by the call) and the objective change dE_dev[count] (<= 0; may be
+ * NULL).  Solutions are not modified.  ICD2S_ERR_RANGE for a size above 24. */
+int icd2s_exact_subqubos_batch(icd2s_state* st, const int32_t* idx_dev, const int32_t* off_dev,
+                               int32_t count, int32_t per_replica, uint8_t* flips_dev, int64_t* dE_dev,
+                               void* stream);
 
 /* Flips every variable marked in flips_dev[replicas][n] and updates the
  * int32 gains g_i = (1 - 2 x_i)(Q_ii + 2 sum_{j != i} Q_ij x_j) and int64

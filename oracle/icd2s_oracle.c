@@ -364,6 +364,28 @@ void orc_subqubo(const int8_t* Q, int32_t n, const uint8_t* x, const int32_t* S,
     free(in_s);
 }
 
+/* Exact Ising machine for small subQUBOs (the "precise solution" of a
+ * subQUBO, Section 3): the assignment y of the m positions that minimises
+ * the Eq. 4 objective, found by trying all 2^m of them; ties go to the
+ * smallest y read as the integer sum_a y_a 2^a.  xs[m] is replaced by the
+ * minimiser; returns f(y) - f(xs).  m <= 24. */
+int64_t orc_subqubo_energy(const int32_t* Qs, int32_t m, const uint8_t* xs);
+int64_t orc_exact_subqubo(const int32_t* Qs, int32_t m, uint8_t* xs)
+{
+    uint8_t* y = (uint8_t*)malloc((size_t)(m > 0 ? m : 1));
+    const int64_t f0 = orc_subqubo_energy(Qs, m, xs);
+    int64_t best = INT64_MAX;
+    uint32_t best_v = 0;
+    for (uint32_t v = 0; v < (1u << m); ++v) {
+        for (int32_t a = 0; a < m; ++a) y[a] = (uint8_t)((v >> a) & 1u);
+        const int64_t f = orc_subqubo_energy(Qs, m, y);
+        if (f < best) { best = f; best_v = v; }
+    }
+    for (int32_t a = 0; a < m; ++a) xs[a] = (uint8_t)((best_v >> a) & 1u);
+    free(y);
+    return best - f0;
+}
+
 /* Energy of the subQUBO (Eq. 4 objective) at xs[m]. */
 int64_t orc_subqubo_energy(const int32_t* Qs, int32_t m, const uint8_t* xs)
 {
@@ -469,6 +491,7 @@ typedef struct {
     int32_t max_iters;
     int32_t select_mode; /* 0: rank by A (Algorithm 4); 1: rank by the learned score;
                             2: learned on even solutions, A on odd ones */
+    int32_t im_mode;     /* 0: annealing Ising machine; 1: exact (m_max <= 24) */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -660,7 +683,10 @@ int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t see
              * the call (Jacobi merge, reading S16) */
             orc_subqubo(Q, n, S_pre, idx + off, m, Qs, NULL);
             for (int32_t a = 0; a < m; ++a) xs[a] = S_pre[idx[off + a]];
-            orc_anneal(Qs, m, xs, prm->sweeps, beta, nlog, seed, (uint32_t)(p * K + k), (uint32_t)t, NULL);
+            if (prm->im_mode == 1)
+                orc_exact_subqubo(Qs, m, xs);
+            else
+                orc_anneal(Qs, m, xs, prm->sweeps, beta, nlog, seed, (uint32_t)(p * K + k), (uint32_t)t, NULL);
             for (int32_t a = 0; a < m; ++a) {
                 x[idx[off + a]] = xs[a];
                 in_sel[(int64_t)p * n + idx[off + a]] = 1;
@@ -712,7 +738,10 @@ void orc_initial_pass(const int8_t* Q, int32_t n, const orc_params* prm, uint64_
             for (int32_t a = 0; a < m; ++a) idx[a] = l * m + a;
             orc_subqubo(Q, n, x, idx, m, Qs, NULL);
             for (int32_t a = 0; a < m; ++a) xs[a] = x[idx[a]];
-            orc_anneal(Qs, m, xs, prm->sweeps, beta, nlog, seed, (uint32_t)p, 0x80000000u | (uint32_t)l, NULL);
+            if (prm->im_mode == 1)
+                orc_exact_subqubo(Qs, m, xs);
+            else
+                orc_anneal(Qs, m, xs, prm->sweeps, beta, nlog, seed, (uint32_t)p, 0x80000000u | (uint32_t)l, NULL);
             for (int32_t a = 0; a < m; ++a) x[idx[a]] = xs[a];
         }
         E[p] = orc_energy(Q, n, x);

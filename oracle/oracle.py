@@ -47,7 +47,7 @@ class Params(C.Structure):
         ("T_max", C.c_double), ("T_min", C.c_double),
         ("w1", C.c_int64), ("w2", C.c_int64), ("w3", C.c_int64),
         ("mut_mode", C.c_int32), ("mut_rate", C.c_double),
-        ("patience", C.c_int32), ("max_iters", C.c_int32), ("select_mode", C.c_int32),
+        ("patience", C.c_int32), ("max_iters", C.c_int32), ("select_mode", C.c_int32), ("im_mode", C.c_int32),
     ]
 
 
@@ -86,6 +86,7 @@ def lib():
                 "orc_subqubo_sizes": (None, [i32, i32, i32, u64, u32, u32, vp]),
                 "orc_subqubo": (None, [vp, i32, vp, vp, i32, vp, vp]),
                 "orc_subqubo_energy": (i64, [vp, i32, vp]),
+                "orc_exact_subqubo": (i64, [vp, i32, vp]),
                 "orc_anneal": (i64, [vp, i32, vp, i32, vp, vp, u64, u32, u32, vp]),
                 "orc_mutate": (i32, [vp, i32, vp, i32, u64, u32, u32, vp]),
                 "orc_run": (i32, [vp, i32, C.POINTER(Params), u64, vp, vp, vp, vp, C.POINTER(Result)]),
@@ -256,6 +257,16 @@ def subqubo_energy(Qs, xs) -> int:
     Qs = _i32(Qs)
     xs = _u8(xs)
     return int(lib().orc_subqubo_energy(_p(Qs), Qs.shape[0], _p(xs)))
+
+
+def exact_subqubo(Qs, xs):
+    """Exact minimiser of the subQUBO objective (ties: smallest sum y_a 2^a).
+    Returns (y, f(y) - f(xs))."""
+    Qs = np.ascontiguousarray(Qs, dtype=np.int32)
+    m = Qs.shape[0]
+    y = _u8(xs).copy()
+    dE = lib().orc_exact_subqubo(_p(Qs), m, _p(y))
+    return y, int(dE)
 
 
 def anneal(Qs, xs, beta, nlog, seed, slot, it):

@@ -276,6 +276,8 @@ static int check_params(const icd2s_state* st, const icd2s_params* p)
     REQ(p->select_mode == 0 || st->mlp, ICD2S_ERR_STATE, "select_mode %d needs a network (icd2s_state_set_mlp)",
         p->select_mode);
     REQ(p->stop_at_target == 0 || p->stop_at_target == 1, ICD2S_ERR_ARG, "stop_at_target must be 0 or 1");
+    REQ(p->im_mode == 0 || (p->im_mode == 1 && p->m_max <= 24 && mi <= 24), ICD2S_ERR_RANGE,
+        "im_mode must be 0, or 1 (exact) with subQUBOs of at most 24 variables");
     return ICD2S_OK;
 }
 
@@ -555,7 +557,7 @@ int icd2s_select_subqubos(icd2s_state* st, const icd2s_select_params* sp, int32_
 static int anneal_impl(icd2s_state* st, const int32_t* idx, const int32_t* off, int count, int per_replica,
                        int m_max, int block_m, int block_base, int sweeps, double T_max, double T_min, uint32_t iter,
                        uint8_t* mask, int ldm, int64_t* dE, cudaStream_t s, bool queued = false,
-                       const int32_t* iter_dev = nullptr)
+                       const int32_t* iter_dev = nullptr, int im_mode = 0)
 {
     int rc = ensure_beta(st, sweeps, T_max, T_min, s);
     if (rc) return rc;
@@ -565,9 +567,36 @@ static int anneal_impl(icd2s_state* st, const int32_t* idx, const int32_t* off, 
     a.slot_base = 0; a.mask = mask; a.ldm = ldm; a.dE = dE; a.attempts_acc = st->counters; a.m_max = m_max;
     a.warps_per_cta = st->tune.anneal_warps_per_cta;
     a.iter_dev = iter_dev;
+    if (im_mode == 1) {  // exact Ising machine (m <= 24)
+        CK(launch_exact(st->d, a, s));
+        return ICD2S_OK;
+    }
     if (queued) { a.queue = st->queue; a.order = st->lpt; }
     CK(launch_anneal(st->d, a, s));
     return ICD2S_OK;
+}
+
+int icd2s_exact_subqubos_batch(icd2s_state* st, const int32_t* idx_dev, const int32_t* off_dev, int32_t count,
+                               int32_t per_replica, uint8_t* flips_dev, int64_t* dE_dev, void* stream)
+{
+    REQ(st && idx_dev && off_dev && flips_dev, ICD2S_ERR_ARG, "NULL argument");
+    REQ(count >= 0, ICD2S_ERR_ARG, "count < 0");
+    REQ(per_replica >= 1 && (long long)count <= (long long)st->R * per_replica, ICD2S_ERR_ARG,
+        "count=%d exceeds replicas * per_replica", count);
+    cudaStream_t s = S(stream);
+    const int n = st->q->n;
+    std::vector<int32_t> off((size_t)count + 1);
+    CK(cudaMemcpyAsync(off.data(), off_dev, sizeof(int32_t) * (count + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int m_max = 1;
+    for (int i = 0; i < count; ++i) {
+        const int m = off[i + 1] - off[i];
+        REQ(m >= 1 && m <= 24 && m <= n, ICD2S_ERR_RANGE, "subQUBO %d has size %d (exact: 1..24, <= n)", i, m);
+        if (m > m_max) m_max = m;
+    }
+    CK(cudaMemsetAsync(flips_dev, 0, (size_t)st->R * n, s));
+    return anneal_impl(st, idx_dev, off_dev, count, per_replica, m_max, 0, 0, 1, 1.0, 1.0, 0u, flips_dev, n, dE_dev,
+                       s, false, nullptr, 1);
 }
 
 int icd2s_anneal_subqubos_batch(icd2s_state* st, const int32_t* idx_dev, const int32_t* off_dev, int32_t count,
@@ -691,7 +720,7 @@ int icd2s_initial_pass(icd2s_state* st, const icd2s_params* p, void* stream)
     const int m = p->m_init > 0 ? p->m_init : p->m_max;
     for (int l = 0; l < st->q->n / m; ++l) {
         rc = anneal_impl(st, nullptr, nullptr, st->R, 1, m, m, l * m, p->sweeps, p->T_max, p->T_min,
-                         0x80000000u | (uint32_t)l, nullptr, 0, nullptr, s);
+                         0x80000000u | (uint32_t)l, nullptr, 0, nullptr, s, false, nullptr, p->im_mode);
         if (rc) return rc;
         CK(launch_apply(st->d, s));
     }
@@ -751,7 +780,7 @@ static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* tra
     mark(st, 1, 1, s);
     mark(st, 2, 0, s);
     rc = anneal_impl(st, st->idx, st->off, R * p->K, p->K, p->m_max, 0, 0, p->sweeps, p->T_max, p->T_min,
-                     (uint32_t)t, nullptr, 0, nullptr, s, queued, it_dev);                 // Eq. 4, Algorithm 4
+                     (uint32_t)t, nullptr, 0, nullptr, s, queued, it_dev, p->im_mode);      // Eq. 4, Algorithm 4
     if (rc) return rc;
     mark(st, 2, 1, s);
     mark(st, 3, 0, s);

@@ -130,6 +130,7 @@ bool tabu_variant_fits(int variant, int n);
 int tabu_num_variants();
 int tabu_default_variant(int n);
 cudaError_t launch_anneal(const Dev& d, const AnnealArgs& a, cudaStream_t s);
+cudaError_t launch_exact(const Dev& d, const AnnealArgs& a, cudaStream_t s);  // exact IM, m <= 24
 cudaError_t launch_limtab(const uint32_t* beta, int sweeps, const uint32_t* nlog, int* lim, cudaStream_t s);
 cudaError_t launch_compact_mask(const Dev& d, const uint8_t* mask, int ldm, cudaStream_t s);
 cudaError_t launch_apply(const Dev& d, cudaStream_t s);

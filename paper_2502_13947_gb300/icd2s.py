@@ -35,6 +35,7 @@ EXPORTS = (
     "icd2s_state_run", "icd2s_mlp_create", "icd2s_mlp_destroy", "icd2s_mlp_set_weights", "icd2s_mlp_get_weights",
     "icd2s_mlp_score", "icd2s_mlp_grad", "icd2s_mlp_train", "icd2s_state_set_mlp", "icd2s_get_features",
     "icd2s_get_hits", "icd2s_log_enable", "icd2s_log_info", "icd2s_log_copy", "icd2s_get_apply_ms",
+    "icd2s_exact_subqubos_batch",
 )
 MLP_PARAMS = 4673
 PHASES = ("tabu", "select", "anneal", "apply_anneal", "mutate", "apply_mutate", "best")
@@ -53,7 +54,7 @@ class Params(C.Structure):
         ("w1", C.c_int64), ("w2", C.c_int64), ("w3", C.c_int64), ("mut_mode", C.c_int32), ("mut_rate", C.c_double),
         ("patience", C.c_int32), ("max_iters", C.c_int32), ("use_graph", C.c_int32), ("refresh_every", C.c_int32),
         ("select_mode", C.c_int32), ("stop_at_target", C.c_int32), ("target_E", C.c_int64),
-        ("reserved", C.c_int32 * 2),
+        ("im_mode", C.c_int32), ("reserved", C.c_int32 * 1),
     ]
 
 
@@ -133,6 +134,7 @@ def lib():
                 "icd2s_refresh": (C.c_int, [vp, i32, P(i32), vp]),
                 "icd2s_get_refresh_ms": (C.c_int, [vp, P(f64)]),
                 "icd2s_get_apply_ms": (C.c_int, [vp, P(f64)]),
+                "icd2s_exact_subqubos_batch": (C.c_int, [vp, vp, vp, i32, i32, vp, vp, vp]),
                 "icd2s_state_run": (C.c_int, [vp, P(Params), vp, vp, P(Stats), vp, vp]),
                 "icd2s_mlp_create": (C.c_int, [u64, P(vp)]),
                 "icd2s_mlp_destroy": (C.c_int, [vp]),
@@ -265,6 +267,12 @@ def icd2s_anneal_subqubos_batch(st, idx_dev: int, off_dev: int, count: int, ap: 
                                 dE_dev: int = 0, stream=0) -> None:
     _check(lib().icd2s_anneal_subqubos_batch(st, C.c_void_p(idx_dev), C.c_void_p(off_dev), count, C.byref(ap),
                                              C.c_void_p(flips_dev), C.c_void_p(dE_dev or None), _s(stream)))
+
+
+def icd2s_exact_subqubos_batch(st, idx_dev: int, off_dev: int, count: int, per_replica: int, flips_dev: int,
+                               dE_dev: int = 0, stream=0) -> None:
+    _check(lib().icd2s_exact_subqubos_batch(st, idx_dev, off_dev, count, per_replica, flips_dev, dE_dev or None,
+                                            _s(stream)))
 
 
 def icd2s_apply_flips_update_gains(st, flips_dev: int, stream=0) -> None:

@@ -184,6 +184,71 @@ def test_anneal(L, orc, sweeps, T_max, density):
     P.close()
 
 
+@pytest.mark.parametrize("density", [1.0, 0.1])
+def test_exact_subqubos(L, orc, density):
+    """Exact Ising machine (all 2^m assignments, Gray-code walk split over the
+    lanes) against the oracle's brute force, m = 1..20 (fewer than 32 lanes
+    for m < 5, one dynamic flip per 16 steps for m >= 9)."""
+    torch = torch_cuda()
+    n, R, K = 600, 3, 3
+    sizes = [1, 3, 4, 5, 6, 8, 13, 16, 20]
+    P = Problem(n, density, 33, R=R, state_seed=77)
+    X0 = random_solutions(n, R, 5)
+    P.load(X0)
+    groups, offs = [], [0]
+    for p in range(R):
+        sz = sizes[p * K:(p + 1) * K]
+        g = random_subsets(n, sz, 200 + p)
+        o = 0
+        for m in sz:
+            groups.append((p, g[o:o + m]))
+            offs.append(offs[-1] + m)
+            o += m
+    idx_d = dev(np.concatenate([g for _, g in groups]).astype(np.int32))
+    off_d = dev(np.array(offs, np.int32))
+    mask = torch.zeros((R, n), dtype=torch.uint8, device="cuda")
+    dE = torch.zeros(len(groups), dtype=torch.int64, device="cuda")
+    I.icd2s_exact_subqubos_batch(P.st, idx_d.data_ptr(), off_d.data_ptr(), len(groups), K, mask.data_ptr(),
+                                 dE.data_ptr())
+    mask, dE = mask.cpu().numpy(), dE.cpu().numpy()
+    want = np.zeros((R, n), np.uint8)
+    for s_, (p, S) in enumerate(groups):
+        Qs, _ = orc.subqubo(P.Q, X0[p], S)
+        y, dEo = orc.exact_subqubo(Qs, X0[p][S])
+        want[p, S] = y != X0[p][S]
+        assert dE[s_] == dEo, (s_, len(S))
+    assert np.array_equal(mask, want)
+    P.close()
+
+
+def test_exact_subqubo_m24_is_a_local_optimum_below_annealing(L, orc):
+    """m = 22 and 24 (too large for the oracle's brute force): no single flip
+    of the returned assignment lowers the subQUBO objective, and it is not
+    above a slow anneal of the same subQUBO."""
+    torch = torch_cuda()
+    n = 300
+    P = Problem(n, 1.0, 44, R=1, state_seed=3)
+    X0 = random_solutions(n, 1, 8)
+    P.load(X0)
+    for m in (22, 24):
+        S = np.sort(random_subsets(n, [m], 9 + m)).astype(np.int32)
+        idx_d, off_d = dev(S), dev(np.array([0, m], np.int32))
+        mask = torch.zeros((1, n), dtype=torch.uint8, device="cuda")
+        dE = torch.zeros(1, dtype=torch.int64, device="cuda")
+        I.icd2s_exact_subqubos_batch(P.st, idx_d.data_ptr(), off_d.data_ptr(), 1, 1, mask.data_ptr(), dE.data_ptr())
+        Qs, _ = orc.subqubo(P.Q, X0[0], S)
+        y = X0[0][S] ^ mask.cpu().numpy()[0][S]
+        f = orc.subqubo_energy(Qs, y)
+        assert f - orc.subqubo_energy(Qs, X0[0][S]) == int(dE.cpu()[0])
+        for a in range(m):
+            y2 = y.copy()
+            y2[a] ^= 1
+            assert orc.subqubo_energy(Qs, y2) >= f
+        x1, dEa, _ = orc.anneal(Qs, X0[0][S], orc.beta_table(300, 3000.0, 0.5), orc.nlog_table(), 1, 0, 0)
+        assert f <= orc.subqubo_energy(Qs, x1)
+    P.close()
+
+
 def test_anneal_rejects_oversized_subqubos(L):
     torch = torch_cuda()
     P = Problem(600, 1.0, 1, R=1)

@@ -48,6 +48,16 @@ def test_run_dense_n64_m16_z8_200_iterations(L, orc):
     assert g["anneal_attempts"] == 8 * (n // 16) * 256 * 16 + 200 * 8 * 256 * 16
 
 
+def test_run_with_the_exact_ising_machine(L, orc):
+    """Algorithm 2 with the exact Ising machine (im_mode 1): uneven K = 2
+    subQUBOs of 6..12 variables, the initial pass on blocks of 12."""
+    n = 64
+    Q = make_qubo(n, 1.0, 77)
+    lp = lib_params(I, n, z=4, K=2, m_min=6, m_max=12, m_init=12, alpha=3 * n, c=2, sweeps=8, T_max=500.0,
+                    mut_mode=0, patience=0, max_iters=12, im_mode=1)
+    _compare_runs(orc, Q, lp, 19)
+
+
 def test_run_with_patience_and_constant_rate(L, orc):
     n = 150
     Q = make_qubo(n, 0.3, 5)

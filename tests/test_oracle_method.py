@@ -283,6 +283,37 @@ def test_anneal_slow_schedule_finds_the_subqubo_optimum(orc):
         assert orc.subqubo_energy(Qs, x1) == opt
 
 
+@pytest.mark.parametrize("m,seed", [(1, 0), (4, 1), (7, 2), (10, 3)])
+def test_exact_subqubo_is_the_full_energy_minimum(orc, m, seed):
+    """The exact Ising machine (all 2^m assignments of the subQUBO) against an
+    independent enumeration of the whole energy (Eq. 1) with the other
+    variables fixed; ties to the smallest assignment sum_a y_a 2^a."""
+    n = 30
+    Q = make_qubo(n, 0.7, seed)
+    x = random_solutions(n, 1, seed)[0]
+    S = np.sort(np.random.default_rng(seed).choice(n, m, replace=False)).astype(np.int32)
+    Qs, _ = orc.subqubo(Q, x, S)
+    y, dE = orc.exact_subqubo(Qs, x[S])
+    best = None
+    for v in range(1 << m):
+        xv = x.copy()
+        xv[S] = [(v >> a) & 1 for a in range(m)]
+        e = full_energy(Q, xv)
+        if best is None or e < best[0]:
+            best = (e, v)
+    assert [int(b) for b in y] == [(best[1] >> a) & 1 for a in range(m)]
+    assert dE == best[0] - full_energy(Q, x)
+
+
+def test_exact_subqubo_ties_take_the_smallest_assignment(orc):
+    Qs = np.zeros((3, 3), np.int32)           # f = 0 everywhere: the answer is y = 0
+    y, dE = orc.exact_subqubo(Qs, np.array([1, 0, 1], np.uint8))
+    assert y.tolist() == [0, 0, 0] and dE == 0
+    Qs = np.diag([-5, 0, -5]).astype(np.int32)  # y_1 is free: the smaller choice y_1 = 0
+    y, dE = orc.exact_subqubo(Qs, np.array([0, 1, 0], np.uint8))
+    assert y.tolist() == [1, 0, 1] and dE == -10
+
+
 def test_anneal_acceptance_frequency_matches_the_table(orc):
     """One variable (m = 1) with a fixed positive gain: the accepted fraction
     over many independent attempts is the table's probability."""
