@@ -1,19 +1,20 @@
 // kernels_exact.cu -- exact Ising machine for small subQUBOs (m <= 24): the
 // "precise solution" of a subQUBO (Section 3) by trying all 2^m assignments.
 //
-// One warp per subQUBO.  Q' = Q[S, S] (diagonal stored as 0) is staged in
-// shared memory, one 32-byte row per position.  The 2^m assignments are
-// walked in Gray-code order t -> y = t xor (t >> 1), split into L = min(32,
-// 2^m) contiguous ranges of 2^k codes (k = m - log2 L), one per lane.  A lane
+// One CTA of 128 walkers per subQUBO.  Q' = Q[S, S] (diagonal stored as 0)
+// is staged in shared memory, one 32-byte row per position.  The 2^m
+// assignments are walked in Gray-code order t -> y = t xor (t >> 1), split
+// into L = min(128, 2^m) contiguous ranges of 2^k codes (k = m - log2 L), one
+// per walker.  A walker
 // first moves from the current assignment to the first code of its range
 // (flipping the differing positions one by one), then steps through its
 // range: step u flips position ctz(u) -- the same position in every lane,
-// because each range starts at a multiple of 2^k -- so all lanes read the
-// same row of Q' (a shared-memory broadcast).  Lanes keep the sign-free field
+// because each range starts at a multiple of 2^k -- so all walkers read the
+// same row of Q' (a shared-memory broadcast).  Walkers keep the sign-free field
 // h_a = (1 - 2 y_a) l_a of every position (l_a the gain): a flip of b changes
 // the objective by l_b and adds 2 Q'_ab (1 - 2 y_b) to every h_a (24
-// multiply-adds; padding rows and columns are 0).  Each lane keeps its best
-// (objective, y) pair; the warp takes the minimum of (objective, y as the
+// multiply-adds; padding rows and columns are 0).  Each walker keeps its best
+// (objective, y) pair; the CTA takes the minimum of (objective, y as the
 // integer sum_a y_a 2^a), which fixes the choice among equal objectives.
 // The gains of the current assignment are the global gains (Eq. 4's bias
 // makes the subQUBO's local gain equal the global one), read from G.
@@ -28,15 +29,15 @@ namespace icd2s {
 
 constexpr int kExactMaxM = 24;
 constexpr int kExactRow = 32;  // bytes per staged row
-constexpr int kExactWarps = 4;
+constexpr int kExactThreads = 128;  // walkers per subQUBO (one CTA each)
+constexpr int kExactLog = 7;        // log2 kExactThreads
 
-__global__ __launch_bounds__(32 * kExactWarps) void k_exact(Dev d, AnnealArgs a)
+__global__ __launch_bounds__(kExactThreads) void k_exact(Dev d, AnnealArgs a)
 {
-    __shared__ __align__(16) int8_t qs_all[kExactWarps][kExactMaxM * kExactRow];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s = blockIdx.x * kExactWarps + warp;
-    if (s >= a.count) return;
-    int8_t* qs = qs_all[warp];
+    __shared__ __align__(16) int8_t qs[kExactMaxM * kExactRow];
+    __shared__ long long wbest[kExactThreads / 32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int s = blockIdx.x;
     const int p = s / a.per_replica;
     const int* S = nullptr;
     int m;
@@ -51,13 +52,13 @@ __global__ __launch_bounds__(32 * kExactWarps) void k_exact(Dev d, AnnealArgs a)
     auto var = [&](int r) { return S ? __ldg(S + r) : a.block_base + r; };
 
     // stage Q' with a zero diagonal and zero padding
-    for (int e = lane; e < kExactMaxM * kExactRow; e += 32) {
+    for (int e = tid; e < kExactMaxM * kExactRow; e += kExactThreads) {
         const int r = e / kExactRow, c = e % kExactRow;
         int8_t v = 0;
         if (r < m && c < m && r != c) v = d.Q[(size_t)var(r) * ld + var(c)];
         qs[e] = v;
     }
-    __syncwarp();
+    __syncthreads();
 
     // current assignment x0 and the sign-free fields at x0 (every lane)
     const int32_t* grow = d.G + (size_t)p * ld;
@@ -98,14 +99,14 @@ __global__ __launch_bounds__(32 * kExactWarps) void k_exact(Dev d, AnnealArgs a)
     // key of (objective, y) ordered lexicographically (0 <= y < 2^24)
     auto keyof = [](int f, unsigned y) { return (long long)f * 4294967296LL + (long long)y; };
 
-    const int lg = m < 5 ? m : 5;            // log2 of the lanes in use
-    const int k = m - lg;                    // Gray-code bits each lane walks
-    const bool active = lane < (1 << lg);
+    const int lg = m < kExactLog ? m : kExactLog;  // log2 of the walkers in use
+    const int k = m - lg;                          // Gray-code bits each walker covers
+    const bool active = tid < (1 << lg);
     unsigned y = x0;
-    int f = 0;                               // objective relative to x0
+    int f = 0;                                     // objective relative to x0
     long long best = LLONG_MAX;
     if (active) {
-        const unsigned t0 = (unsigned)lane << k;
+        const unsigned t0 = (unsigned)tid << k;
         const unsigned y0 = t0 ^ (t0 >> 1);
         unsigned diff = y0 ^ x0;
         while (diff) {
@@ -146,6 +147,11 @@ __global__ __launch_bounds__(32 * kExactWarps) void k_exact(Dev d, AnnealArgs a)
         const long long other = __shfl_xor_sync(0xffffffffu, best, o);
         best = other < best ? other : best;
     }
+    if (lane == 0) wbest[warp] = best;
+    __syncthreads();
+    if (warp != 0) return;
+#pragma unroll
+    for (int w = 1; w < kExactThreads / 32; ++w) best = wbest[w] < best ? wbest[w] : best;
     const unsigned ybest = (unsigned)((unsigned long long)best & 0xffffffffull);
     const int fbest = (int)((best - (long long)ybest) / 4294967296LL);
     const unsigned changed = (ybest ^ x0) & ((m >= 32) ? 0xffffffffu : ((1u << m) - 1u));
@@ -172,8 +178,7 @@ cudaError_t launch_exact(const Dev& d, const AnnealArgs& a, cudaStream_t s)
 {
     if (a.count <= 0) return cudaSuccess;
     if (a.m_max > kExactMaxM) return cudaErrorInvalidValue;
-    const int grid = (a.count + kExactWarps - 1) / kExactWarps;
-    k_exact<<<grid, 32 * kExactWarps, 0, s>>>(d, a);
+    k_exact<<<a.count, kExactThreads, 0, s>>>(d, a);
     note_launch(1);
     return cudaGetLastError();
 }
