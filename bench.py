@@ -473,12 +473,14 @@ def run_gpu(args, w):
 # iteration budget is spent (a miss, censored at the budget).
 TTT_INSTANCES = {"n5000-d0.5": dict(n=5000, density=0.5, qseed=0),
                  "n10000-d0.5": dict(n=10000, density=0.5, qseed=0)}
-TTT_METHODS = {  # (K, m_min, m_max, select_mode)
-    "plain": (1, 64, 64, 0),
-    "batched": (16, 32, 256, 0),
-    "learned": (1, 64, 64, 1),
-    "learned+batched": (16, 32, 256, 1),
-    "hybrid+batched": (16, 32, 256, 2),
+TTT_METHODS = {  # (K, m_min, m_max, select_mode, ablation)
+    "plain": (1, 64, 64, 0, 0),
+    "batched": (16, 32, 256, 0, 0),
+    "learned": (1, 64, 64, 1, 0),
+    "learned+batched": (16, 32, 256, 1, 0),
+    "hybrid+batched": (16, 32, 256, 2, 0),
+    "No_IM": (1, 64, 64, 0, 1),      # the simplified versions of Section 4
+    "No_SM": (1, 64, 64, 0, 2),
 }
 # improvement logs of the plain method for training: shapes of the n = 64
 # dense, n = 2500 sparse and n = 5000 batched workloads, instance seeds 200+
@@ -547,10 +549,11 @@ def run_ttt(args):
             longs.append(r["best_E"])
         E_star = min(longs)
         res = dict(target_E=E_star, target_runs=longs, budget_iters=args.ttt_budget)
-        for meth, (K, m_min, m_max, mode) in TTT_METHODS.items():
+        for meth, (K, m_min, m_max, mode, ablation) in TTT_METHODS.items():
             per = []
             for seed in range(args.ttt_seeds):
                 p = ttt_params(I, n, K, m_min, m_max, mode, args.ttt_budget)
+                p.ablation = ablation
                 p.stop_at_target, p.target_E = 1, E_star
                 st = I.icd2s_state_create(q, p.z, seed)
                 if mode:
@@ -572,7 +575,7 @@ def run_ttt(args):
     line = {"metric": "time-to-target energy", "unit": "ms", "higher_is_better": False, "n_gpus": 1,
             "data": "synthetic", "dtype": "int32/int64 (network: bf16 weights, f32)",
             "config": {"workload": "time-to-target, z=32, alpha=5n, c=n/150, 256 sweeps, T 2000->1, Eq. 5 mutation",
-                       "methods": {k: dict(K=v[0], m_min=v[1], m_max=v[2], select_mode=v[3])
+                       "methods": {k: dict(K=v[0], m_min=v[1], m_max=v[2], select_mode=v[3], ablation=v[4])
                                    for k, v in TTT_METHODS.items()}},
             "train": train_info, "results": results, "wall_s": round(time.time() - t0, 1)}
     print(json.dumps(line), flush=True)

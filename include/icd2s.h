@@ -84,7 +84,12 @@ typedef struct icd2s_params {
     int64_t target_E;
     int32_t im_mode;       /* Ising machine: 0 = the cosine-schedule annealer; 1 = exact (every
                               assignment of the subQUBO is tried; m_max, m_init <= 24) */
-    int32_t reserved[1];
+    int32_t ablation;      /* the simplified versions of Section 4 (Fig. 23): 0 = the method;
+                              1 = No_IM (no Ising-machine call, neither in Call_IM_Solution_Set nor
+                              in the main loop, where the mutation then ranges over all variables); 2 = No_SM (no control parameters: subsets
+                              and mutation candidates ranked by a random key
+                              Philox(ctr = (j / 4, 7 << 24, p, t)).word[j mod 4] >> 1, and each
+                              candidate flips with probability 1/2).  Needs select_mode 0. */
 } icd2s_params;
 
 /* Per-call anneal parameters (the emulated Ising machine). */

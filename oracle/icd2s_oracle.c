@@ -442,8 +442,18 @@ int64_t orc_anneal(const int32_t* Qs, int32_t m, uint8_t* xs, int32_t sweeps,
 /* P_i with P_i = floor((A_i - A_min)(2^32 - 1) / (A_max - A_min)) over the  */
 /* whole row (2^31 when A_max = A_min).  Returns the number of flips.        */
 /* ------------------------------------------------------------------------ */
+static int32_t orc_mutate_p(const int32_t* A, int32_t n, const uint8_t* in_sel, int32_t L, uint64_t seed,
+                            uint32_t p, uint32_t iter, uint8_t* x, int half);
 int32_t orc_mutate(const int32_t* A, int32_t n, const uint8_t* in_sel, int32_t L, uint64_t seed,
                    uint32_t p, uint32_t iter, uint8_t* x)
+{
+    return orc_mutate_p(A, n, in_sel, L, seed, p, iter, x, 0);
+}
+
+/* half != 0: every candidate flips with probability 1/2 (P = 2^31), the
+ * No_SM ablation's mutation without control parameters. */
+static int32_t orc_mutate_p(const int32_t* A, int32_t n, const uint8_t* in_sel, int32_t L, uint64_t seed,
+                            uint32_t p, uint32_t iter, uint8_t* x, int half)
 {
     int32_t amin = A[0], amax = A[0];
     for (int32_t j = 1; j < n; ++j) {
@@ -458,7 +468,7 @@ int32_t orc_mutate(const int32_t* A, int32_t n, const uint8_t* in_sel, int32_t L
         if (in_sel[i]) continue;
         taken += 1;
         uint64_t P;
-        if (amax == amin)
+        if (amax == amin || half)
             P = 2147483648ull;
         else
             P = ((uint64_t)((int64_t)A[i] - amin) * 4294967295ull) / (uint64_t)((int64_t)amax - amin);
@@ -492,6 +502,8 @@ typedef struct {
     int32_t select_mode; /* 0: rank by A (Algorithm 4); 1: rank by the learned score;
                             2: learned on even solutions, A on odd ones */
     int32_t im_mode;     /* 0: annealing Ising machine; 1: exact (m_max <= 24) */
+    int32_t ablation;    /* 0: the method; 1: No_IM (no Ising-machine call); 2: No_SM (no control
+                            parameters: a random ranking and flip probability 1/2) */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -650,11 +662,21 @@ int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t see
     for (int32_t p = 0; p < z; ++p) {
         orc_delta(T + (int64_t)p * n, n, del);
         orc_aggregate(eta_hat, gam, del, n, prm->w1, prm->w2, prm->w3, A + (int64_t)p * n);
+        if (prm->ablation == 2)  /* No_SM: the ranking key is Philox(ctr = (j / 4, 7 << 24, p, t)) >> 1 */
+            for (int32_t j = 0; j < n; ++j)
+                A[(int64_t)p * n + j] =
+                    (int32_t)(orc_word(seed, (uint32_t)(j / 4), 7u << 24, (uint32_t)p, (uint32_t)t, j % 4) >> 1);
     }
     /* Call_IM_Partial_Solution_Set (Algorithm 4) */
     for (int32_t p = 0; p < z; ++p) {
         uint8_t* x = S + (int64_t)p * n;
         const int32_t* Ap = A + (int64_t)p * n;
+        if (prm->ablation == 1) {  /* No_IM: no subset, no Ising-machine call */
+            memset(in_sel + (int64_t)p * n, 0, (size_t)n);
+            msel[p] = 0;
+            E[p] = orc_energy(Q, n, x);
+            continue;
+        }
         orc_subqubo_sizes(K, prm->m_min, prm->m_max, seed, (uint32_t)p, (uint32_t)t, sizes);
         const int learned = prm->select_mode == 1 || (prm->select_mode == 2 && p % 2 == 0);
         if (learned || F_out || score_out) {
@@ -704,7 +726,8 @@ int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t see
     for (int32_t p = 0; p < z; ++p) {
         uint8_t* x = S + (int64_t)p * n;
         int32_t L = (int32_t)floor((double)(n - msel[p]) * r);
-        orc_mutate(A + (int64_t)p * n, n, in_sel + (int64_t)p * n, L, seed, (uint32_t)p, (uint32_t)t, x);
+        orc_mutate_p(A + (int64_t)p * n, n, in_sel + (int64_t)p * n, L, seed, (uint32_t)p, (uint32_t)t, x,
+                     prm->ablation == 2);
         E[p] = orc_energy(Q, n, x);
     }
     orc_best_update(S, E, z, n, best_E, best_x, &improved, winner);
@@ -734,7 +757,7 @@ void orc_initial_pass(const int8_t* Q, int32_t n, const orc_params* prm, uint64_
     orc_nlog_table(nlog);
     for (int32_t p = 0; p < prm->z; ++p) {
         uint8_t* x = S + (int64_t)p * n;
-        for (int32_t l = 0; l < n / m; ++l) {
+        for (int32_t l = 0; l < (prm->ablation == 1 ? 0 : n / m); ++l) {  /* No_IM: no IM call at all */
             for (int32_t a = 0; a < m; ++a) idx[a] = l * m + a;
             orc_subqubo(Q, n, x, idx, m, Qs, NULL);
             for (int32_t a = 0; a < m; ++a) xs[a] = x[idx[a]];

@@ -278,6 +278,8 @@ static int check_params(const icd2s_state* st, const icd2s_params* p)
     REQ(p->stop_at_target == 0 || p->stop_at_target == 1, ICD2S_ERR_ARG, "stop_at_target must be 0 or 1");
     REQ(p->im_mode == 0 || (p->im_mode == 1 && p->m_max <= 24 && mi <= 24), ICD2S_ERR_RANGE,
         "im_mode must be 0, or 1 (exact) with subQUBOs of at most 24 variables");
+    REQ(p->ablation >= 0 && p->ablation <= 2, ICD2S_ERR_ARG, "ablation=%d outside 0..2", p->ablation);
+    REQ(p->ablation == 0 || p->select_mode == 0, ICD2S_ERR_ARG, "the ablations use the paper's selection rule");
     return ICD2S_OK;
 }
 
@@ -520,17 +522,18 @@ int icd2s_tabu(icd2s_state* st, int32_t alpha, int32_t c, void* stream)
 // iter_dev: non-null when the iteration number comes from device memory (a replayed step).
 static int select_impl(icd2s_state* st, int64_t w1, int64_t w2, int64_t w3, int K, int m_min, int m_max,
                        uint32_t iter, cudaStream_t s, const int32_t* iter_dev = nullptr, int mode = 0,
-                       bool count_hits = true)
+                       bool count_hits = true, int ablation = 0)
 {
     const int n = st->q->n;
     REQ(K >= 1 && K <= 64, ICD2S_ERR_RANGE, "K=%d outside 1..64", K);
     REQ(m_min >= 1 && m_min <= m_max && m_max <= kMaxM, ICD2S_ERR_RANGE, "sizes %d..%d outside 1..256", m_min, m_max);
+    if (ablation == 1) m_min = m_max = 0;  // No_IM: an empty subset (only A and its ranking are made)
     REQ((long long)K * m_max <= n, ICD2S_ERR_ARG, "K*m_max exceeds n");
     const int64_t wl = (int64_t)1 << 24;
     REQ(w1 >= -wl && w1 <= wl && w2 >= -wl && w2 <= wl && w3 >= -wl && w3 <= wl, ICD2S_ERR_RANGE, "|w| > 2^24");
     CK(launch_gamma(st->d, s));
     CK(launch_sizes(st->R, K, m_min, m_max, st->d.k0, st->d.k1, iter, iter_dev, st->off, st->lpt, st->queue, s));
-    CK(launch_select(st->d, w1, w2, w3, K, st->off, st->idx, mode, count_hits, s));
+    CK(launch_select(st->d, w1, w2, w3, K, st->off, st->idx, mode, count_hits, s, iter, iter_dev, ablation));
     st->have_select = true;
     st->sel_K = K;
     return ICD2S_OK;
@@ -718,6 +721,7 @@ int icd2s_initial_pass(icd2s_state* st, const icd2s_params* p, void* stream)
     if (rc) return rc;
     cudaStream_t s = S(stream);
     const int m = p->m_init > 0 ? p->m_init : p->m_max;
+    if (p->ablation == 1) return ICD2S_OK;  // No_IM: no Ising-machine call at all
     for (int l = 0; l < st->q->n / m; ++l) {
         rc = anneal_impl(st, nullptr, nullptr, st->R, 1, m, m, l * m, p->sweeps, p->T_max, p->T_min,
                          0x80000000u | (uint32_t)l, nullptr, 0, nullptr, s, false, nullptr, p->im_mode);
@@ -775,13 +779,15 @@ static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* tra
         }
     }
     rc = select_impl(st, p->w1, p->w2, p->w3, p->K, p->m_min, p->m_max, (uint32_t)t, s, it_dev,
-                     p->select_mode);                                                       // Eq. 6-8, Alg. 3-4
+                     p->select_mode, true, p->ablation);                                    // Eq. 6-8, Alg. 3-4
     if (rc) return rc;
     mark(st, 1, 1, s);
     mark(st, 2, 0, s);
-    rc = anneal_impl(st, st->idx, st->off, R * p->K, p->K, p->m_max, 0, 0, p->sweeps, p->T_max, p->T_min,
-                     (uint32_t)t, nullptr, 0, nullptr, s, queued, it_dev, p->im_mode);      // Eq. 4, Algorithm 4
-    if (rc) return rc;
+    if (p->ablation != 1) {                                                                 // No_IM skips the IM
+        rc = anneal_impl(st, st->idx, st->off, R * p->K, p->K, p->m_max, 0, 0, p->sweeps, p->T_max, p->T_min,
+                         (uint32_t)t, nullptr, 0, nullptr, s, queued, it_dev, p->im_mode);  // Eq. 4, Algorithm 4
+        if (rc) return rc;
+    }
     mark(st, 2, 1, s);
     mark(st, 3, 0, s);
     CK(launch_apply(st->d, s));
@@ -789,7 +795,8 @@ static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* tra
     CK(launch_best(st->d, trace_it ? trace_it + R : nullptr, 0, nullptr, s));
     const double r = p->mut_mode == 0 ? mutation_rate(t) : p->mut_rate;        // Eq. 5
     mark(st, 4, 0, s);
-    CK(launch_mutate(st->d, st->sel_K, st->off, r, (uint32_t)t, it_dev, st->rates, nullptr, st->q->n, s));
+    CK(launch_mutate(st->d, st->sel_K, st->off, r, (uint32_t)t, it_dev, st->rates, nullptr, st->q->n, s,
+                     p->ablation == 2));
     mark(st, 4, 1, s);
     mark(st, 5, 0, s);
     CK(launch_apply(st->d, s));

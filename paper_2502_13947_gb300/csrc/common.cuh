@@ -30,7 +30,8 @@ constexpr int kMaxM = 256;
 constexpr int kMaxReplicas = 4096;
 constexpr int kMaxSweeps = 16384;   // the acceptance-limit table is sweeps x 4096 int32
 
-constexpr uint32_t kTagInit = 1u, kTagAnneal = 2u, kTagMut = 3u, kTagSize = 4u, kTagMlpInit = 5u, kTagTrain = 6u;
+constexpr uint32_t kTagInit = 1u, kTagAnneal = 2u, kTagMut = 3u, kTagSize = 4u, kTagMlpInit = 5u, kTagTrain = 6u,
+                   kTagRank = 7u;
 
 // Proposal network 6-64-64-1: flat parameters W1[64][6], b1[64], W2[64][64],
 // b2[64], w3[64], b3 (row o of W1/W2 = weights into hidden unit o).
@@ -109,10 +110,14 @@ cudaError_t launch_sizes(int R, int K, int m_min, int m_max, uint32_t k0, uint32
                          const int32_t* iter_dev, int32_t* off, int32_t* order, int32_t* queue, cudaStream_t s);
 // mode: 0 rank S' by A; 1 by d.score; 2 by d.score on even replicas.  Hit
 // counts d.H are incremented for S' when count_hits.
+// ablation 2 (No_SM): A is replaced by the random key Philox(ctr = (j / 4, 7 << 24, p, t)) >> 1.
 cudaError_t launch_select(const Dev& d, int64_t w1, int64_t w2, int64_t w3, int K, const int32_t* off,
-                          int32_t* idx, int mode, bool count_hits, cudaStream_t s);
+                          int32_t* idx, int mode, bool count_hits, cudaStream_t s, uint32_t iter = 0,
+                          const int32_t* iter_dev = nullptr, int ablation = 0);
+// half: every candidate flips with probability 1/2 (No_SM) instead of the normalised A.
 cudaError_t launch_mutate(const Dev& d, int K, const int32_t* off, double rate, uint32_t iter,
-                          const int32_t* iter_dev, const double* rates, uint8_t* mask, int ldm, cudaStream_t s);
+                          const int32_t* iter_dev, const double* rates, uint8_t* mask, int ldm, cudaStream_t s,
+                          bool half = false);
 struct AnnealArgs {
     const int32_t* idx; const int32_t* off; int count; int per_replica;
     int block_m; int block_base;          // idx == nullptr: contiguous block [base, base+m)

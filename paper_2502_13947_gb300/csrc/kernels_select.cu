@@ -135,8 +135,10 @@ cudaError_t launch_sizes(int R, int K, int m_min, int m_max, uint32_t k0, uint32
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(1024) void k_select(Dev d, int64_t w1, int64_t w2, int64_t w3, int K,
                                                  const int32_t* __restrict__ off, int32_t* __restrict__ idx, int mode,
-                                                 int32_t* __restrict__ H)
+                                                 int32_t* __restrict__ H, uint32_t iter_arg, const int32_t* iter_dev,
+                                                 int ablation)
 {
+    const uint32_t iter = iter_dev ? (uint32_t)*iter_dev : iter_arg;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int red[33];
     __shared__ int goff[65];
@@ -158,7 +160,10 @@ __global__ __launch_bounds__(1024) void k_select(Dev d, int64_t w1, int64_t w2, 
             const int t = Trow[j];
             const int dl = mt > 0 ? (int)(((long long)(mt - t) * 65536) / mt) : 0;
             const long long v = w1 * (long long)d.etahat[j] + w2 * (long long)d.gamma[j] - w3 * (long long)dl;
-            const int a = (int)floor_div_65536(v);
+            const int a = ablation == 2   // No_SM: a random ranking key instead of A
+                              ? (int)(philox10((uint32_t)(j >> 2), kTagRank << 24, (uint32_t)p, iter, d.k0,
+                                               d.k1).v[j & 3] >> 1)
+                              : (int)floor_div_65536(v);
             Arow[j] = a;
             Drow[j] = dl;
             key = ((unsigned long long)(~((unsigned)a ^ 0x80000000u)) << 32) | (unsigned)j;
@@ -220,12 +225,14 @@ __global__ __launch_bounds__(1024) void k_select(Dev d, int64_t w1, int64_t w2, 
 }
 
 cudaError_t launch_select(const Dev& d, int64_t w1, int64_t w2, int64_t w3, int K, const int32_t* off,
-                          int32_t* idx, int mode, bool count_hits, cudaStream_t s)
+                          int32_t* idx, int mode, bool count_hits, cudaStream_t s, uint32_t iter,
+                          const int32_t* iter_dev, int ablation)
 {
     const size_t sm = 8 * (size_t)next_pow2(d.n);
     cudaError_t e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_select<<<d.R, 1024, sm, s>>>(d, w1, w2, w3, K, off, idx, mode, count_hits ? d.H : nullptr);
+    k_select<<<d.R, 1024, sm, s>>>(d, w1, w2, w3, K, off, idx, mode, count_hits ? d.H : nullptr, iter, iter_dev,
+                                   ablation);
     note_launch(1);
     return cudaGetLastError();
 }
@@ -233,7 +240,7 @@ cudaError_t launch_select(const Dev& d, int64_t w1, int64_t w2, int64_t w3, int 
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(1024) void k_mutate(Dev d, int K, const int32_t* __restrict__ off, double rate_arg,
                                                  uint32_t iter_arg, const int32_t* iter_dev, const double* rates,
-                                                 uint8_t* mask, int ldm)
+                                                 uint8_t* mask, int ldm, int half)
 {
     __shared__ int red[33];
     __shared__ int wsum[32];
@@ -268,7 +275,7 @@ __global__ __launch_bounds__(1024) void k_mutate(Dev d, int K, const int32_t* __
         const int rank = taken + before + __popc(bal & ((1u << lane) - 1u));
         if (pred && rank < L) {
             unsigned long long P;
-            if (amax == amin) P = 2147483648ull;
+            if (amax == amin || half) P = 2147483648ull;
             else P = ((unsigned long long)((long long)Arow[i] - amin) * 4294967295ull) /
                      (unsigned long long)((long long)amax - amin);
             const u32x4 w = philox10((uint32_t)(i >> 2), kTagMut << 24, (uint32_t)p, iter, d.k0, d.k1);
@@ -284,9 +291,10 @@ __global__ __launch_bounds__(1024) void k_mutate(Dev d, int K, const int32_t* __
 }
 
 cudaError_t launch_mutate(const Dev& d, int K, const int32_t* off, double rate, uint32_t iter,
-                          const int32_t* iter_dev, const double* rates, uint8_t* mask, int ldm, cudaStream_t s)
+                          const int32_t* iter_dev, const double* rates, uint8_t* mask, int ldm, cudaStream_t s,
+                          bool half)
 {
-    k_mutate<<<d.R, 1024, 0, s>>>(d, K, off, rate, iter, iter_dev, rates, mask, ldm);
+    k_mutate<<<d.R, 1024, 0, s>>>(d, K, off, rate, iter, iter_dev, rates, mask, ldm, half ? 1 : 0);
     note_launch(1);
     return cudaGetLastError();
 }

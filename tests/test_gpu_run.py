@@ -58,6 +58,16 @@ def test_run_with_the_exact_ising_machine(L, orc):
     _compare_runs(orc, Q, lp, 19)
 
 
+@pytest.mark.parametrize("ablation", [1, 2])
+def test_run_ablations(L, orc, ablation):
+    """The simplified versions of Section 4: No_IM (1) and No_SM (2)."""
+    n = 90
+    Q = make_qubo(n, 0.6, 5 + ablation)
+    lp = lib_params(I, n, z=5, K=2, m_min=7, m_max=12, m_init=12, alpha=2 * n, c=3, sweeps=16, T_max=300.0,
+                    mut_mode=0, patience=0, max_iters=10, ablation=ablation)
+    _compare_runs(orc, Q, lp, 23)
+
+
 def test_run_with_patience_and_constant_rate(L, orc):
     n = 150
     Q = make_qubo(n, 0.3, 5)

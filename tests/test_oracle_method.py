@@ -432,3 +432,65 @@ def test_run_batched_uneven_subqubos(orc):
     r = orc.run(Q, prm, 3)
     assert r["iters"] == 4 and r["best_E"] == orc.energy(Q, r["best_x"])
     assert np.all(np.diff(r["trace"][:, -1]) <= 0)
+
+
+# ----------------------------------------------------------------------------- ablations (Section 4, Fig. 23)
+def _abl_setup(orc, ablation, n=60, z=4, seed=5):
+    Q = make_qubo(n, 0.5, seed)
+    prm = orc.default_params(n, z=z, K=2, m_min=6, m_max=9, m_init=10, alpha=2 * n, c=3, sweeps=16, T_max=80.0,
+                             mut_mode=0, max_iters=3)
+    prm.ablation = ablation
+    S = random_solutions(n, z, seed + 1)
+    return Q, prm, S
+
+
+def test_no_im_ablation_is_tabu_then_mutation(orc):
+    """No_IM: the Ising-machine phase changes nothing and selects nothing; the
+    step is the Tabu search followed by the mutation over all variables."""
+    Q, prm, S = _abl_setup(orc, 1)
+    t, seed, n, z = 0, 11, Q.shape[0], prm.z
+    r = orc.step(Q, prm, seed, t, S, H=np.zeros(S.shape, np.int32))
+    assert np.array_equal(r["trace3"][z:2 * z], r["trace3"][:z]) and not r["H"].any()
+    eh = orc.eta_hat(orc.eta(Q))
+    X = np.stack([orc.tabu(Q, S[p], prm.alpha, prm.c)[0] for p in range(z)])
+    gam = orc.gamma(X)
+    L = int(np.floor(n * orc.mutation_rate(t)))
+    for p in range(z):
+        _, _, T, _ = orc.tabu(Q, S[p], prm.alpha, prm.c)
+        A = orc.aggregate(eh, gam, orc.delta(T))
+        want, _ = orc.mutate(A, np.zeros(n, np.uint8), L, seed, p, t, X[p])
+        assert np.array_equal(r["S"][p], want)
+
+
+def test_no_sm_ablation_ranks_at_random_and_flips_with_probability_half(orc):
+    """No_SM: S' and the mutation candidates come from the ranking of the
+    Philox keys (ctr (j/4, 7 << 24, p, t)) >> 1 instead of A, and every
+    candidate flips iff its mutation word is below 2^31."""
+    Q, prm, S = _abl_setup(orc, 2, n=80, seed=9)
+    t, seed, n, z = 1, 21, Q.shape[0], prm.z
+    r = orc.step(Q, prm, seed, t, S, H=np.zeros(S.shape, np.int32))
+    key = np.array([seed & 0xffffffff, seed >> 32], np.uint32)
+    for p in range(z):
+        rk = np.array([orc.philox([j // 4, 7 << 24, p, t], key)[j % 4] >> 1 for j in range(n)], np.int64)
+        sizes = orc.subqubo_sizes(prm.K, prm.m_min, prm.m_max, seed, p, t)
+        sel = np.sort(orc.select(rk.astype(np.int32), sizes))
+        assert np.flatnonzero(r["H"][p]).tolist() == sel.tolist()
+    # mutation: the first L candidates outside S' in the random order, each
+    # flipped iff its word is below 2^31 (the state before the mutation comes
+    # from the same step with a zero mutation rate)
+    prm0 = orc.Params.from_buffer_copy(prm)
+    prm0.mut_mode, prm0.mut_rate = 1, 0.0
+    r0 = orc.step(Q, prm0, seed, t, S, H=np.zeros(S.shape, np.int32))
+    flipped_any = False
+    for p in range(z):
+        rk = np.array([orc.philox([j // 4, 7 << 24, p, t], key)[j % 4] >> 1 for j in range(n)], np.int64)
+        sel = set(np.flatnonzero(r["H"][p]).tolist())
+        L = int(np.floor((n - len(sel)) * orc.mutation_rate(t)))
+        cands = [j for j in orc.rank(rk.astype(np.int32)).tolist() if j not in sel][:L]
+        want = r0["S"][p].copy()
+        for j in cands:
+            if orc.philox([j // 4, 3 << 24, p, t], key)[j % 4] < 2 ** 31:
+                want[j] ^= 1
+        assert np.array_equal(r["S"][p], want)
+        flipped_any |= bool((want != r0["S"][p]).any())
+    assert flipped_any
