@@ -177,8 +177,23 @@ void orc_init_solutions(int32_t n, int32_t z, uint64_t seed, uint8_t* S)
 /* x is replaced by x_min; T (toggle counts) and C (tabu memory at the end)  */
 /* are returned; the return value is OV_min = f(x_min).                      */
 /* ------------------------------------------------------------------------ */
+int64_t orc_tabu_asp(const int8_t* Q, int32_t n, uint8_t* x, int32_t alpha, int32_t c,
+                     int32_t* T, int32_t* C, int32_t aspiration, int32_t* moves);
 int64_t orc_tabu(const int8_t* Q, int32_t n, uint8_t* x, int32_t alpha, int32_t c,
                  int32_t* T, int32_t* C)
+{
+    return orc_tabu_asp(Q, n, x, alpha, c, T, C, 0, NULL);
+}
+
+/* The same search with the aspiration criterion the text of Section 2.4
+ * describes (reading S4: off by default): a tabu move is admissible when it
+ * would give a better objective than the best visited so far.  A variable
+ * moved while tabu adds c to its remaining tabu memory, so with aspiration
+ * every move can become tabu; the search then takes the unmasked arg-min
+ * (reading S6).  moves[alpha] (optional) receives the variable moved at each
+ * iteration. */
+int64_t orc_tabu_asp(const int8_t* Q, int32_t n, uint8_t* x, int32_t alpha, int32_t c,
+                     int32_t* T, int32_t* C, int32_t aspiration, int32_t* moves)
 {
     int32_t* dx = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
     uint8_t* xmin = (uint8_t*)malloc((size_t)n);
@@ -189,9 +204,16 @@ int64_t orc_tabu(const int8_t* Q, int32_t n, uint8_t* x, int32_t alpha, int32_t 
     for (int32_t k = 0; k < n; ++k) { C[k] = 0; T[k] = 0; }
     for (int32_t it = 0; it < alpha; ++it) {
         int32_t i = -1;                                /* argmin over the non-tabu moves (C <= 0) */
-        for (int32_t k = 0; k < n; ++k)
-            if (C[k] <= 0 && (i < 0 || dx[k] < dx[i]))
+        for (int32_t k = 0; k < n; ++k) {
+            const int admissible = C[k] <= 0 || (aspiration && OV + dx[k] < OVmin);
+            if (admissible && (i < 0 || dx[k] < dx[i]))
                 i = k;
+        }
+        if (i < 0)                                     /* every move tabu, none aspirated */
+            for (int32_t k = 0; k < n; ++k)
+                if (i < 0 || dx[k] < dx[i])
+                    i = k;
+        if (moves) moves[it] = i;
         int32_t gi = dx[i];
         int32_t si = 1 - 2 * x[i];
         for (int32_t j = 0; j < n; ++j)                /* O(n) move-value update */
@@ -504,6 +526,7 @@ typedef struct {
     int32_t im_mode;     /* 0: annealing Ising machine; 1: exact (m_max <= 24) */
     int32_t ablation;    /* 0: the method; 1: No_IM (no Ising-machine call); 2: No_SM (no control
                             parameters: a random ranking and flip probability 1/2) */
+    int32_t aspiration;  /* Tabu search with the aspiration criterion (reading S4) */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -654,7 +677,8 @@ int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t see
 
     /* Tabu search on every solution (Algorithm 1) */
     for (int32_t p = 0; p < z; ++p)
-        E[p] = orc_tabu(Q, n, S + (int64_t)p * n, prm->alpha, prm->c, T + (int64_t)p * n, C + (int64_t)p * n);
+        E[p] = orc_tabu_asp(Q, n, S + (int64_t)p * n, prm->alpha, prm->c, T + (int64_t)p * n,
+                            C + (int64_t)p * n, prm->aspiration, NULL);
     orc_best_update(S, E, z, n, best_E, best_x, &improved, winner);
     if (trace3) memcpy(trace3, E, sizeof(int64_t) * (size_t)z);
     /* Deviation_Extraction (Eq. 8), Control_Parameters_Aggregation (Algorithm 3) */

@@ -48,7 +48,7 @@ class Params(C.Structure):
         ("w1", C.c_int64), ("w2", C.c_int64), ("w3", C.c_int64),
         ("mut_mode", C.c_int32), ("mut_rate", C.c_double),
         ("patience", C.c_int32), ("max_iters", C.c_int32), ("select_mode", C.c_int32), ("im_mode", C.c_int32),
-        ("ablation", C.c_int32),
+        ("ablation", C.c_int32), ("aspiration", C.c_int32),
     ]
 
 
@@ -77,6 +77,7 @@ def lib():
                 "orc_mutation_rate": (f64, [i32]),
                 "orc_init_solutions": (None, [i32, i32, u64, vp]),
                 "orc_tabu": (i64, [vp, i32, vp, i32, i32, vp, vp]),
+                "orc_tabu_asp": (i64, [vp, i32, vp, i32, i32, vp, vp, i32, vp]),
                 "orc_eta": (None, [vp, i32, vp]),
                 "orc_eta_hat": (None, [vp, i32, vp]),
                 "orc_gamma": (None, [vp, i32, i32, vp]),
@@ -179,6 +180,17 @@ def tabu(Q, x, alpha, c):
     Cm = np.zeros(n, dtype=np.int32)
     E = lib().orc_tabu(_p(Q), n, _p(x), alpha, c, _p(T), _p(Cm))
     return x, int(E), T, Cm
+
+
+def tabu_asp(Q, x, alpha, c, aspiration=True):
+    """Tabu search with the aspiration criterion.  Returns (x_min, E_min, T, C, moves)."""
+    Q, n = _q(Q)
+    x = _u8(x).copy()
+    T = np.zeros(n, dtype=np.int32)
+    Cm = np.zeros(n, dtype=np.int32)
+    mv = np.zeros(max(alpha, 1), dtype=np.int32)
+    E = lib().orc_tabu_asp(_p(Q), n, _p(x), alpha, c, _p(T), _p(Cm), 1 if aspiration else 0, _p(mv))
+    return x, int(E), T, Cm, mv[:alpha]
 
 
 def eta(Q):

@@ -494,3 +494,70 @@ def test_no_sm_ablation_ranks_at_random_and_flips_with_probability_half(orc):
         assert np.array_equal(r["S"][p], want)
         flipped_any |= bool((want != r0["S"][p]).any())
     assert flipped_any
+
+
+# ----------------------------------------------------------------------------- aspiration (reading S4)
+def _replay_aspiration(Q, x0, alpha, c):
+    """The aspiration rule executed with full energies (Eq. 1 from scratch):
+    the lowest E(x with x_k flipped) among the free variables and the tabu ones
+    that beat the best visited; if there are none, among all (reading S6);
+    ties to the lowest index.  Returns (moves, best E, best x, fallbacks, aspirated)."""
+    n = Q.shape[0]
+    x = x0.copy()
+    Ebest, xbest = full_energy(Q, x), x.copy()
+    C = np.zeros(n, np.int64)
+    moves, fallbacks, aspirated = [], 0, 0
+    for _ in range(alpha):
+        e = [full_energy(Q, np.where(np.arange(n) == k, 1 - x, x)) for k in range(n)]
+        cand = [(e[k], k) for k in range(n) if C[k] <= 0 or e[k] < Ebest]
+        if not cand:
+            cand = [(e[k], k) for k in range(n)]
+            fallbacks += 1
+        ek, k = min(cand)
+        aspirated += int(C[k] > 0)
+        moves.append(k)
+        x[k] ^= 1
+        C[k] += c
+        C[C > 0] -= 1
+        if ek < Ebest:
+            Ebest, xbest = ek, x.copy()
+    return moves, Ebest, xbest, fallbacks, aspirated
+
+
+def test_tabu_with_aspiration_follows_the_rule_by_full_energies(orc):
+    fired = 0
+    for seed in range(12):
+        n = 6 + seed % 5
+        Q = make_qubo(n, 1.0, 300 + seed)
+        x0 = random_solutions(n, 1, seed)[0]
+        alpha, c = 4 * n, n - 1
+        xm, Em, T, Cm, mv = orc.tabu_asp(Q, x0, alpha, c)
+        moves, Eb, xb, _, asp = _replay_aspiration(Q, x0, alpha, c)
+        assert mv.tolist() == moves and Em == Eb and np.array_equal(xm, xb), seed
+        fired += asp
+    assert fired > 0
+
+
+def test_tabu_with_aspiration_when_every_move_is_tabu(orc):
+    """Tenure c = n: a variable moved while tabu keeps c more iterations of
+    tabu memory, every move becomes tabu, and the search takes the unmasked
+    arg-min (instances where this happens, found by a search over seeds)."""
+    falls = 0
+    for seed in (0, 6, 12, 14, 16, 18):
+        n = 4 + seed % 5
+        Q = make_qubo(n, 1.0, 1000 + seed)
+        x0 = random_solutions(n, 1, seed)[0]
+        xm, Em, T, Cm, mv = orc.tabu_asp(Q, x0, 8 * n, n)
+        moves, Eb, xb, fb, _ = _replay_aspiration(Q, x0, 8 * n, n)
+        assert mv.tolist() == moves and Em == Eb and np.array_equal(xm, xb), seed
+        falls += fb
+    assert falls > 0
+
+
+def test_tabu_without_aspiration_is_algorithm_1(orc):
+    Q = make_qubo(40, 0.5, 3)
+    x0 = random_solutions(40, 1, 4)[0]
+    a = orc.tabu(Q, x0, 200, 5)
+    b = orc.tabu_asp(Q, x0, 200, 5, aspiration=False)
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1]
+    assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
