@@ -90,6 +90,12 @@ typedef struct icd2s_params {
                               and mutation candidates ranked by a random key
                               Philox(ctr = (j / 4, 7 << 24, p, t)).word[j mod 4] >> 1, and each
                               candidate flips with probability 1/2).  Needs select_mode 0. */
+    int32_t aspiration;    /* 1: Tabu search with the aspiration criterion the text of Section 2.4
+                              describes and Algorithm 1 omits (reading S4): a tabu move is also
+                              admissible when it would beat the best objective visited so far; a
+                              variable moved while tabu keeps c more iterations of tabu memory, and
+                              when every move is tabu the unmasked arg-min is taken */
+    int32_t reserved[3];
 } icd2s_params;
 
 /* Per-call anneal parameters (the emulated Ising machine). */
@@ -185,6 +191,8 @@ int icd2s_get_best(icd2s_state* st, uint8_t* x_best, int64_t* E_best);
  * parameters and can be read with icd2s_get_tabu. */
 int icd2s_tabu(icd2s_state* st, int32_t alpha, int32_t c, void* stream);
 int icd2s_get_tabu(icd2s_state* st, int32_t* T, int32_t* C);
+/* icd2s_tabu with the aspiration criterion (see icd2s_params.aspiration). */
+int icd2s_tabu_aspiration(icd2s_state* st, int32_t alpha, int32_t c, void* stream);
 
 /* Control parameters and selection: gamma (Eq. 8) over the replicas, Delta
  * (Eq. 7) from the last Tabu toggle counts, A = w1 eta + w2 gamma - w3 Delta

@@ -280,6 +280,7 @@ static int check_params(const icd2s_state* st, const icd2s_params* p)
         "im_mode must be 0, or 1 (exact) with subQUBOs of at most 24 variables");
     REQ(p->ablation >= 0 && p->ablation <= 2, ICD2S_ERR_ARG, "ablation=%d outside 0..2", p->ablation);
     REQ(p->ablation == 0 || p->select_mode == 0, ICD2S_ERR_ARG, "the ablations use the paper's selection rule");
+    REQ(p->aspiration == 0 || p->aspiration == 1, ICD2S_ERR_ARG, "aspiration must be 0 or 1");
     return ICD2S_OK;
 }
 
@@ -287,7 +288,7 @@ extern "C" {
 
 const char* icd2s_last_error(void) { return g_err; }
 
-int32_t icd2s_version(void) { return 100; }
+int32_t icd2s_version(void) { return 101; }
 
 int icd2s_default_params(int32_t n, icd2s_params* out)
 {
@@ -516,6 +517,17 @@ int icd2s_tabu(icd2s_state* st, int32_t alpha, int32_t c, void* stream)
     REQ(c >= 1 && c <= n, ICD2S_ERR_ARG, "tenure c=%d outside 1..n", c);
     REQ(tabu_smem_bytes(n, alpha) <= 227 * 1024, ICD2S_ERR_RANGE, "alpha=%d too large for n=%d", alpha, n);
     CK(launch_tabu(st->d, alpha, c, st->tune.tabu_variant, S(stream)));
+    return ICD2S_OK;
+}
+
+int icd2s_tabu_aspiration(icd2s_state* st, int32_t alpha, int32_t c, void* stream)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    const int n = st->q->n;
+    REQ(alpha >= 0, ICD2S_ERR_ARG, "alpha < 0");
+    REQ(c >= 1 && c <= n, ICD2S_ERR_ARG, "tenure c=%d outside 1..n", c);
+    REQ(tabu_smem_bytes(n, alpha) <= 227 * 1024, ICD2S_ERR_RANGE, "alpha=%d too large for n=%d", alpha, n);
+    CK(launch_tabu(st->d, alpha, c, st->tune.tabu_variant, S(stream), true));
     return ICD2S_OK;
 }
 
@@ -766,7 +778,7 @@ static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* tra
     const bool feats = wants_features(st, p);
     if (feats && (rc = ensure_features(st, s))) return rc;
     mark(st, 0, 0, s);
-    CK(launch_tabu(st->d, p->alpha, p->c, st->tune.tabu_variant, s));                     // Algorithm 1
+    CK(launch_tabu(st->d, p->alpha, p->c, st->tune.tabu_variant, s, p->aspiration != 0));  // Algorithm 1
     mark(st, 0, 1, s);
     CK(launch_best(st->d, trace_it, 0, nullptr, s));
     mark(st, 1, 0, s);

@@ -99,7 +99,8 @@ cudaError_t launch_init_x(const Dev& d, cudaStream_t s);
 cudaError_t launch_recompute(const Dev& d, const uint8_t* X, int ldx, int R, int32_t* G, int64_t* E,
                              cudaStream_t s);  // gains + energies of X (padded rows)
 cudaError_t launch_pad_rows(const uint8_t* src, int n, int rows, uint8_t* dst, int ld, cudaStream_t s);
-cudaError_t launch_tabu(const Dev& d, int alpha, int c, int w_words, cudaStream_t s);
+// variant: kernel shape (< 0: default); aspiration: Tabu with the aspiration criterion.
+cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_t s, bool aspiration = false);
 size_t tabu_smem_bytes(int n, int alpha);
 cudaError_t launch_gamma(const Dev& d, cudaStream_t s);
 // Iteration context read by the kernels of a captured outer iteration (a CUDA

@@ -49,7 +49,10 @@ __device__ __forceinline__ unsigned long long pack_key(unsigned hi, unsigned lo)
 
 }  // namespace
 
-template <int W, int MAXT>
+// ASP: the aspiration criterion (reading S4): a tabu variable is also a
+// candidate when its move would beat the best objective visited so far, i.e.
+// g < OVmin - OV, which in key units is (key >> 5) < OVmin - OV + bias.
+template <int W, int MAXT, bool ASP>
 __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
 {
     static_assert(4 * W <= (1 << kKeyShift), "the local index must fit the key");
@@ -95,7 +98,7 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
     }
 
     // the warp's arg-min over free variables at iteration `itn`, published to slot `slot`
-    auto warp_argmin = [&](int itn, int slot) {
+    auto warp_argmin = [&](int itn, int slot, unsigned ulim) {
         unsigned tk = 0xffffffffu;
 #pragma unroll
         for (int w = 0; w < W; ++w)
@@ -104,7 +107,8 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
                 const unsigned k = 4 * w + b;
                 // ((g + bias) << 5) | k with g = (1 - 2x) gf, as one multiply-add modulo 2^32
                 const unsigned key = (unsigned)gf[w][b] * s32[w][b] + ((kKeyBias << kKeyShift) | k);
-                tk = itn >= fa[w][b] ? min(tk, key) : tk;
+                const bool ok = itn >= fa[w][b] || (ASP && (key >> kKeyShift) < ulim);
+                tk = ok ? min(tk, key) : tk;
             }
         const unsigned wg = __reduce_min_sync(0xffffffffu, tk >> kKeyShift);
         const unsigned k = tk & ((1u << kKeyShift) - 1u);
@@ -120,18 +124,28 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
         return pack_key(hi, lo);
     };
 
-    __syncthreads();  // shared-memory clears visible
-    warp_argmin(0, 0);
-    __syncthreads();
-    unsigned long long key = block_argmin(0);
-
     long long OV = d.E[p], OVmin = OV;
     int best_it = -1;
+    // aspiration limit in key units: clamp(OVmin - OV + bias, 0, 2^27)
+    auto asp_limit = [&]() -> unsigned {
+        const long long v = OVmin - OV + (long long)kKeyBias;
+        return v <= 0 ? 0u : (v >= (1LL << 27) ? (1u << 27) : (unsigned)v);
+    };
+
+    __syncthreads();  // shared-memory clears visible
+    warp_argmin(0, 0, ASP ? asp_limit() : 0u);
+    __syncthreads();
+    unsigned long long key = block_argmin(0);
 
     for (int it = 0; it < alpha; ++it) {
         const int gi = (int)(unsigned)(key >> 32) - (int)kKeyBias;
         const unsigned jx = (unsigned)key;
         const int i = (int)(jx >> 1);
+        if (i >= n) {  // no move at all (a warp without candidates publishes index ~0): stop, uniformly
+            if (tid == 0) d.flags[2] = 1;
+            alpha = it;
+            break;
+        }
         const int si2 = (jx & 1u) ? -2 : 2;       // 2 (1 - 2 x_i)
         const int8_t* row = Q + (size_t)i * ld;
         int rv[W];
@@ -156,19 +170,35 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
                         gf[w][b] -= (int)(int8_t)(rv[w] >> (8 * b)) * si2;
                         xb ^= 1u << (4 * w + b);
                         s32[w][b] = 0u - s32[w][b];
-                        fa[w][b] = it + c;
+                        // C += c: free again c iterations after the later of now and the
+                        // iteration it was to become free (a tabu move, by aspiration)
+                        fa[w][b] = max(fa[w][b], it) + c;
                     }
             }
-        if (tid == 0) {  // the objective, best visit, toggle count and move log: one thread
+        if (ASP || tid == 0) {  // the objective and best visit: one thread (every thread with aspiration)
             OV += gi;
             if (OV < OVmin) { OVmin = OV; best_it = it; }
+        }
+        if (tid == 0) {         // toggle count and move log
             Ts[i] += 1;
             mlog[it] = (uint16_t)i;
         }
         const int slot = (it + 1) & 1;
-        warp_argmin(it + 1, slot);
+        warp_argmin(it + 1, slot, ASP ? asp_limit() : 0u);
         __syncthreads();
         key = block_argmin(slot);
+        if constexpr (ASP) {
+            // A variable moved again while tabu keeps c more iterations of tabu
+            // memory, so every move can be tabu and none aspirated: then the
+            // unmasked arg-min (reading S6).  No warp had a candidate iff the
+            // index half of the block's key is all ones.  key is uniform.
+            if ((unsigned)key == 0xffffffffu && it + 1 < alpha) {
+                __syncthreads();                      // every thread has read this slot
+                warp_argmin(INT_MAX - 1, slot, 0u);   // every real variable (padding stays out)
+                __syncthreads();
+                key = block_argmin(slot);
+            }
+        }
     }
 
     // toggle counts out; parity of the moves made after the best visit
@@ -253,16 +283,16 @@ size_t tabu_smem_bytes(int n, int alpha)
     return 528 + 4 * (size_t)ld + (size_t)ld / 8 + 2 * (size_t)alpha + 16;
 }
 
-template <int W, int MAXT>
+template <int W, int MAXT, bool ASP>
 static cudaError_t launch_tabu_w(const Dev& d, int alpha, int c, cudaStream_t s)
 {
     int nt = (d.n + 4 * W - 1) / (4 * W);
     nt = (nt + 31) / 32 * 32;
     if (nt > MAXT) return cudaErrorInvalidConfiguration;
     const size_t sm = tabu_smem_bytes(d.n, alpha);
-    cudaError_t e = cudaFuncSetAttribute(k_tabu<W, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_tabu<W, MAXT, ASP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_tabu<W, MAXT><<<d.R, nt, sm, s>>>(d, alpha, c);
+    k_tabu<W, MAXT, ASP><<<d.R, nt, sm, s>>>(d, alpha, c);
     note_launch(1);
     return cudaGetLastError();
 }
@@ -294,17 +324,23 @@ int tabu_default_variant(int n)
 }
 
 // variant: index into kTabuVariants; < 0 picks the default.
-cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_t s)
+cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_t s, bool aspiration)
 {
     if (variant < 0) variant = tabu_default_variant(d.n);
     if (!tabu_variant_fits(variant, d.n)) return cudaErrorInvalidConfiguration;
-    switch (variant) {
-        case 0: return launch_tabu_w<1, 1024>(d, alpha, c, s);
-        case 1: return launch_tabu_w<2, 1024>(d, alpha, c, s);
-        case 2: return launch_tabu_w<3, 1024>(d, alpha, c, s);
-        case 3: return launch_tabu_w<4, 1024>(d, alpha, c, s);
-        case 4: return launch_tabu_w<4, 256>(d, alpha, c, s);
-        case 5: return launch_tabu_w<8, 256>(d, alpha, c, s);
+    switch (variant * 2 + (aspiration ? 1 : 0)) {
+        case 0: return launch_tabu_w<1, 1024, false>(d, alpha, c, s);
+        case 1: return launch_tabu_w<1, 1024, true>(d, alpha, c, s);
+        case 2: return launch_tabu_w<2, 1024, false>(d, alpha, c, s);
+        case 3: return launch_tabu_w<2, 1024, true>(d, alpha, c, s);
+        case 4: return launch_tabu_w<3, 1024, false>(d, alpha, c, s);
+        case 5: return launch_tabu_w<3, 1024, true>(d, alpha, c, s);
+        case 6: return launch_tabu_w<4, 1024, false>(d, alpha, c, s);
+        case 7: return launch_tabu_w<4, 1024, true>(d, alpha, c, s);
+        case 8: return launch_tabu_w<4, 256, false>(d, alpha, c, s);
+        case 9: return launch_tabu_w<4, 256, true>(d, alpha, c, s);
+        case 10: return launch_tabu_w<8, 256, false>(d, alpha, c, s);
+        case 11: return launch_tabu_w<8, 256, true>(d, alpha, c, s);
         default: return cudaErrorInvalidValue;
     }
 }

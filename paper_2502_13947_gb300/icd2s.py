@@ -35,7 +35,7 @@ EXPORTS = (
     "icd2s_state_run", "icd2s_mlp_create", "icd2s_mlp_destroy", "icd2s_mlp_set_weights", "icd2s_mlp_get_weights",
     "icd2s_mlp_score", "icd2s_mlp_grad", "icd2s_mlp_train", "icd2s_state_set_mlp", "icd2s_get_features",
     "icd2s_get_hits", "icd2s_log_enable", "icd2s_log_info", "icd2s_log_copy", "icd2s_get_apply_ms",
-    "icd2s_exact_subqubos_batch",
+    "icd2s_exact_subqubos_batch", "icd2s_tabu_aspiration",
 )
 MLP_PARAMS = 4673
 PHASES = ("tabu", "select", "anneal", "apply_anneal", "mutate", "apply_mutate", "best")
@@ -54,7 +54,7 @@ class Params(C.Structure):
         ("w1", C.c_int64), ("w2", C.c_int64), ("w3", C.c_int64), ("mut_mode", C.c_int32), ("mut_rate", C.c_double),
         ("patience", C.c_int32), ("max_iters", C.c_int32), ("use_graph", C.c_int32), ("refresh_every", C.c_int32),
         ("select_mode", C.c_int32), ("stop_at_target", C.c_int32), ("target_E", C.c_int64),
-        ("im_mode", C.c_int32), ("ablation", C.c_int32),
+        ("im_mode", C.c_int32), ("ablation", C.c_int32), ("aspiration", C.c_int32), ("reserved", C.c_int32 * 3),
     ]
 
 
@@ -135,6 +135,7 @@ def lib():
                 "icd2s_get_refresh_ms": (C.c_int, [vp, P(f64)]),
                 "icd2s_get_apply_ms": (C.c_int, [vp, P(f64)]),
                 "icd2s_exact_subqubos_batch": (C.c_int, [vp, vp, vp, i32, i32, vp, vp, vp]),
+                "icd2s_tabu_aspiration": (C.c_int, [vp, i32, i32, vp]),
                 "icd2s_state_run": (C.c_int, [vp, P(Params), vp, vp, P(Stats), vp, vp]),
                 "icd2s_mlp_create": (C.c_int, [u64, P(vp)]),
                 "icd2s_mlp_destroy": (C.c_int, [vp]),
@@ -242,6 +243,10 @@ def icd2s_get_best(st, n: int):
 
 def icd2s_tabu(st, alpha: int, c: int, stream=0) -> None:
     _check(lib().icd2s_tabu(st, alpha, c, _s(stream)))
+
+
+def icd2s_tabu_aspiration(st, alpha: int, c: int, stream=0) -> None:
+    _check(lib().icd2s_tabu_aspiration(st, alpha, c, _s(stream)))
 
 
 def icd2s_get_tabu(st, R: int, n: int):

@@ -104,6 +104,46 @@ def test_tabu(L, orc, n, R, alpha, c, density):
     P.close()
 
 
+@pytest.mark.parametrize("n,R,alpha,c,variant", [(40, 3, 160, 39, -1), (300, 4, 900, 60, -1), (300, 2, 900, 60, 4),
+                                                 (2500, 2, 5000, 16, -1), (5000, 2, 4000, 33, -1),
+                                                 (5000, 2, 4000, 33, 3)])
+def test_tabu_with_aspiration(L, orc, n, R, alpha, c, variant):
+    """The aspiration criterion (reading S4) in several kernel shapes; long
+    tenures make tabu moves that beat the best visited admissible."""
+    P = Problem(n, 0.5, n + 1, R=R)
+    X0 = random_solutions(n, R, n + c)
+    P.load(X0)
+    if variant >= 0:
+        I.icd2s_set_tuning(P.st, tabu_variant=variant)
+    I.icd2s_tabu_aspiration(P.st, alpha, c)
+    x, g, E = P.state()
+    T, Cm = I.icd2s_get_tabu(P.st, R, n)
+    for p in range(R):
+        xo, Eo, To, Co, _ = orc.tabu_asp(P.Q, X0[p], alpha, c)
+        assert np.array_equal(x[p], xo), p
+        assert E[p] == Eo
+        assert np.array_equal(T[p], To) and np.array_equal(Cm[p], Co)
+        assert np.array_equal(g[p], orc.gains(P.Q, xo))
+    P.close()
+
+
+def test_tabu_with_aspiration_when_every_move_is_tabu(L, orc):
+    """Tenure c = n: every move becomes tabu and the kernel takes the
+    unmasked arg-min like the oracle (instances where this happens)."""
+    for seed in (0, 6, 12, 14, 16, 18):
+        n = 4 + seed % 5
+        P = Problem(n, 1.0, 1000 + seed, R=1)
+        X0 = random_solutions(n, 1, seed)
+        P.load(X0)
+        I.icd2s_tabu_aspiration(P.st, 8 * n, n)
+        x, g, E = P.state()
+        T, Cm = I.icd2s_get_tabu(P.st, 1, n)
+        xo, Eo, To, Co, _ = orc.tabu_asp(P.Q, X0[0], 8 * n, n)
+        assert np.array_equal(x[0], xo) and E[0] == Eo, seed
+        assert np.array_equal(T[0], To) and np.array_equal(Cm[0], Co), seed
+        P.close()
+
+
 # ----------------------------------------------------------------------------- Eq. 6-8, Alg. 3, selection
 @pytest.mark.parametrize("n,R,K,m_min,m_max", [(500, 6, 3, 8, 40), (333, 4, 1, 64, 64), (2500, 3, 16, 32, 150)])
 def test_control_parameters_and_selection(L, orc, n, R, K, m_min, m_max):

@@ -68,6 +68,14 @@ def test_run_ablations(L, orc, ablation):
     _compare_runs(orc, Q, lp, 23)
 
 
+def test_run_with_aspiration(L, orc):
+    n = 120
+    Q = make_qubo(n, 0.4, 55)
+    lp = lib_params(I, n, z=4, K=1, m_min=16, m_max=16, m_init=16, alpha=3 * n, c=40, sweeps=16, T_max=300.0,
+                    mut_mode=0, patience=0, max_iters=8, aspiration=1)
+    _compare_runs(orc, Q, lp, 31)
+
+
 def test_run_with_patience_and_constant_rate(L, orc):
     n = 150
     Q = make_qubo(n, 0.3, 5)
