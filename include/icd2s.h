@@ -161,6 +161,11 @@ int icd2s_default_params(int32_t n, icd2s_params* out);
 int icd2s_qubo_create(const int8_t* Q_host, int32_t n, icd2s_qubo** out);
 int icd2s_qubo_destroy(icd2s_qubo* q);
 int icd2s_qubo_size(const icd2s_qubo* q, int32_t* n_out);
+/* 2 max_j sum_i |Q_ij|, computed once at creation: no gain
+ * g_j = (1 - 2x_j)(Q_jj + 2 sum_{i != j} Q_ij x_i) of any x exceeds it in
+ * magnitude (Section 2.4).  The Tabu search uses it to decide whether a move
+ * fits a 32-bit key. */
+int icd2s_qubo_gain_bound(const icd2s_qubo* q, int64_t* bound_out);
 
 /* Eq. 1 for `count` binary rows x_dev[count][n] (dense, row stride n, values
  * 0/1) into E_dev[count] (int64).  Enqueued on `stream`. */
@@ -381,13 +386,17 @@ int icd2s_get_apply_ms(icd2s_state* st, double* ms);
  * computes the same results bit for bit).  tabu_variant indexes the Tabu
  * kernel's (variables per thread, block size) builds, -1 = default;
  * anneal_warps_per_cta = subQUBOs per CTA of the Ising-machine kernel,
- * 0 = default. */
+ * 0 = default.  The Tabu search packs a move into one 32-bit key (one
+ * reduction per warp and per block) when every gain of the instance fits
+ * beside the index: 2 max_j sum_i |Q_ij| + 1 < 2^(30 - b), b = bits of n;
+ * tabu_wide_keys = 1 keeps the two-reduction 64-bit keys anyway. */
 typedef struct icd2s_tuning {
     int32_t tabu_variant;
     int32_t anneal_warps_per_cta;
     int32_t refresh_bn;       /* tensor-core refresh: replicas per tile (128 or 256; 0 = default) */
     int32_t refresh_splits;   /* tensor-core refresh: K splits (0 = about one CTA per SM) */
-    int32_t reserved[4];
+    int32_t tabu_wide_keys;   /* 0 = compact Tabu keys where they apply, 1 = never */
+    int32_t reserved[3];
 } icd2s_tuning;
 int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t);
 int icd2s_get_tuning(icd2s_state* st, icd2s_tuning* t);

@@ -98,6 +98,7 @@ struct icd2s_qubo {
     int32_t* diag = nullptr;
     int32_t* eta = nullptr;
     int32_t* etahat = nullptr;
+    long long gain_bound = 0;  // 2 max_j sum_i |Q_ij|: bounds every gain of every solution
     // scratch of icd2s_energy (grown on demand)
     int cap = 0;
     uint8_t* xpad = nullptr;
@@ -335,15 +336,17 @@ int icd2s_qubo_create(const int8_t* Q_host, int32_t n, icd2s_qubo** out)
     cudaError_t e;
     if ((e = dalloc(&q->Q, (size_t)n * q->ld)) != cudaSuccess || (e = dalloc(&q->diag, q->ld)) != cudaSuccess ||
         (e = dalloc(&q->eta, q->ld)) != cudaSuccess || (e = dalloc(&q->etahat, q->ld)) != cudaSuccess ||
-        (e = dalloc(&mism, 1)) != cudaSuccess)
+        (e = dalloc(&mism, 2)) != cudaSuccess)
         return bail(fail(ICD2S_ERR_OOM, "device allocation failed: %s", cudaGetErrorString(e)));
-    int bad = 0;
+    int got[2] = {0, 0};  // symmetry mismatches, max_j eta_j
     if ((e = cudaMemset(q->Q, 0, (size_t)n * q->ld)) == cudaSuccess &&
         (e = cudaMemcpy2D(q->Q, q->ld, Q_host, n, n, n, cudaMemcpyHostToDevice)) == cudaSuccess &&
-        (e = cudaMemset(mism, 0, sizeof(int))) == cudaSuccess &&
-        (e = launch_prepare(q->Q, n, q->ld, q->eta, q->etahat, q->diag, mism, 0)) == cudaSuccess &&
-        (e = cudaMemcpy(&bad, mism, sizeof(int), cudaMemcpyDeviceToHost)) == cudaSuccess) {
+        (e = cudaMemset(mism, 0, 2 * sizeof(int))) == cudaSuccess &&
+        (e = launch_prepare(q->Q, n, q->ld, q->eta, q->etahat, q->diag, mism, mism + 1, 0)) == cudaSuccess &&
+        (e = cudaMemcpy(got, mism, 2 * sizeof(int), cudaMemcpyDeviceToHost)) == cudaSuccess) {
         cudaFree(mism);
+        const int bad = got[0];
+        q->gain_bound = 2LL * got[1];
         if (bad) return bail(fail(ICD2S_ERR_ASYMMETRIC, "Q is not symmetric (%d mismatched entries)", bad));
         *out = q;
         return ICD2S_OK;
@@ -369,6 +372,13 @@ int icd2s_qubo_size(const icd2s_qubo* q, int32_t* n_out)
     return ICD2S_OK;
 }
 
+int icd2s_qubo_gain_bound(const icd2s_qubo* q, int64_t* bound_out)
+{
+    REQ(q && bound_out, ICD2S_ERR_ARG, "NULL argument");
+    *bound_out = q->gain_bound;
+    return ICD2S_OK;
+}
+
 int icd2s_energy(icd2s_qubo* q, const uint8_t* x_dev, int32_t count, int64_t* E_dev, void* stream)
 {
     REQ(q && (count == 0 || (x_dev && E_dev)), ICD2S_ERR_ARG, "NULL argument");
@@ -386,6 +396,7 @@ int icd2s_energy(icd2s_qubo* q, const uint8_t* x_dev, int32_t count, int64_t* E_
     }
     Dev d{};
     d.Q = q->Q; d.diag = q->diag; d.etahat = q->etahat; d.n = q->n; d.ld = q->ld; d.R = count;
+    d.gain_bound = q->gain_bound;
     CK(launch_pad_rows(x_dev, q->n, count, q->xpad, q->ld, s));
     CK(launch_recompute(d, q->xpad, q->ld, count, q->hpad, E_dev, s));
     return ICD2S_OK;
@@ -416,6 +427,7 @@ int icd2s_state_create(icd2s_qubo* q, int32_t replicas, uint64_t seed, icd2s_sta
     }
     Dev& d = st->d;
     d.Q = q->Q; d.diag = q->diag; d.etahat = q->etahat; d.n = q->n; d.ld = q->ld; d.R = replicas;
+    d.gain_bound = q->gain_bound;
     d.X = st->X; d.G = st->G; d.E = st->E; d.T = st->T; d.C = st->C; d.gamma = st->gamma; d.A = st->A;
     d.delta = st->delta; d.order = st->order; d.sel = st->sel; d.FL = st->FL; d.FCNT = st->FCNT;
     d.DEACC = st->DEACC; d.DONE = st->DONE; d.best_x = st->best_x; d.best_E = st->best_E; d.flags = st->flags;
@@ -516,7 +528,7 @@ int icd2s_tabu(icd2s_state* st, int32_t alpha, int32_t c, void* stream)
     REQ(alpha >= 0, ICD2S_ERR_ARG, "alpha < 0");
     REQ(c >= 1 && c <= n, ICD2S_ERR_ARG, "tenure c=%d outside 1..n", c);
     REQ(tabu_smem_bytes(n, alpha) <= 227 * 1024, ICD2S_ERR_RANGE, "alpha=%d too large for n=%d", alpha, n);
-    CK(launch_tabu(st->d, alpha, c, st->tune.tabu_variant, S(stream)));
+    CK(launch_tabu(st->d, alpha, c, st->tune.tabu_variant, S(stream), false, st->tune.tabu_wide_keys != 0));
     return ICD2S_OK;
 }
 
@@ -527,7 +539,7 @@ int icd2s_tabu_aspiration(icd2s_state* st, int32_t alpha, int32_t c, void* strea
     REQ(alpha >= 0, ICD2S_ERR_ARG, "alpha < 0");
     REQ(c >= 1 && c <= n, ICD2S_ERR_ARG, "tenure c=%d outside 1..n", c);
     REQ(tabu_smem_bytes(n, alpha) <= 227 * 1024, ICD2S_ERR_RANGE, "alpha=%d too large for n=%d", alpha, n);
-    CK(launch_tabu(st->d, alpha, c, st->tune.tabu_variant, S(stream), true));
+    CK(launch_tabu(st->d, alpha, c, st->tune.tabu_variant, S(stream), true, st->tune.tabu_wide_keys != 0));
     return ICD2S_OK;
 }
 
@@ -778,7 +790,8 @@ static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* tra
     const bool feats = wants_features(st, p);
     if (feats && (rc = ensure_features(st, s))) return rc;
     mark(st, 0, 0, s);
-    CK(launch_tabu(st->d, p->alpha, p->c, st->tune.tabu_variant, s, p->aspiration != 0));  // Algorithm 1
+    CK(launch_tabu(st->d, p->alpha, p->c, st->tune.tabu_variant, s, p->aspiration != 0,
+                   st->tune.tabu_wide_keys != 0));  // Algorithm 1
     mark(st, 0, 1, s);
     CK(launch_best(st->d, trace_it, 0, nullptr, s));
     mark(st, 1, 0, s);
@@ -929,6 +942,8 @@ int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t)
         t->refresh_splits);
     REQ(t->anneal_warps_per_cta >= 0 && t->anneal_warps_per_cta <= 4, ICD2S_ERR_ARG,
         "anneal_warps_per_cta=%d outside 0..4", t->anneal_warps_per_cta);
+    REQ(t->tabu_wide_keys == 0 || t->tabu_wide_keys == 1, ICD2S_ERR_ARG, "tabu_wide_keys=%d must be 0 or 1",
+        t->tabu_wide_keys);
     st->tune = *t;
     ++st->gen;  // launch configurations changed: re-capture
     return ICD2S_OK;
@@ -986,7 +1001,7 @@ int icd2s_autotune(icd2s_state* st, const icd2s_params* p, icd2s_tuning* chosen,
         for (int rep = 0; rep < 2; ++rep) {
             if ((rc = restore())) return rc;
             CK(cudaEventRecord(e0, s));
-            CK(launch_tabu(st->d, alpha, p->c, v, s));
+            CK(launch_tabu(st->d, alpha, p->c, v, s, p->aspiration != 0, st->tune.tabu_wide_keys != 0));
             CK(cudaEventRecord(e1, s));
             CK(cudaEventSynchronize(e1));
             float ms = 0.f;

@@ -84,6 +84,7 @@ struct Dev {
     int32_t* H; float* F; float* score;
     int32_t* ACC; unsigned* TT; int apply_splits;     // split write-back: partial sums, tile tickets
     uint32_t k0, k1; // Philox key = seed halves
+    long long gain_bound;  // max_j 2 sum_i |Q_ij| >= |g_j| for every x
 };
 
 // Counts kernel launches (process-wide, for reporting).
@@ -93,14 +94,19 @@ void note_launch(int kernels);
 void set_error_message(const char* msg);
 
 // ---- launchers (each returns cudaGetLastError() of its launch) ----
+// eta_max[0] receives max_j eta_j (eta_j = sum_i |Q_ij|).
 cudaError_t launch_prepare(const int8_t* Q, int n, int ld, int32_t* eta, int32_t* etahat, int32_t* diag,
-                           int* mismatches, cudaStream_t s);
+                           int* mismatches, int* eta_max, cudaStream_t s);
 cudaError_t launch_init_x(const Dev& d, cudaStream_t s);
 cudaError_t launch_recompute(const Dev& d, const uint8_t* X, int ldx, int R, int32_t* G, int64_t* E,
                              cudaStream_t s);  // gains + energies of X (padded rows)
 cudaError_t launch_pad_rows(const uint8_t* src, int n, int rows, uint8_t* dst, int ld, cudaStream_t s);
 // variant: kernel shape (< 0: default); aspiration: Tabu with the aspiration criterion.
-cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_t s, bool aspiration = false);
+// wide_keys: the two-reduction keys even where the compact ones apply.
+cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_t s, bool aspiration = false,
+                        bool wide_keys = false);
+// Shift of the compact Tabu keys for n and the instance's gain bound (0: they do not apply).
+int tabu_key_shift(int n, long long gain_bound);
 size_t tabu_smem_bytes(int n, int alpha);
 cudaError_t launch_gamma(const Dev& d, cudaStream_t s);
 // Iteration context read by the kernels of a captured outer iteration (a CUDA

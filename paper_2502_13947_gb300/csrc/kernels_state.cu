@@ -320,7 +320,8 @@ __global__ void k_eta(const int8_t* __restrict__ Q, int n, int ld, int32_t* eta,
     diag[j] = Q[(size_t)j * ld + j];
 }
 
-__global__ __launch_bounds__(1024) void k_etahat(const int32_t* __restrict__ eta, int n, int ld, int32_t* etahat)
+__global__ __launch_bounds__(1024) void k_etahat(const int32_t* __restrict__ eta, int n, int ld, int32_t* etahat,
+                                                 int* eta_max)
 {
     __shared__ int red[32];
     int mx = 0;
@@ -330,12 +331,13 @@ __global__ __launch_bounds__(1024) void k_etahat(const int32_t* __restrict__ eta
     __syncthreads();
     mx = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, red[w]);
+    if (threadIdx.x == 0) *eta_max = mx;
     for (int j = threadIdx.x; j < ld; j += blockDim.x)
         etahat[j] = (j < n && mx > 0) ? (int32_t)(((long long)eta[j] * 65536) / mx) : 0;
 }
 
 cudaError_t launch_prepare(const int8_t* Q, int n, int ld, int32_t* eta, int32_t* etahat, int32_t* diag,
-                           int* mismatches, cudaStream_t s)
+                           int* mismatches, int* eta_max, cudaStream_t s)
 {
     const int tiles = (n + 31) / 32;
     k_symcheck<<<dim3(tiles, tiles), dim3(32, 8), 0, s>>>(Q, n, ld, mismatches);
@@ -345,7 +347,7 @@ cudaError_t launch_prepare(const int8_t* Q, int n, int ld, int32_t* eta, int32_t
     k_eta<<<(ld + 255) / 256, 256, 0, s>>>(Q, n, ld, eta, diag);
     note_launch(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_etahat<<<1, 1024, 0, s>>>(eta, n, ld, etahat);
+    k_etahat<<<1, 1024, 0, s>>>(eta, n, ld, etahat, eta_max);
     note_launch(1);
     return cudaGetLastError();
 }

@@ -24,6 +24,12 @@
 //      minima; every thread reduces those itself, so the loop has exactly one
 //      barrier.
 // Ties go to the lowest index, exactly as a scan in index order would.
+// Compact keys (CK): when every gain of the instance is known to satisfy
+// |g| < 2^(31 - sh) - 1 with sh = 1 + (bits of n), the whole move fits one
+// 32-bit key (g + 2^(31 - sh)) << sh | j << 1 | x_j, so the warp and the block
+// each take their arg-min with a single redux.sync and the key carries x_i.
+// The bound |g_j| <= |Q_jj| + 2 sum_{i != j} |Q_ij| <= 2 sum_i |Q_ij| holds for
+// every x, so it is computed once per instance.
 // The objective OV is tracked in int64 by thread 0, which also keeps the toggle
 // counts and the move log and publishes the best visit at the end.  The move
 // log (uint16 per iteration) stays in shared memory; after the last
@@ -52,12 +58,13 @@ __device__ __forceinline__ unsigned long long pack_key(unsigned hi, unsigned lo)
 // ASP: the aspiration criterion (reading S4): a tabu variable is also a
 // candidate when its move would beat the best objective visited so far, i.e.
 // g < OVmin - OV, which in key units is (key >> 5) < OVmin - OV + bias.
-template <int W, int MAXT, bool ASP>
-__global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
+template <int W, int MAXT, bool ASP, bool CK>
+__global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh)
 {
     static_assert(4 * W <= (1 << kKeyShift), "the local index must fit the key");
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* wkeys = reinterpret_cast<unsigned long long*>(smem);         // [2][32]
+    unsigned* wkeys32 = reinterpret_cast<unsigned*>(smem);                            // [2][32] (CK)
     int* nF = reinterpret_cast<int*>(smem + 512);                                     // [1]; +520: best visit
     int32_t* Ts = reinterpret_cast<int32_t*>(smem + 528);                             // [ld]
     uint32_t* undo = reinterpret_cast<uint32_t*>(smem + 528 + 4 * (size_t)d.ld);      // [ld / 32]
@@ -75,7 +82,12 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
     if (tid == 0) *nF = 0;
 
     int gf[W][4], fa[W][4];
-    unsigned s32[W][4];  // 32 (1 - 2 x_j) mod 2^32: the key is gf * s32 + const, one multiply-add
+    // 2^shift (1 - 2 x_j) mod 2^32: the key is gf * s32 + kc, one multiply-add
+    unsigned s32[W][4];
+    // CK: kc = bias << sh | j << 1 | x_j; otherwise the constant bias << 5 | local index
+    unsigned kc[W][4];
+    const unsigned cbias = CK ? 1u << (31 - sh) : kKeyBias;
+    const unsigned imask = CK ? (1u << (sh - 1)) - 1u : 0u;  // CK: the index field (2^(sh-1) > n)
     unsigned xb = 0;  // bit 4w+b = x of the owned variable
 #pragma unroll
     for (int w = 0; w < W; ++w) {
@@ -92,7 +104,10 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
             const unsigned xj = (xv >> (8 * b)) & 1u;
             xb |= xj << (4 * w + b);
             gf[w][b] = xj ? -gv[b] : gv[b];
-            s32[w][b] = xj ? (unsigned)-32 : 32u;
+            const unsigned one = CK ? 1u << sh : 1u << kKeyShift;
+            s32[w][b] = xj ? 0u - one : one;
+            kc[w][b] = CK ? (cbias << sh) | ((unsigned)(j0 + b) << 1) | xj
+                          : (kKeyBias << kKeyShift) | (unsigned)(4 * w + b);
             fa[w][b] = (j0 + b < n) ? 0 : INT_MAX;  // padding never becomes free
         }
     }
@@ -104,12 +119,16 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
         for (int w = 0; w < W; ++w)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const unsigned k = 4 * w + b;
-                // ((g + bias) << 5) | k with g = (1 - 2x) gf, as one multiply-add modulo 2^32
-                const unsigned key = (unsigned)gf[w][b] * s32[w][b] + ((kKeyBias << kKeyShift) | k);
-                const bool ok = itn >= fa[w][b] || (ASP && (key >> kKeyShift) < ulim);
+                // ((g + bias) << shift) | low bits with g = (1 - 2x) gf, one multiply-add modulo 2^32
+                const unsigned key = (unsigned)gf[w][b] * s32[w][b] + kc[w][b];
+                const bool ok = itn >= fa[w][b] || (ASP && (key >> (CK ? sh : kKeyShift)) < ulim);
                 tk = ok ? min(tk, key) : tk;
             }
+        if constexpr (CK) {
+            const unsigned wk = __reduce_min_sync(0xffffffffu, tk);
+            if (lane == 0) wkeys32[slot * 32 + warp] = wk;
+            return;
+        }
         const unsigned wg = __reduce_min_sync(0xffffffffu, tk >> kKeyShift);
         const unsigned k = tk & ((1u << kKeyShift) - 1u);
         const unsigned j = 4u * (unsigned)(tid + (int)(k >> 2) * NT) + (k & 3u);
@@ -118,6 +137,10 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
         if (lane == 0) wkeys[slot * 32 + warp] = pack_key(wg, wj);
     };
     auto block_argmin = [&](int slot) -> unsigned long long {
+        if constexpr (CK) {
+            const unsigned k = lane < NW ? wkeys32[slot * 32 + lane] : 0xffffffffu;
+            return __reduce_min_sync(0xffffffffu, k);
+        }
         const unsigned long long k = lane < NW ? wkeys[slot * 32 + lane] : ~0ull;
         const unsigned hi = __reduce_min_sync(0xffffffffu, (unsigned)(k >> 32));
         const unsigned lo = __reduce_min_sync(0xffffffffu, (unsigned)(k >> 32) == hi ? (unsigned)k : 0xffffffffu);
@@ -126,10 +149,10 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
 
     long long OV = d.E[p], OVmin = OV;
     int best_it = -1;
-    // aspiration limit in key units: clamp(OVmin - OV + bias, 0, 2^27)
+    // aspiration limit in key units: clamp(OVmin - OV + bias, 0, 2 bias)
     auto asp_limit = [&]() -> unsigned {
-        const long long v = OVmin - OV + (long long)kKeyBias;
-        return v <= 0 ? 0u : (v >= (1LL << 27) ? (1u << 27) : (unsigned)v);
+        const long long v = OVmin - OV + (long long)cbias;
+        return v <= 0 ? 0u : (v >= 2LL * cbias ? 2u * cbias : (unsigned)v);
     };
 
     __syncthreads();  // shared-memory clears visible
@@ -138,8 +161,10 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
     unsigned long long key = block_argmin(0);
 
     for (int it = 0; it < alpha; ++it) {
-        const int gi = (int)(unsigned)(key >> 32) - (int)kKeyBias;
-        const unsigned jx = (unsigned)key;
+        // the chosen move: its gain, index and value (CK: no candidate is the key ~0,
+        // whose index field 2^(sh-1) - 1 >= n; otherwise its index half is ~0)
+        const int gi = CK ? (int)((unsigned)key >> sh) - (int)cbias : (int)(unsigned)(key >> 32) - (int)kKeyBias;
+        const unsigned jx = CK ? (unsigned)key & (2u * imask + 1u) : (unsigned)key;
         const int i = (int)(jx >> 1);
         if (i >= n) {  // no move at all (a warp without candidates publishes index ~0): stop, uniformly
             if (tid == 0) d.flags[2] = 1;
@@ -170,6 +195,7 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
                         gf[w][b] -= (int)(int8_t)(rv[w] >> (8 * b)) * si2;
                         xb ^= 1u << (4 * w + b);
                         s32[w][b] = 0u - s32[w][b];
+                        if (CK) kc[w][b] ^= 1u;
                         // C += c: free again c iterations after the later of now and the
                         // iteration it was to become free (a tabu move, by aspiration)
                         fa[w][b] = max(fa[w][b], it) + c;
@@ -191,7 +217,7 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c)
             // A variable moved again while tabu keeps c more iterations of tabu
             // memory, so every move can be tabu and none aspirated: then the
             // unmasked arg-min (reading S6).  No warp had a candidate iff the
-            // index half of the block's key is all ones.  key is uniform.
+            // block's key (its index half without CK) is all ones.  key is uniform.
             if ((unsigned)key == 0xffffffffu && it + 1 < alpha) {
                 __syncthreads();                      // every thread has read this slot
                 warp_argmin(INT_MAX - 1, slot, 0u);   // every real variable (padding stays out)
@@ -283,16 +309,16 @@ size_t tabu_smem_bytes(int n, int alpha)
     return 528 + 4 * (size_t)ld + (size_t)ld / 8 + 2 * (size_t)alpha + 16;
 }
 
-template <int W, int MAXT, bool ASP>
-static cudaError_t launch_tabu_w(const Dev& d, int alpha, int c, cudaStream_t s)
+template <int W, int MAXT, bool ASP, bool CK>
+static cudaError_t launch_tabu_w(const Dev& d, int alpha, int c, int sh, cudaStream_t s)
 {
     int nt = (d.n + 4 * W - 1) / (4 * W);
     nt = (nt + 31) / 32 * 32;
     if (nt > MAXT) return cudaErrorInvalidConfiguration;
     const size_t sm = tabu_smem_bytes(d.n, alpha);
-    cudaError_t e = cudaFuncSetAttribute(k_tabu<W, MAXT, ASP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_tabu<W, MAXT, ASP, CK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_tabu<W, MAXT, ASP><<<d.R, nt, sm, s>>>(d, alpha, c);
+    k_tabu<W, MAXT, ASP, CK><<<d.R, nt, sm, s>>>(d, alpha, c, sh);
     note_launch(1);
     return cudaGetLastError();
 }
@@ -323,24 +349,41 @@ int tabu_default_variant(int n)
     return -1;
 }
 
-// variant: index into kTabuVariants; < 0 picks the default.
-cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_t s, bool aspiration)
+int tabu_key_shift(int n, long long gain_bound)
+{
+    int ib = 0;
+    while ((1 << ib) <= n) ++ib;   // 2^ib > n: the index field never reads as a variable when all ones
+    const int sh = ib + 1;
+    return sh <= 30 && gain_bound + 1 < (1LL << (31 - sh)) ? sh : 0;
+}
+
+// variant: index into kTabuVariants; < 0 picks the default.  Compact keys are
+// used when the instance's gain bound allows them, unless wide_keys is set.
+cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_t s, bool aspiration, bool wide_keys)
 {
     if (variant < 0) variant = tabu_default_variant(d.n);
     if (!tabu_variant_fits(variant, d.n)) return cudaErrorInvalidConfiguration;
-    switch (variant * 2 + (aspiration ? 1 : 0)) {
-        case 0: return launch_tabu_w<1, 1024, false>(d, alpha, c, s);
-        case 1: return launch_tabu_w<1, 1024, true>(d, alpha, c, s);
-        case 2: return launch_tabu_w<2, 1024, false>(d, alpha, c, s);
-        case 3: return launch_tabu_w<2, 1024, true>(d, alpha, c, s);
-        case 4: return launch_tabu_w<3, 1024, false>(d, alpha, c, s);
-        case 5: return launch_tabu_w<3, 1024, true>(d, alpha, c, s);
-        case 6: return launch_tabu_w<4, 1024, false>(d, alpha, c, s);
-        case 7: return launch_tabu_w<4, 1024, true>(d, alpha, c, s);
-        case 8: return launch_tabu_w<4, 256, false>(d, alpha, c, s);
-        case 9: return launch_tabu_w<4, 256, true>(d, alpha, c, s);
-        case 10: return launch_tabu_w<8, 256, false>(d, alpha, c, s);
-        case 11: return launch_tabu_w<8, 256, true>(d, alpha, c, s);
+    // the 1024-thread shapes with 12 and 16 variables per thread would spill the
+    // per-variable key constants: they keep the wide keys
+    const bool compact_fits = kTabuVariants[variant].maxt < 1024 || kTabuVariants[variant].W <= 2;
+    const int sh = wide_keys || !compact_fits ? 0 : tabu_key_shift(d.n, d.gain_bound);
+    const int sel = (variant * 2 + (aspiration ? 1 : 0)) * 2 + (sh ? 1 : 0);
+    switch (sel) {
+#define ICD2S_TABU_WIDE(V, W, MAXT)                                                      \
+        case 4 * V + 0: return launch_tabu_w<W, MAXT, false, false>(d, alpha, c, sh, s); \
+        case 4 * V + 2: return launch_tabu_w<W, MAXT, true, false>(d, alpha, c, sh, s);
+#define ICD2S_TABU_BOTH(V, W, MAXT)                                                      \
+        ICD2S_TABU_WIDE(V, W, MAXT)                                                      \
+        case 4 * V + 1: return launch_tabu_w<W, MAXT, false, true>(d, alpha, c, sh, s);  \
+        case 4 * V + 3: return launch_tabu_w<W, MAXT, true, true>(d, alpha, c, sh, s);
+        ICD2S_TABU_BOTH(0, 1, 1024)
+        ICD2S_TABU_BOTH(1, 2, 1024)
+        ICD2S_TABU_WIDE(2, 3, 1024)
+        ICD2S_TABU_WIDE(3, 4, 1024)
+        ICD2S_TABU_BOTH(4, 4, 256)
+        ICD2S_TABU_BOTH(5, 8, 256)
+#undef ICD2S_TABU_BOTH
+#undef ICD2S_TABU_WIDE
         default: return cudaErrorInvalidValue;
     }
 }

@@ -26,7 +26,7 @@ OK, ERR_ARG, ERR_ASYMMETRIC, ERR_RANGE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_INVA
 # every entry point declared in include/icd2s.h
 EXPORTS = (
     "icd2s_last_error", "icd2s_version", "icd2s_default_params", "icd2s_qubo_create", "icd2s_qubo_destroy",
-    "icd2s_qubo_size", "icd2s_energy", "icd2s_state_create", "icd2s_state_destroy", "icd2s_state_load",
+    "icd2s_qubo_size", "icd2s_qubo_gain_bound", "icd2s_energy", "icd2s_state_create", "icd2s_state_destroy", "icd2s_state_load",
     "icd2s_get_state", "icd2s_get_best", "icd2s_tabu", "icd2s_get_tabu", "icd2s_select_subqubos",
     "icd2s_get_control", "icd2s_anneal_subqubos_batch", "icd2s_apply_flips_update_gains", "icd2s_mutate",
     "icd2s_best_update", "icd2s_initial_pass", "icd2s_step", "icd2s_step_host", "icd2s_run", "icd2s_tables",
@@ -105,6 +105,7 @@ def lib():
                 "icd2s_qubo_create": (C.c_int, [vp, i32, P(vp)]),
                 "icd2s_qubo_destroy": (C.c_int, [vp]),
                 "icd2s_qubo_size": (C.c_int, [vp, P(i32)]),
+                "icd2s_qubo_gain_bound": (C.c_int, [vp, P(C.c_int64)]),
                 "icd2s_energy": (C.c_int, [vp, vp, i32, vp, vp]),
                 "icd2s_state_create": (C.c_int, [vp, i32, u64, P(vp)]),
                 "icd2s_state_destroy": (C.c_int, [vp]),
@@ -202,6 +203,12 @@ def icd2s_qubo_size(h) -> int:
     n = C.c_int32()
     _check(lib().icd2s_qubo_size(h, C.byref(n)))
     return n.value
+
+
+def icd2s_qubo_gain_bound(h) -> int:
+    b = C.c_int64()
+    _check(lib().icd2s_qubo_gain_bound(h, C.byref(b)))
+    return b.value
 
 
 def icd2s_energy(q, x_dev: int, count: int, E_dev: int, stream=0) -> None:
@@ -456,18 +463,18 @@ def icd2s_apply_flips_static(Q_dev: int, n: int, ld: int, replicas: int, flips_d
 
 class Tuning(C.Structure):
     _fields_ = [("tabu_variant", C.c_int32), ("anneal_warps_per_cta", C.c_int32), ("refresh_bn", C.c_int32),
-                ("refresh_splits", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("refresh_splits", C.c_int32), ("tabu_wide_keys", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 def _tuning_dict(t):
     return dict(tabu_variant=t.tabu_variant, anneal_warps_per_cta=t.anneal_warps_per_cta,
-                refresh_bn=t.refresh_bn, refresh_splits=t.refresh_splits)
+                refresh_bn=t.refresh_bn, refresh_splits=t.refresh_splits, tabu_wide_keys=t.tabu_wide_keys)
 
 
 def icd2s_set_tuning(st, tabu_variant: int = -1, anneal_warps_per_cta: int = 0, refresh_bn: int = 0,
-                     refresh_splits: int = 0) -> None:
+                     refresh_splits: int = 0, tabu_wide_keys: int = 0) -> None:
     t = Tuning(tabu_variant=tabu_variant, anneal_warps_per_cta=anneal_warps_per_cta, refresh_bn=refresh_bn,
-               refresh_splits=refresh_splits)
+               refresh_splits=refresh_splits, tabu_wide_keys=tabu_wide_keys)
     _check(lib().icd2s_set_tuning(st, C.byref(t)))
 
 

@@ -144,6 +144,113 @@ def test_tabu_with_aspiration_when_every_move_is_tabu(L, orc):
         P.close()
 
 
+# ----------------------------------------------------------------------------- Tabu keys
+def _compact_shift(n, bound):
+    """Shift of the one-reduction Tabu keys: the index field holds n itself
+    (2^b > n), and g + 2^(31 - sh) must stay inside [1, 2^(32 - sh) - 2]."""
+    sh = int(n).bit_length() + 1
+    return sh if bound + 1 < (1 << (31 - sh)) else 0
+
+
+def _tabu_both_keys(P, X0, alpha, c, asp, variant=-1):
+    """Runs the search with the compact keys (where the instance allows them)
+    and with the wide keys from the same start; returns both results."""
+    out = []
+    for wide in (0, 1):
+        P.load(X0)
+        I.icd2s_set_tuning(P.st, tabu_variant=variant, tabu_wide_keys=wide)
+        (I.icd2s_tabu_aspiration if asp else I.icd2s_tabu)(P.st, alpha, c)
+        out.append(P.state() + I.icd2s_get_tabu(P.st, P.R, P.n))
+    return out
+
+
+def _check_tabu(orc, Q, X0, alpha, c, asp, res):
+    x, g, E, T, Cm = res
+    for p in range(X0.shape[0]):
+        xo, Eo, To, Co, _ = orc.tabu_asp(Q, X0[p], alpha, c, aspiration=asp)
+        assert np.array_equal(x[p], xo) and E[p] == Eo, p
+        assert np.array_equal(T[p], To) and np.array_equal(Cm[p], Co), p
+        assert np.array_equal(g[p], orc.gains(Q, xo)), p
+
+
+@pytest.mark.parametrize("n,density,seed", [(40, 1.0, 2), (2500, 0.1, 3), (5000, 0.5, 4), (700, 1.0, 5)])
+def test_gain_bound(L, orc, n, density, seed):
+    """icd2s_qubo_gain_bound = 2 max_j sum_i |Q_ij|, and no gain of the
+    sampled solutions (nor of the worst-case solution of the heaviest column)
+    exceeds it."""
+    Q = make_qubo(n, density, seed)
+    q = I.icd2s_qubo_create(Q)
+    bound = I.icd2s_qubo_gain_bound(q)
+    I.icd2s_qubo_destroy(q)
+    colsum = np.abs(Q.astype(np.int64)).sum(axis=0)
+    assert bound == 2 * int(colsum.max())
+    j = int(colsum.argmax())
+    worst = (Q[:, j] > 0).astype(np.uint8)   # every positive coupling of j on, j off
+    worst[j] = 0
+    for x in list(random_solutions(n, 4, seed)) + [worst]:
+        assert int(np.abs(orc.gains(Q, x).astype(np.int64)).max()) <= bound
+
+
+@pytest.mark.parametrize("n,density,variant,asp", [(700, 0.5, -1, 0), (700, 0.5, 1, 1), (2500, 0.1, -1, 0),
+                                                   (2500, 0.1, -1, 1), (300, 1.0, 4, 0), (300, 1.0, 5, 1),
+                                                   (64, 1.0, -1, 1)])
+def test_tabu_compact_and_wide_keys(L, orc, n, density, variant, asp):
+    """Instances whose gains fit one 32-bit key: the compact and the wide
+    keys give the oracle's search, with and without aspiration."""
+    R, alpha, c = 3, 3 * n, max(2, n // 40)
+    P = Problem(n, density, 7 * n + 1, R=R)
+    assert _compact_shift(n, I.icd2s_qubo_gain_bound(P.q)) > 0
+    X0 = random_solutions(n, R, n + 17)
+    for res in _tabu_both_keys(P, X0, alpha, c, asp, variant):
+        _check_tabu(orc, P.Q, X0, alpha, c, asp, res)
+    P.close()
+
+
+@pytest.mark.parametrize("extra", [0, 1])
+def test_tabu_compact_keys_at_the_gain_bound(L, orc, extra):
+    """n = 8192 (index field of 14 bits, key shift 15): the heaviest column
+    sums to 32767 (gain bound 65534, the largest the compact keys take) or,
+    with one more unit entry, 32768 (the wide keys only).  The start puts
+    the heavy variable at its extreme gains +-(127 + 2 * 32640) so the keys
+    span their whole range."""
+    n, R, alpha, c, h = 8192, 2, 1500, 54, 5000
+    Q = make_qubo(n, 0.0005, 91).astype(np.int16)
+    rng = np.random.Generator(np.random.PCG64(92))
+    nb = np.sort(rng.choice(np.setdiff1d(np.arange(n), [h]), 258 + extra, replace=False))
+    Q[h, :] = 0
+    Q[:, h] = 0
+    Q[h, h] = 127
+    Q[h, nb[:257]] = 127
+    Q[h, nb[257:]] = 1
+    Q[nb, h] = Q[h, nb]
+    Q = Q.astype(np.int8)
+    q = I.icd2s_qubo_create(Q)
+    bound = I.icd2s_qubo_gain_bound(q)
+    assert bound == 65534 + 2 * extra
+    assert (_compact_shift(n, bound) == 15) == (extra == 0)
+    st = I.icd2s_state_create(q, R, 3)
+
+    class _P:
+        pass
+    P = _P()
+    P.st, P.R, P.n, P.q = st, R, n, q
+    P.load = lambda X: I.icd2s_state_load(st, X)
+    P.state = lambda: I.icd2s_get_state(st, R, n)
+    X0 = random_solutions(n, R, 93)
+    X0[:, nb[:257]] = 1
+    X0[:, nb[257:]] = 1
+    X0[0, h], X0[1, h] = 0, 1          # the heavy variable's largest gain, and its negative
+    g0 = orc.gains(Q, X0[1])
+    assert int(g0[h]) == -(127 + 2 * (257 * 127 + 1 + extra))
+    try:
+        for asp in (0, 1):
+            for res in _tabu_both_keys(P, X0, alpha, c, asp):
+                _check_tabu(orc, Q, X0, alpha, c, asp, res)
+    finally:
+        I.icd2s_state_destroy(st)
+        I.icd2s_qubo_destroy(q)
+
+
 # ----------------------------------------------------------------------------- Eq. 6-8, Alg. 3, selection
 @pytest.mark.parametrize("n,R,K,m_min,m_max", [(500, 6, 3, 8, 40), (333, 4, 1, 64, 64), (2500, 3, 16, 32, 150)])
 def test_control_parameters_and_selection(L, orc, n, R, K, m_min, m_max):
