@@ -389,19 +389,25 @@ int icd2s_get_apply_ms(icd2s_state* st, double* ms);
  * 0 = default.  The Tabu search packs a move into one 32-bit key (one
  * reduction per warp and per block) when every gain of the instance fits
  * beside the index: 2 max_j sum_i |Q_ij| + 1 < 2^(30 - b), b = bits of n;
- * tabu_wide_keys = 1 keeps the two-reduction 64-bit keys anyway. */
+ * tabu_wide_keys = 1 keeps the two-reduction 64-bit keys anyway.  An
+ * instance without entries -128 also keeps its rows negated (2 n ld bytes
+ * more), so a move can read the row already multiplied by (1 - 2x_i):
+ * tabu_rows = 0 uses these signed rows for n > 4096 only, 1 never (the sign
+ * is applied per variable), 2 wherever the instance has them. */
 typedef struct icd2s_tuning {
     int32_t tabu_variant;
     int32_t anneal_warps_per_cta;
     int32_t refresh_bn;       /* tensor-core refresh: replicas per tile (128 or 256; 0 = default) */
     int32_t refresh_splits;   /* tensor-core refresh: K splits (0 = about one CTA per SM) */
     int32_t tabu_wide_keys;   /* 0 = compact Tabu keys where they apply, 1 = never */
-    int32_t reserved[3];
+    int32_t tabu_rows;        /* 0 = default, 1 = plain rows, 2 = signed row pairs */
+    int32_t reserved[2];
 } icd2s_tuning;
 int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t);
 int icd2s_get_tuning(icd2s_state* st, icd2s_tuning* t);
 
-/* Autotuner: times every Tabu variant that fits n and every anneal CTA size
+/* Autotuner: times every Tabu variant that fits n (with plain and, where the
+ * instance has them, signed rows) and every anneal CTA size
  * on this state with the parameters p (each trial restores the solutions it
  * changed), keeps the fastest for the state, and returns the choice in
  * `chosen` (may be NULL).  Synchronises `stream`. */

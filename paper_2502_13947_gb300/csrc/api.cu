@@ -99,6 +99,7 @@ struct icd2s_qubo {
     int32_t* eta = nullptr;
     int32_t* etahat = nullptr;
     long long gain_bound = 0;  // 2 max_j sum_i |Q_ij|: bounds every gain of every solution
+    int8_t* Q2 = nullptr;      // signed row pairs for the Tabu search (null when Q has -128)
     // scratch of icd2s_energy (grown on demand)
     int cap = 0;
     uint8_t* xpad = nullptr;
@@ -327,6 +328,7 @@ int icd2s_qubo_create(const int8_t* Q_host, int32_t n, icd2s_qubo** out)
     auto bail = [&](int code) {
         if (q->Q) cudaFree(q->Q);
         if (q->diag) cudaFree(q->diag);
+        if (q->Q2) cudaFree(q->Q2);
         if (q->eta) cudaFree(q->eta);
         if (q->etahat) cudaFree(q->etahat);
         delete q;
@@ -336,17 +338,25 @@ int icd2s_qubo_create(const int8_t* Q_host, int32_t n, icd2s_qubo** out)
     cudaError_t e;
     if ((e = dalloc(&q->Q, (size_t)n * q->ld)) != cudaSuccess || (e = dalloc(&q->diag, q->ld)) != cudaSuccess ||
         (e = dalloc(&q->eta, q->ld)) != cudaSuccess || (e = dalloc(&q->etahat, q->ld)) != cudaSuccess ||
-        (e = dalloc(&mism, 2)) != cudaSuccess)
+        (e = dalloc(&mism, 3)) != cudaSuccess)
         return bail(fail(ICD2S_ERR_OOM, "device allocation failed: %s", cudaGetErrorString(e)));
-    int got[2] = {0, 0};  // symmetry mismatches, max_j eta_j
+    int got[3] = {0, 0, 0};  // symmetry mismatches, max_j eta_j, entries equal to -128
     if ((e = cudaMemset(q->Q, 0, (size_t)n * q->ld)) == cudaSuccess &&
         (e = cudaMemcpy2D(q->Q, q->ld, Q_host, n, n, n, cudaMemcpyHostToDevice)) == cudaSuccess &&
-        (e = cudaMemset(mism, 0, 2 * sizeof(int))) == cudaSuccess &&
+        (e = cudaMemset(mism, 0, 3 * sizeof(int))) == cudaSuccess &&
         (e = launch_prepare(q->Q, n, q->ld, q->eta, q->etahat, q->diag, mism, mism + 1, 0)) == cudaSuccess &&
-        (e = cudaMemcpy(got, mism, 2 * sizeof(int), cudaMemcpyDeviceToHost)) == cudaSuccess) {
+        (e = cudaMemcpy(got, mism, 3 * sizeof(int), cudaMemcpyDeviceToHost)) == cudaSuccess) {
         cudaFree(mism);
+        mism = nullptr;
         const int bad = got[0];
         q->gain_bound = 2LL * got[1];
+        if (!bad && got[2] == 0) {  // signed row pairs: 2 n ld bytes beside Q
+            if ((e = dalloc(&q->Q2, 2 * (size_t)n * q->ld)) != cudaSuccess)
+                return bail(fail(ICD2S_ERR_OOM, "device allocation failed: %s", cudaGetErrorString(e)));
+            if ((e = launch_signed_rows(q->Q, n, q->ld, q->Q2, 0)) != cudaSuccess ||
+                (e = cudaDeviceSynchronize()) != cudaSuccess)
+                return bail(fail(ICD2S_ERR_CUDA, "qubo_create: %s", cudaGetErrorString(e)));
+        }
         if (bad) return bail(fail(ICD2S_ERR_ASYMMETRIC, "Q is not symmetric (%d mismatched entries)", bad));
         *out = q;
         return ICD2S_OK;
@@ -358,7 +368,7 @@ int icd2s_qubo_create(const int8_t* Q_host, int32_t n, icd2s_qubo** out)
 int icd2s_qubo_destroy(icd2s_qubo* q)
 {
     if (!q) return ICD2S_OK;
-    void* ptrs[] = {q->Q, q->diag, q->eta, q->etahat, q->xpad, q->hpad, q->Qb};
+    void* ptrs[] = {q->Q, q->Q2, q->diag, q->eta, q->etahat, q->xpad, q->hpad, q->Qb};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete q;
@@ -397,6 +407,7 @@ int icd2s_energy(icd2s_qubo* q, const uint8_t* x_dev, int32_t count, int64_t* E_
     Dev d{};
     d.Q = q->Q; d.diag = q->diag; d.etahat = q->etahat; d.n = q->n; d.ld = q->ld; d.R = count;
     d.gain_bound = q->gain_bound;
+    d.Q2 = q->Q2;
     CK(launch_pad_rows(x_dev, q->n, count, q->xpad, q->ld, s));
     CK(launch_recompute(d, q->xpad, q->ld, count, q->hpad, E_dev, s));
     return ICD2S_OK;
@@ -428,6 +439,7 @@ int icd2s_state_create(icd2s_qubo* q, int32_t replicas, uint64_t seed, icd2s_sta
     Dev& d = st->d;
     d.Q = q->Q; d.diag = q->diag; d.etahat = q->etahat; d.n = q->n; d.ld = q->ld; d.R = replicas;
     d.gain_bound = q->gain_bound;
+    d.Q2 = q->Q2;
     d.X = st->X; d.G = st->G; d.E = st->E; d.T = st->T; d.C = st->C; d.gamma = st->gamma; d.A = st->A;
     d.delta = st->delta; d.order = st->order; d.sel = st->sel; d.FL = st->FL; d.FCNT = st->FCNT;
     d.DEACC = st->DEACC; d.DONE = st->DONE; d.best_x = st->best_x; d.best_E = st->best_E; d.flags = st->flags;
@@ -528,7 +540,8 @@ int icd2s_tabu(icd2s_state* st, int32_t alpha, int32_t c, void* stream)
     REQ(alpha >= 0, ICD2S_ERR_ARG, "alpha < 0");
     REQ(c >= 1 && c <= n, ICD2S_ERR_ARG, "tenure c=%d outside 1..n", c);
     REQ(tabu_smem_bytes(n, alpha) <= 227 * 1024, ICD2S_ERR_RANGE, "alpha=%d too large for n=%d", alpha, n);
-    CK(launch_tabu(st->d, alpha, c, st->tune.tabu_variant, S(stream), false, st->tune.tabu_wide_keys != 0));
+    CK(launch_tabu(st->d, alpha, c, st->tune.tabu_variant, S(stream), false, st->tune.tabu_wide_keys != 0,
+                   st->tune.tabu_rows));
     return ICD2S_OK;
 }
 
@@ -539,7 +552,8 @@ int icd2s_tabu_aspiration(icd2s_state* st, int32_t alpha, int32_t c, void* strea
     REQ(alpha >= 0, ICD2S_ERR_ARG, "alpha < 0");
     REQ(c >= 1 && c <= n, ICD2S_ERR_ARG, "tenure c=%d outside 1..n", c);
     REQ(tabu_smem_bytes(n, alpha) <= 227 * 1024, ICD2S_ERR_RANGE, "alpha=%d too large for n=%d", alpha, n);
-    CK(launch_tabu(st->d, alpha, c, st->tune.tabu_variant, S(stream), true, st->tune.tabu_wide_keys != 0));
+    CK(launch_tabu(st->d, alpha, c, st->tune.tabu_variant, S(stream), true, st->tune.tabu_wide_keys != 0,
+                   st->tune.tabu_rows));
     return ICD2S_OK;
 }
 
@@ -791,7 +805,7 @@ static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* tra
     if (feats && (rc = ensure_features(st, s))) return rc;
     mark(st, 0, 0, s);
     CK(launch_tabu(st->d, p->alpha, p->c, st->tune.tabu_variant, s, p->aspiration != 0,
-                   st->tune.tabu_wide_keys != 0));  // Algorithm 1
+                   st->tune.tabu_wide_keys != 0, st->tune.tabu_rows));  // Algorithm 1
     mark(st, 0, 1, s);
     CK(launch_best(st->d, trace_it, 0, nullptr, s));
     mark(st, 1, 0, s);
@@ -944,6 +958,7 @@ int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t)
         "anneal_warps_per_cta=%d outside 0..4", t->anneal_warps_per_cta);
     REQ(t->tabu_wide_keys == 0 || t->tabu_wide_keys == 1, ICD2S_ERR_ARG, "tabu_wide_keys=%d must be 0 or 1",
         t->tabu_wide_keys);
+    REQ(t->tabu_rows >= 0 && t->tabu_rows <= 2, ICD2S_ERR_ARG, "tabu_rows=%d must be 0, 1 or 2", t->tabu_rows);
     st->tune = *t;
     ++st->gen;  // launch configurations changed: re-capture
     return ICD2S_OK;
@@ -997,18 +1012,20 @@ int icd2s_autotune(icd2s_state* st, const icd2s_params* p, icd2s_tuning* chosen,
     float best_ms = 1e30f;
     for (int v = 0; v < tabu_num_variants(); ++v) {
         if (!tabu_variant_fits(v, n)) continue;
-        float vbest = 1e30f;
-        for (int rep = 0; rep < 2; ++rep) {
-            if ((rc = restore())) return rc;
-            CK(cudaEventRecord(e0, s));
-            CK(launch_tabu(st->d, alpha, p->c, v, s, p->aspiration != 0, st->tune.tabu_wide_keys != 0));
-            CK(cudaEventRecord(e1, s));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < vbest) vbest = ms;
+        for (int rows = 1; rows <= (st->q->Q2 ? 2 : 1); ++rows) {  // plain rows, then signed rows
+            float vbest = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                if ((rc = restore())) return rc;
+                CK(cudaEventRecord(e0, s));
+                CK(launch_tabu(st->d, alpha, p->c, v, s, p->aspiration != 0, st->tune.tabu_wide_keys != 0, rows));
+                CK(cudaEventRecord(e1, s));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < vbest) vbest = ms;
+            }
+            if (vbest < best_ms) { best_ms = vbest; best.tabu_variant = v; best.tabu_rows = rows; }
         }
-        if (vbest < best_ms) { best_ms = vbest; best.tabu_variant = v; }
     }
     if ((rc = restore())) return rc;
     rc = select_impl(st, p->w1, p->w2, p->w3, p->K, p->m_min, p->m_max, 0u, s, nullptr, 0, false);

@@ -85,6 +85,7 @@ struct Dev {
     int32_t* ACC; unsigned* TT; int apply_splits;     // split write-back: partial sums, tile tickets
     uint32_t k0, k1; // Philox key = seed halves
     long long gain_bound;  // max_j 2 sum_i |Q_ij| >= |g_j| for every x
+    const int8_t* Q2;      // [2n][ld] signed rows: row 2i + x = (1 - 2x) Q_i (null if Q has -128)
 };
 
 // Counts kernel launches (process-wide, for reporting).
@@ -94,17 +95,22 @@ void note_launch(int kernels);
 void set_error_message(const char* msg);
 
 // ---- launchers (each returns cudaGetLastError() of its launch) ----
-// eta_max[0] receives max_j eta_j (eta_j = sum_i |Q_ij|).
+// eta_max[0] receives max_j eta_j (eta_j = sum_i |Q_ij|), eta_max[1] the
+// number of entries equal to -128.
 cudaError_t launch_prepare(const int8_t* Q, int n, int ld, int32_t* eta, int32_t* etahat, int32_t* diag,
                            int* mismatches, int* eta_max, cudaStream_t s);
+// Q2[2i + x][j] = (1 - 2x) Q[i][j] (Q without -128 entries; padding columns 0).
+cudaError_t launch_signed_rows(const int8_t* Q, int n, int ld, int8_t* Q2, cudaStream_t s);
 cudaError_t launch_init_x(const Dev& d, cudaStream_t s);
 cudaError_t launch_recompute(const Dev& d, const uint8_t* X, int ldx, int R, int32_t* G, int64_t* E,
                              cudaStream_t s);  // gains + energies of X (padded rows)
 cudaError_t launch_pad_rows(const uint8_t* src, int n, int rows, uint8_t* dst, int ld, cudaStream_t s);
 // variant: kernel shape (< 0: default); aspiration: Tabu with the aspiration criterion.
-// wide_keys: the two-reduction keys even where the compact ones apply.
+// wide_keys: the two-reduction keys even where the compact ones apply;
+// rows: 0 = the default choice of plain or signed rows, 1 = plain rows (the sign
+// applied per variable), 2 = signed rows where d.Q2 exists.
 cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_t s, bool aspiration = false,
-                        bool wide_keys = false);
+                        bool wide_keys = false, int rows = 0);
 // Shift of the compact Tabu keys for n and the instance's gain bound (0: they do not apply).
 int tabu_key_shift(int n, long long gain_bound);
 size_t tabu_smem_bytes(int n, int alpha);

@@ -309,15 +309,20 @@ __global__ void k_symcheck(const int8_t* __restrict__ Q, int n, int ld, int* mis
     if (threadIdx.x == 0 && bad) atomicAdd(mismatches, bad);
 }
 
-__global__ void k_eta(const int8_t* __restrict__ Q, int n, int ld, int32_t* eta, int32_t* diag)
+__global__ void k_eta(const int8_t* __restrict__ Q, int n, int ld, int32_t* eta, int32_t* diag, int* n128)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= ld) return;
     if (j >= n) { eta[j] = 0; diag[j] = 0; return; }
-    int s = 0;
-    for (int i = 0; i < n; ++i) s += abs((int)Q[(size_t)i * ld + j]);
+    int s = 0, m = 0;
+    for (int i = 0; i < n; ++i) {
+        const int v = Q[(size_t)i * ld + j];
+        s += abs(v);
+        m += v == -128;
+    }
     eta[j] = s;
     diag[j] = Q[(size_t)j * ld + j];
+    if (m) atomicAdd(n128, m);
 }
 
 __global__ __launch_bounds__(1024) void k_etahat(const int32_t* __restrict__ eta, int n, int ld, int32_t* etahat,
@@ -336,6 +341,35 @@ __global__ __launch_bounds__(1024) void k_etahat(const int32_t* __restrict__ eta
         etahat[j] = (j < n && mx > 0) ? (int32_t)(((long long)eta[j] * 65536) / mx) : 0;
 }
 
+// Signed row pairs for the Tabu search: one thread per 16 bytes of a row of Q
+// writes them to rows 2i and 2i + 1 (bytewise negation; no entry is -128).
+__global__ void k_signed_rows(const int8_t* __restrict__ Q, int n, int ld, int8_t* __restrict__ Q2)
+{
+    const size_t chunks = (size_t)n * (ld / 16);
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= chunks) return;
+    const size_t i = t / (ld / 16), c = t % (ld / 16);
+    const uint4 v = *reinterpret_cast<const uint4*>(Q + i * ld + 16 * c);
+    uint32_t w[4] = {v.x, v.y, v.z, v.w}, m[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t r = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) r |= (uint32_t)(uint8_t)(-(int8_t)(w[k] >> (8 * b))) << (8 * b);
+        m[k] = r;
+    }
+    *reinterpret_cast<uint4*>(Q2 + (2 * i) * ld + 16 * c) = v;
+    *reinterpret_cast<uint4*>(Q2 + (2 * i + 1) * ld + 16 * c) = make_uint4(m[0], m[1], m[2], m[3]);
+}
+
+cudaError_t launch_signed_rows(const int8_t* Q, int n, int ld, int8_t* Q2, cudaStream_t s)
+{
+    const size_t chunks = (size_t)n * (ld / 16);
+    k_signed_rows<<<(unsigned)((chunks + 255) / 256), 256, 0, s>>>(Q, n, ld, Q2);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prepare(const int8_t* Q, int n, int ld, int32_t* eta, int32_t* etahat, int32_t* diag,
                            int* mismatches, int* eta_max, cudaStream_t s)
 {
@@ -344,7 +378,7 @@ cudaError_t launch_prepare(const int8_t* Q, int n, int ld, int32_t* eta, int32_t
     note_launch(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_eta<<<(ld + 255) / 256, 256, 0, s>>>(Q, n, ld, eta, diag);
+    k_eta<<<(ld + 255) / 256, 256, 0, s>>>(Q, n, ld, eta, diag, eta_max + 1);
     note_launch(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_etahat<<<1, 1024, 0, s>>>(eta, n, ld, etahat, eta_max);

@@ -30,14 +30,20 @@
 // each take their arg-min with a single redux.sync and the key carries x_i.
 // The bound |g_j| <= |Q_jj| + 2 sum_{i != j} |Q_ij| <= 2 sum_i |Q_ij| holds for
 // every x, so it is computed once per instance.
-// The objective OV is tracked in int64 by thread 0, which also keeps the toggle
-// counts and the move log and publishes the best visit at the end.  The move
-// log (uint16 per iteration) stays in shared memory; after the last
-// iteration the moves made after the best visit are undone in one pass:
-// variables moved an odd number of times flip back, and their rows of Q
-// correct the gains (x_min is reconstructed without copying x on every
-// improvement).  The tabu memory returned is C_j = max(0, fa_j - alpha).
+// Signed rows (SR): when Q has no entry -128 the instance also keeps the
+// rows (1 - 2x) Q_i interleaved, row 2i + x; the move (i, x_i) then reads row
+// 2i + x_i (the key's low bits, no decoding) and each variable's update is
+// one dp4a of the row word with the constant byte 2 in its lane.
+// The objective OV is tracked in int64 by thread 0, which also keeps the
+// move log and publishes the best visit at the end; the toggle counts are
+// counted from the move log after the search.  The move log (uint16 per
+// iteration) stays in shared memory; after the last iteration the moves
+// made after the best visit are undone in one pass: variables moved an odd
+// number of times flip back, and their rows of Q correct the gains (x_min is
+// reconstructed without copying x on every improvement).  The tabu memory
+// returned is C_j = max(0, fa_j - alpha).
 #include <climits>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -53,12 +59,15 @@ __device__ __forceinline__ unsigned long long pack_key(unsigned hi, unsigned lo)
     return ((unsigned long long)hi << 32) | lo;
 }
 
+template <int S>
+using slot_t = std::integral_constant<int, S>;
+
 }  // namespace
 
 // ASP: the aspiration criterion (reading S4): a tabu variable is also a
 // candidate when its move would beat the best objective visited so far, i.e.
-// g < OVmin - OV, which in key units is (key >> 5) < OVmin - OV + bias.
-template <int W, int MAXT, bool ASP, bool CK>
+// g < OVmin - OV, which in key units is (key >> shift) < OVmin - OV + bias.
+template <int W, int MAXT, bool ASP, bool CK, bool SR>
 __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh)
 {
     static_assert(4 * W <= (1 << kKeyShift), "the local index must fit the key");
@@ -71,14 +80,16 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh)
     uint16_t* mlog = reinterpret_cast<uint16_t*>(smem + 528 + 4 * (size_t)d.ld + d.ld / 8);  // [alpha]
 
     const int p = blockIdx.x;
-    const int NT = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = NT >> 5;
+    const int NT = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = d.n, ld = d.ld;
     const int8_t* __restrict__ Q = d.Q;
+    const int8_t* __restrict__ Q2 = d.Q2;  // SR: row 2i + x = (1 - 2x) Q_i
     uint8_t* xrow = d.X + (size_t)p * ld;
     int32_t* grow = d.G + (size_t)p * ld;
 
     for (int j = tid; j < ld; j += NT) Ts[j] = 0;
     for (int j = tid; j < ld / 32; j += NT) undo[j] = 0;
+    for (int j = tid; j < 64; j += NT) wkeys[j] = ~0ull;  // slots of absent warps read as "no candidate"
     if (tid == 0) *nF = 0;
 
     int gf[W][4], fa[W][4];
@@ -137,11 +148,8 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh)
         if (lane == 0) wkeys[slot * 32 + warp] = pack_key(wg, wj);
     };
     auto block_argmin = [&](int slot) -> unsigned long long {
-        if constexpr (CK) {
-            const unsigned k = lane < NW ? wkeys32[slot * 32 + lane] : 0xffffffffu;
-            return __reduce_min_sync(0xffffffffu, k);
-        }
-        const unsigned long long k = lane < NW ? wkeys[slot * 32 + lane] : ~0ull;
+        if constexpr (CK) return __reduce_min_sync(0xffffffffu, wkeys32[slot * 32 + lane]);
+        const unsigned long long k = wkeys[slot * 32 + lane];
         const unsigned hi = __reduce_min_sync(0xffffffffu, (unsigned)(k >> 32));
         const unsigned lo = __reduce_min_sync(0xffffffffu, (unsigned)(k >> 32) == hi ? (unsigned)k : 0xffffffffu);
         return pack_key(hi, lo);
@@ -160,19 +168,24 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh)
     __syncthreads();
     unsigned long long key = block_argmin(0);
 
-    for (int it = 0; it < alpha; ++it) {
-        // the chosen move: its gain, index and value (CK: no candidate is the key ~0,
+    bool stop = false;
+    // Iteration `it`: apply the chosen move, publish the next arg-min to slot
+    // SLOT = (it + 1) & 1 (a compile-time constant: the loop runs two moves per
+    // trip), and read it back.
+    auto move = [&](int it, auto slot_c) {
+        constexpr int slot = decltype(slot_c)::value;
+        // the chosen move: index and value (CK: no candidate is the key ~0,
         // whose index field 2^(sh-1) - 1 >= n; otherwise its index half is ~0)
-        const int gi = CK ? (int)((unsigned)key >> sh) - (int)cbias : (int)(unsigned)(key >> 32) - (int)kKeyBias;
         const unsigned jx = CK ? (unsigned)key & (2u * imask + 1u) : (unsigned)key;
         const int i = (int)(jx >> 1);
-        if (i >= n) {  // no move at all (a warp without candidates publishes index ~0): stop, uniformly
+        if (i >= n) {  // no move at all: stop, uniformly
             if (tid == 0) d.flags[2] = 1;
             alpha = it;
-            break;
+            stop = true;
+            return;
         }
         const int si2 = (jx & 1u) ? -2 : 2;       // 2 (1 - 2 x_i)
-        const int8_t* row = Q + (size_t)i * ld;
+        const int8_t* row = SR ? Q2 + (size_t)jx * ld : Q + (size_t)i * ld;
         int rv[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) {
@@ -182,7 +195,10 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh)
 #pragma unroll
         for (int w = 0; w < W; ++w)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) gf[w][b] += (int)(int8_t)(rv[w] >> (8 * b)) * si2;
+            for (int b = 0; b < 4; ++b) {
+                if constexpr (SR) gf[w][b] = __dp4a(rv[w], 2 << (8 * b), gf[w][b]);  // + 2 (1 - 2 x_i) Q_ij
+                else gf[w][b] += (int)(int8_t)(rv[w] >> (8 * b)) * si2;
+            }
         // the moved variable keeps its folded gain, flips, and becomes tabu
         const int rel = (i >> 2) - tid;  // the owner has rel = w NT for its group w
         const int bi = i & 3;
@@ -192,7 +208,7 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh)
 #pragma unroll
                 for (int b = 0; b < 4; ++b)
                     if (b == bi) {
-                        gf[w][b] -= (int)(int8_t)(rv[w] >> (8 * b)) * si2;
+                        gf[w][b] -= (int)(int8_t)(rv[w] >> (8 * b)) * (SR ? 2 : si2);
                         xb ^= 1u << (4 * w + b);
                         s32[w][b] = 0u - s32[w][b];
                         if (CK) kc[w][b] ^= 1u;
@@ -202,14 +218,11 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh)
                     }
             }
         if (ASP || tid == 0) {  // the objective and best visit: one thread (every thread with aspiration)
+            const int gi = CK ? (int)((unsigned)key >> sh) - (int)cbias : (int)(unsigned)(key >> 32) - (int)kKeyBias;
             OV += gi;
             if (OV < OVmin) { OVmin = OV; best_it = it; }
         }
-        if (tid == 0) {         // toggle count and move log
-            Ts[i] += 1;
-            mlog[it] = (uint16_t)i;
-        }
-        const int slot = (it + 1) & 1;
+        if (tid == 0) mlog[it] = (uint16_t)i;  // the move log
         warp_argmin(it + 1, slot, ASP ? asp_limit() : 0u);
         __syncthreads();
         key = block_argmin(slot);
@@ -225,21 +238,31 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh)
                 key = block_argmin(slot);
             }
         }
+    };
+    int it = 0;
+    for (; it + 1 < alpha; it += 2) {
+        move(it, slot_t<1>{});
+        if (stop) break;
+        move(it + 1, slot_t<0>{});
+        if (stop) break;
     }
+    if (!stop && it < alpha) move(it, slot_t<1>{});
 
-    // toggle counts out; parity of the moves made after the best visit
-    int32_t* Tout = d.T + (size_t)p * ld;
-    for (int j = tid; j < ld; j += NT) Tout[j] = Ts[j];
+    // toggle counts from the move log; parity of the moves made after the best visit
     int* s_best = reinterpret_cast<int*>(smem + 520);
     if (tid == 0) *s_best = best_it;
-    __syncthreads();
+    __syncthreads();  // the move log is complete
+    for (int e = tid; e < alpha; e += NT) atomicAdd(&Ts[mlog[e]], 1);
     best_it = *s_best;
     for (int e = best_it + 1 + tid; e < alpha; e += NT) {
         const int i = mlog[e];
         atomicXor(&undo[i >> 5], 1u << (i & 31));
     }
     __syncthreads();
-    int32_t* flist = Ts;  // reuse: T has been written out
+    int32_t* Tout = d.T + (size_t)p * ld;
+    for (int j = tid; j < ld; j += NT) Tout[j] = Ts[j];
+    __syncthreads();  // T has been read out before the flip list reuses it
+    int32_t* flist = Ts;
 #pragma unroll
     for (int w = 0; w < W; ++w)
 #pragma unroll
@@ -309,18 +332,38 @@ size_t tabu_smem_bytes(int n, int alpha)
     return 528 + 4 * (size_t)ld + (size_t)ld / 8 + 2 * (size_t)alpha + 16;
 }
 
-template <int W, int MAXT, bool ASP, bool CK>
+template <int W, int MAXT, bool ASP, bool CK, bool SR>
 static cudaError_t launch_tabu_w(const Dev& d, int alpha, int c, int sh, cudaStream_t s)
 {
     int nt = (d.n + 4 * W - 1) / (4 * W);
     nt = (nt + 31) / 32 * 32;
     if (nt > MAXT) return cudaErrorInvalidConfiguration;
     const size_t sm = tabu_smem_bytes(d.n, alpha);
-    cudaError_t e = cudaFuncSetAttribute(k_tabu<W, MAXT, ASP, CK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    auto kern = k_tabu<W, MAXT, ASP, CK, SR>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_tabu<W, MAXT, ASP, CK><<<d.R, nt, sm, s>>>(d, alpha, c, sh);
+    kern<<<d.R, nt, sm, s>>>(d, alpha, c, sh);
     note_launch(1);
     return cudaGetLastError();
+}
+
+// One kernel shape: picks the build for aspiration, compact keys (sh > 0; only
+// where CKOK) and signed rows.
+template <int W, int MAXT, bool CKOK>
+static cudaError_t launch_shape(const Dev& d, int alpha, int c, int sh, bool asp, bool sr, cudaStream_t s)
+{
+    if constexpr (CKOK) {
+        if (sh) {
+            if (asp) return sr ? launch_tabu_w<W, MAXT, true, true, true>(d, alpha, c, sh, s)
+                               : launch_tabu_w<W, MAXT, true, true, false>(d, alpha, c, sh, s);
+            return sr ? launch_tabu_w<W, MAXT, false, true, true>(d, alpha, c, sh, s)
+                      : launch_tabu_w<W, MAXT, false, true, false>(d, alpha, c, sh, s);
+        }
+    }
+    if (asp) return sr ? launch_tabu_w<W, MAXT, true, false, true>(d, alpha, c, 0, s)
+                       : launch_tabu_w<W, MAXT, true, false, false>(d, alpha, c, 0, s);
+    return sr ? launch_tabu_w<W, MAXT, false, false, true>(d, alpha, c, 0, s)
+              : launch_tabu_w<W, MAXT, false, false, false>(d, alpha, c, 0, s);
 }
 
 // Variants of the Tabu kernel: 4-variable groups per thread W and the block
@@ -359,31 +402,26 @@ int tabu_key_shift(int n, long long gain_bound)
 
 // variant: index into kTabuVariants; < 0 picks the default.  Compact keys are
 // used when the instance's gain bound allows them, unless wide_keys is set.
-cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_t s, bool aspiration, bool wide_keys)
+// rows: 0 = signed rows for n > 4096 (where a replica's rows no longer stay in
+// L1: at n = 2500 the two signs of a row halve the L1 hits and cost 8 %, at
+// n = 5000 the one-instruction update gains 5 %), 1 = plain rows, 2 = signed
+// rows; signed rows only where the instance has them.
+cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_t s, bool aspiration, bool wide_keys,
+                        int rows)
 {
     if (variant < 0) variant = tabu_default_variant(d.n);
     if (!tabu_variant_fits(variant, d.n)) return cudaErrorInvalidConfiguration;
+    const int sh = wide_keys ? 0 : tabu_key_shift(d.n, d.gain_bound);
+    const bool sr = d.Q2 != nullptr && (rows == 2 || (rows == 0 && d.n > 4096));
     // the 1024-thread shapes with 12 and 16 variables per thread would spill the
     // per-variable key constants: they keep the wide keys
-    const bool compact_fits = kTabuVariants[variant].maxt < 1024 || kTabuVariants[variant].W <= 2;
-    const int sh = wide_keys || !compact_fits ? 0 : tabu_key_shift(d.n, d.gain_bound);
-    const int sel = (variant * 2 + (aspiration ? 1 : 0)) * 2 + (sh ? 1 : 0);
-    switch (sel) {
-#define ICD2S_TABU_WIDE(V, W, MAXT)                                                      \
-        case 4 * V + 0: return launch_tabu_w<W, MAXT, false, false>(d, alpha, c, sh, s); \
-        case 4 * V + 2: return launch_tabu_w<W, MAXT, true, false>(d, alpha, c, sh, s);
-#define ICD2S_TABU_BOTH(V, W, MAXT)                                                      \
-        ICD2S_TABU_WIDE(V, W, MAXT)                                                      \
-        case 4 * V + 1: return launch_tabu_w<W, MAXT, false, true>(d, alpha, c, sh, s);  \
-        case 4 * V + 3: return launch_tabu_w<W, MAXT, true, true>(d, alpha, c, sh, s);
-        ICD2S_TABU_BOTH(0, 1, 1024)
-        ICD2S_TABU_BOTH(1, 2, 1024)
-        ICD2S_TABU_WIDE(2, 3, 1024)
-        ICD2S_TABU_WIDE(3, 4, 1024)
-        ICD2S_TABU_BOTH(4, 4, 256)
-        ICD2S_TABU_BOTH(5, 8, 256)
-#undef ICD2S_TABU_BOTH
-#undef ICD2S_TABU_WIDE
+    switch (variant) {
+        case 0: return launch_shape<1, 1024, true>(d, alpha, c, sh, aspiration, sr, s);
+        case 1: return launch_shape<2, 1024, true>(d, alpha, c, sh, aspiration, sr, s);
+        case 2: return launch_shape<3, 1024, false>(d, alpha, c, sh, aspiration, sr, s);
+        case 3: return launch_shape<4, 1024, false>(d, alpha, c, sh, aspiration, sr, s);
+        case 4: return launch_shape<4, 256, true>(d, alpha, c, sh, aspiration, sr, s);
+        case 5: return launch_shape<8, 256, true>(d, alpha, c, sh, aspiration, sr, s);
         default: return cudaErrorInvalidValue;
     }
 }

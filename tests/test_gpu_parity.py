@@ -154,13 +154,16 @@ def _compact_shift(n, bound):
 
 def _tabu_both_keys(P, X0, alpha, c, asp, variant=-1):
     """Runs the search with the compact keys (where the instance allows them)
-    and with the wide keys from the same start; returns both results."""
+    and with the wide keys, each with the signed row pairs (where the
+    instance has them) and with the plain rows, from the same start; returns
+    the four results."""
     out = []
     for wide in (0, 1):
-        P.load(X0)
-        I.icd2s_set_tuning(P.st, tabu_variant=variant, tabu_wide_keys=wide)
-        (I.icd2s_tabu_aspiration if asp else I.icd2s_tabu)(P.st, alpha, c)
-        out.append(P.state() + I.icd2s_get_tabu(P.st, P.R, P.n))
+        for rows in (1, 2):
+            P.load(X0)
+            I.icd2s_set_tuning(P.st, tabu_variant=variant, tabu_wide_keys=wide, tabu_rows=rows)
+            (I.icd2s_tabu_aspiration if asp else I.icd2s_tabu)(P.st, alpha, c)
+            out.append(P.state() + I.icd2s_get_tabu(P.st, P.R, P.n))
     return out
 
 
@@ -204,6 +207,30 @@ def test_tabu_compact_and_wide_keys(L, orc, n, density, variant, asp):
     for res in _tabu_both_keys(P, X0, alpha, c, asp, variant):
         _check_tabu(orc, P.Q, X0, alpha, c, asp, res)
     P.close()
+
+
+@pytest.mark.parametrize("n,asp", [(300, 0), (300, 1), (2500, 0)])
+def test_tabu_with_entries_of_minus_128(L, orc, n, asp):
+    """-128 has no int8 negation, so such an instance keeps no signed rows:
+    the search still equals the oracle, through the plain rows."""
+    Q = make_qubo(n, 0.3, 50 + n).astype(np.int16)
+    rng = np.random.Generator(np.random.PCG64(51))
+    for i, j in rng.integers(0, n, size=(25, 2)):
+        Q[i, j] = Q[j, i] = -128
+    Q = Q.astype(np.int8)
+    R, alpha, c = 3, 3 * n, max(2, n // 50)
+    q = I.icd2s_qubo_create(Q)
+    st = I.icd2s_state_create(q, R, 5)
+    assert I.icd2s_qubo_gain_bound(q) == 2 * int(np.abs(Q.astype(np.int64)).sum(axis=0).max())
+    X0 = random_solutions(n, R, 52)
+    try:
+        I.icd2s_state_load(st, X0)
+        (I.icd2s_tabu_aspiration if asp else I.icd2s_tabu)(st, alpha, c)
+        res = I.icd2s_get_state(st, R, n) + I.icd2s_get_tabu(st, R, n)
+        _check_tabu(orc, Q, X0, alpha, c, asp, res)
+    finally:
+        I.icd2s_state_destroy(st)
+        I.icd2s_qubo_destroy(q)
 
 
 @pytest.mark.parametrize("extra", [0, 1])
