@@ -401,7 +401,12 @@ typedef struct icd2s_tuning {
     int32_t refresh_splits;   /* tensor-core refresh: K splits (0 = about one CTA per SM) */
     int32_t tabu_wide_keys;   /* 0 = compact Tabu keys where they apply, 1 = never */
     int32_t tabu_rows;        /* 0 = default, 1 = plain rows, 2 = signed row pairs */
-    int32_t reserved[2];
+    int32_t anneal_scheme;    /* sweep of the Ising-machine kernel (every scheme gives the same
+                                 trajectory): 0 = default (4), 1 = rounds of decisions, 2 =
+                                 position by position, 3 = position by position with the next
+                                 test taken for both outcomes, 4 = 1 or 3 per sweep, whichever
+                                 the previous sweep's accepts predict cheaper */
+    int32_t reserved[1];
 } icd2s_tuning;
 int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t);
 int icd2s_get_tuning(icd2s_state* st, icd2s_tuning* t);

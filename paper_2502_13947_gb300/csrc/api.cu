@@ -607,6 +607,7 @@ static int anneal_impl(icd2s_state* st, const int32_t* idx, const int32_t* off, 
     a.block_base = block_base; a.limtab = st->limtab; a.sweeps = sweeps; a.iter = iter;
     a.slot_base = 0; a.mask = mask; a.ldm = ldm; a.dE = dE; a.attempts_acc = st->counters; a.m_max = m_max;
     a.warps_per_cta = st->tune.anneal_warps_per_cta;
+    a.scheme = st->tune.anneal_scheme;
     a.iter_dev = iter_dev;
     if (im_mode == 1) {  // exact Ising machine (m <= 24)
         CK(launch_exact(st->d, a, s));
@@ -959,6 +960,8 @@ int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t)
     REQ(t->tabu_wide_keys == 0 || t->tabu_wide_keys == 1, ICD2S_ERR_ARG, "tabu_wide_keys=%d must be 0 or 1",
         t->tabu_wide_keys);
     REQ(t->tabu_rows >= 0 && t->tabu_rows <= 2, ICD2S_ERR_ARG, "tabu_rows=%d must be 0, 1 or 2", t->tabu_rows);
+    REQ(t->anneal_scheme >= 0 && t->anneal_scheme <= 4, ICD2S_ERR_ARG, "anneal_scheme=%d outside 0..4",
+        t->anneal_scheme);
     st->tune = *t;
     ++st->gen;  // launch configurations changed: re-capture
     return ICD2S_OK;

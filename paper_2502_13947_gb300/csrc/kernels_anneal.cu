@@ -67,7 +67,11 @@ __device__ __forceinline__ int accept_limit(uint32_t thr, uint32_t beta)
 
 // Anneals subQUBO s with the calling warp; Qs is the warp's (32 P)^2-byte
 // shared-memory tile.  Warp-synchronous: no block-level barriers.
-template <int P>
+// SEQ: 0 = rounds (multi-accept for P <= 4, first accept for P = 8);
+// 1 = position by position; 2 = position by position with the next
+// position's decision taken for both outcomes of the current one; 3 = per
+// sweep, rounds or 2, whichever the previous sweep's accepts predict cheaper.
+template <int P, int SEQ>
 __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, int s, int lane, int8_t* Qs)
 {
     using Seg = typename RowSeg<P>::T;
@@ -194,94 +198,194 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
             X[q] ^= A[q];
         }
     };
-    int limA[4][P];
-    load_limits(0, limA);
-    for (int k4 = 0; k4 < a.sweeps; k4 += 4) {
-        int limB[4][P];
-        if (k4 + 4 < a.sweeps) load_limits(k4 + 4, limB);
+    // One sweep, position by position in order: the owner's test against the
+    // current gain decides (one ballot), and every lane adds the flipped
+    // row's entries (zero factor when rejected), so there is no branch.  Row
+    // b's segment is loaded one position ahead.
+    auto sweep_seq = [&](const int (&lim)[P]) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int k = k4 + r;
-            if (k >= a.sweeps) break;
-            int lim[P];
-            unsigned M[P];  // lanes whose position q has not been visited in this sweep
+        for (int q = 0; q < P; ++q) {
+            if (32 * q >= m) break;
+            const int8_t* base = Qs + (size_t)(32 * q) * MC + lane * P;
+            Seg rn = *reinterpret_cast<const Seg*>(base);
+            bool t = sg[q] * h[q] <= lim[q];  // the decision input of position 32 q
+#pragma unroll(P <= 4 ? 32 : 8)
+            for (int L = 0; L < 32; ++L) {
+                if (32 * q + L >= m) break;
+                const Seg rb = rn;
+                if (L < 31) rn = *reinterpret_cast<const Seg*>(base + (size_t)(L + 1) * MC);
+                const int fx = ((X[q] >> L) & 1u) ? -2 : 2;  // 2 (1 - 2 x_b)
+                if constexpr (SEQ == 1) {
+                    const bool acc = (__ballot_sync(0xffffffffu, t) >> L) & 1u;
+                    const int f = acc ? fx : 0;
 #pragma unroll
-            for (int q = 0; q < P; ++q) {
-                lim[q] = limA[r][q];
-                M[q] = 0xffffffffu;
-            }
-            if constexpr (kSparse) {
-                // Rounds of several accepts: the tentative decisions of all
-                // unvisited positions are taken against the current gains; a
-                // position's decision is final unless it is coupled to an
-                // earlier tentatively accepted position (whose flip would
-                // change its gain).  The first such position ends the round:
-                // the accepts before it are pairwise uncoupled, so applying
-                // them in any order gives exactly the gains a one-at-a-time
-                // sweep sees.
-                const unsigned below = (1u << lane) - 1u;
-                while (true) {
-                    unsigned B[P], any = 0u;
+                    for (int q2 = 0; q2 < P; ++q2) h[q2] += f * (int)(int8_t)(uint8_t)(rb >> (8 * q2));
+                    if (acc && lane == L) { dE += sg[q] * h[q]; sg[q] = -sg[q]; }
+                    X[q] ^= (unsigned)acc << L;
+                    t = sg[q] * h[q] <= lim[q];
+                } else {
+                    // fields if b flips, and the next position's test for either outcome
+                    int hp[P];
 #pragma unroll
-                    for (int q = 0; q < P; ++q) {
-                        B[q] = __ballot_sync(0xffffffffu, sg[q] * h[q] <= lim[q]) & M[q];
-                        any |= B[q];
-                    }
-                    if (!any) break;
-                    unsigned Cf[P];
+                    for (int q2 = 0; q2 < P; ++q2) hp[q2] = h[q2] + fx * (int)(int8_t)(uint8_t)(rb >> (8 * q2));
+                    const bool tA = sg[q] * hp[q] <= lim[q], tR = sg[q] * h[q] <= lim[q];
+                    const bool acc = (__ballot_sync(0xffffffffu, t) >> L) & 1u;
 #pragma unroll
-                    for (int q = 0; q < P; ++q) {
-                        unsigned c = nz[q][q] & B[q] & below;
-#pragma unroll
-                        for (int q2 = 0; q2 < q; ++q2) c |= nz[q][q2] & B[q2];
-                        Cf[q] = __ballot_sync(0xffffffffu, c != 0u) & M[q];
-                    }
-                    int qc = P, Lc = 0;
-#pragma unroll
-                    for (int q = P - 1; q >= 0; --q)
-                        if (Cf[q]) { qc = q; Lc = __ffs(Cf[q]) - 1; }
-                    unsigned A[P];
-#pragma unroll
-                    for (int q = 0; q < P; ++q) {
-                        A[q] = q < qc ? B[q] : (q == qc ? (B[q] & ((1u << Lc) - 1u)) : 0u);
-                        apply_fields(A[q], q);
-                    }
-                    flip_signs(A);
-                    if (qc == P) break;  // every remaining decision was final
-#pragma unroll
-                    for (int q = 0; q < P; ++q)
-                        M[q] = q < qc ? 0u : (q == qc ? (M[q] & (0xffffffffu << Lc)) : M[q]);
-                }
-            } else {
-                // one accept per round: the first accepted unvisited position
-                while (true) {
-                    unsigned B[P];
-#pragma unroll
-                    for (int q = 0; q < P; ++q) B[q] = __ballot_sync(0xffffffffu, sg[q] * h[q] <= lim[q]) & M[q];
-                    int qs = -1;
-                    unsigned bq = 0u;
-#pragma unroll
-                    for (int q = P - 1; q >= 0; --q)
-                        if (B[q]) { qs = q; bq = B[q]; }
-                    if (qs < 0) break;
-                    const int L = __ffs(bq) - 1;
-                    unsigned A[P];
-#pragma unroll
-                    for (int q = 0; q < P; ++q) {
-                        A[q] = q == qs ? (1u << L) : 0u;
-                        if (q == qs) apply_fields(A[q], q);
-                    }
-                    flip_signs(A);
-#pragma unroll
-                    for (int q = 0; q < P; ++q)
-                        M[q] = q < qs ? 0u : (q == qs ? (M[q] & (0xfffffffeu << L)) : M[q]);
+                    for (int q2 = 0; q2 < P; ++q2) h[q2] = acc ? hp[q2] : h[q2];
+                    if (acc && lane == L) { dE += sg[q] * h[q]; sg[q] = -sg[q]; }
+                    X[q] ^= (unsigned)acc << L;
+                    t = acc ? tA : tR;
                 }
             }
         }
+    };
+
+    // One sweep in rounds (see above); returns the number of rounds.
+    auto sweep_rounds = [&](const int (&lim)[P]) -> int {
+        unsigned M[P];  // lanes whose position q has not been visited in this sweep
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int q = 0; q < P; ++q) M[q] = 0xffffffffu;
+        int rounds = 0;
+        if constexpr (kSparse) {
+            // Rounds of several accepts: the tentative decisions of all
+            // unvisited positions are taken against the current gains; a
+            // position's decision is final unless it is coupled to an
+            // earlier tentatively accepted position (whose flip would
+            // change its gain).  The first such position ends the round:
+            // the accepts before it are pairwise uncoupled, so applying
+            // them in any order gives exactly the gains a one-at-a-time
+            // sweep sees.
+            const unsigned below = (1u << lane) - 1u;
+            while (true) {
+                ++rounds;
+                unsigned B[P], any = 0u;
 #pragma unroll
-            for (int q = 0; q < P; ++q) limA[r][q] = limB[r][q];
+                for (int q = 0; q < P; ++q) {
+                    B[q] = __ballot_sync(0xffffffffu, sg[q] * h[q] <= lim[q]) & M[q];
+                    any |= B[q];
+                }
+                if (!any) break;
+                unsigned Cf[P];
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    unsigned c = nz[q][q] & B[q] & below;
+#pragma unroll
+                    for (int q2 = 0; q2 < q; ++q2) c |= nz[q][q2] & B[q2];
+                    Cf[q] = __ballot_sync(0xffffffffu, c != 0u) & M[q];
+                }
+                int qc = P, Lc = 0;
+#pragma unroll
+                for (int q = P - 1; q >= 0; --q)
+                    if (Cf[q]) { qc = q; Lc = __ffs(Cf[q]) - 1; }
+                unsigned A[P];
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    A[q] = q < qc ? B[q] : (q == qc ? (B[q] & ((1u << Lc) - 1u)) : 0u);
+                    apply_fields(A[q], q);
+                }
+                flip_signs(A);
+                if (qc == P) break;  // every remaining decision was final
+#pragma unroll
+                for (int q = 0; q < P; ++q)
+                    M[q] = q < qc ? 0u : (q == qc ? (M[q] & (0xffffffffu << Lc)) : M[q]);
+            }
+        } else {
+            // one accept per round: the first accepted unvisited position
+            while (true) {
+                ++rounds;
+                unsigned B[P];
+#pragma unroll
+                for (int q = 0; q < P; ++q) B[q] = __ballot_sync(0xffffffffu, sg[q] * h[q] <= lim[q]) & M[q];
+                int qs = -1;
+                unsigned bq = 0u;
+#pragma unroll
+                for (int q = P - 1; q >= 0; --q)
+                    if (B[q]) { qs = q; bq = B[q]; }
+                if (qs < 0) break;
+                const int L = __ffs(bq) - 1;
+                unsigned A[P];
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    A[q] = q == qs ? (1u << L) : 0u;
+                    if (q == qs) apply_fields(A[q], q);
+                }
+                flip_signs(A);
+#pragma unroll
+                for (int q = 0; q < P; ++q)
+                    M[q] = q < qs ? 0u : (q == qs ? (M[q] & (0xfffffffeu << L)) : M[q]);
+            }
+        }
+        return rounds;
+    };
+
+    if constexpr (SEQ != 0) {
+        // the limits of sweep k + 1 are loaded while sweep k runs; a Philox
+        // block of each owned position covers 4 sweeps
+        u32x4 ub[P];
+        auto philox_block = [&](int k) {
+#pragma unroll
+            for (int q = 0; q < P; ++q)
+                ub[q] = philox10((uint32_t)(k >> 2), (kTagAnneal << 24) | (uint32_t)(lane + 32 * q), slot, iter,
+                                 d.k0, d.k1);
+        };
+        auto limits_of = [&](int k, int (&out)[P]) {
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int w = k & 3;
+                const uint32_t u = w == 0 ? ub[q].v[0] : (w == 1 ? ub[q].v[1] : (w == 2 ? ub[q].v[2] : ub[q].v[3]));
+                out[q] = valid[q] ? __ldg(a.limtab + (size_t)k * 4096 + (u >> 20)) : INT_MIN;
+            }
+        };
+        // SEQ 3 picks the scheme per sweep from the previous sweep's accepts:
+        // a round costs about as much as 7 positions of the by-position sweep,
+        // and the last rounds sweep gives the rounds per accept.  Both schemes
+        // give the same trajectory, so the choice only changes the time.
+        int a_prev = m, r_last = 1, a_last = kSparse ? 3 : 1;
+        int limN[P];
+        philox_block(0);
+        limits_of(0, limN);
+#pragma unroll 1
+        for (int k = 0; k < a.sweeps; ++k) {
+            int lim[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) lim[q] = limN[q];
+            if (k + 1 < a.sweeps) {
+                if (((k + 1) & 3) == 0) philox_block(k + 1);
+                limits_of(k + 1, limN);
+            }
+            if constexpr (SEQ == 3) {
+                unsigned Xs[P];
+#pragma unroll
+                for (int q = 0; q < P; ++q) Xs[q] = X[q];
+                const bool rounds_now = 7 * (r_last * a_prev + a_last) < m * a_last;
+                int r = 0;
+                if (rounds_now) r = sweep_rounds(lim);
+                else sweep_seq(lim);
+                int acc = 0;
+#pragma unroll
+                for (int q = 0; q < P; ++q) acc += __popc(X[q] ^ Xs[q]);
+                a_prev = acc;
+                if (rounds_now && acc > 0) { r_last = r; a_last = acc; }
+            } else {
+                sweep_seq(lim);
+            }
+        }
+    } else {
+        int limA[4][P];
+        load_limits(0, limA);
+        for (int k4 = 0; k4 < a.sweeps; k4 += 4) {
+            int limB[4][P];
+            if (k4 + 4 < a.sweeps) load_limits(k4 + 4, limB);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (k4 + r >= a.sweeps) break;
+                sweep_rounds(limA[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < P; ++q) limA[r][q] = limB[r][q];
+        }
     }
 
     unsigned changed = 0;
@@ -323,7 +427,7 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
 }
 
 // One warp per subQUBO, subQUBO s = CTA * warps + warp (sizes up to 32 P).
-template <int P>
+template <int P, int SEQ>
 __global__ __launch_bounds__(128) void k_anneal(Dev d, AnnealArgs a)
 {
     constexpr int MC = 32 * P;
@@ -331,7 +435,7 @@ __global__ __launch_bounds__(128) void k_anneal(Dev d, AnnealArgs a)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const int s = blockIdx.x * wpb + wib;
     if (s >= a.count) return;  // whole warp leaves; no block-level barriers below
-    anneal_one<P>(d, a, s, lane, reinterpret_cast<int8_t*>(smem) + (size_t)wib * MC * MC);
+    anneal_one<P, SEQ>(d, a, s, lane, reinterpret_cast<int8_t*>(smem) + (size_t)wib * MC * MC);
 }
 
 // Persistent batch of subQUBOs of uneven size: every warp takes the next
@@ -339,7 +443,7 @@ __global__ __launch_bounds__(128) void k_anneal(Dev d, AnnealArgs a)
 // descending, built by k_sizes) and anneals it with the narrowest lane layout
 // that fits its size.  The queue is one counter; no warp ever waits on
 // another, and each subQUBO's result does not depend on which warp runs it.
-template <int PMAX>
+template <int PMAX, int SEQ>
 __global__ __launch_bounds__(128) void k_anneal_queue(Dev d, AnnealArgs a)
 {
     constexpr int MC = 32 * PMAX;
@@ -353,10 +457,10 @@ __global__ __launch_bounds__(128) void k_anneal_queue(Dev d, AnnealArgs a)
         if (next >= a.count) break;
         const int s = a.order[next];
         const int m = a.off[s + 1] - a.off[s];
-        if (m <= 32) anneal_one<1>(d, a, s, lane, Qs);
-        else if (m <= 64) { if constexpr (PMAX >= 2) anneal_one<2>(d, a, s, lane, Qs); }
-        else if (m <= 128) { if constexpr (PMAX >= 4) anneal_one<4>(d, a, s, lane, Qs); }
-        else { if constexpr (PMAX >= 8) anneal_one<8>(d, a, s, lane, Qs); }
+        if (m <= 32) anneal_one<1, SEQ>(d, a, s, lane, Qs);
+        else if (m <= 64) { if constexpr (PMAX >= 2) anneal_one<2, SEQ>(d, a, s, lane, Qs); }
+        else if (m <= 128) { if constexpr (PMAX >= 4) anneal_one<4, SEQ>(d, a, s, lane, Qs); }
+        else { if constexpr (PMAX >= 8) anneal_one<8, SEQ>(d, a, s, lane, Qs); }
         __syncwarp();  // the tile is reused by the next subQUBO
     }
 }
@@ -380,37 +484,37 @@ cudaError_t launch_limtab(const uint32_t* beta, int sweeps, const uint32_t* nlog
     return cudaGetLastError();
 }
 
-template <int P>
+template <int P, int SEQ>
 static cudaError_t launch_anneal_p(const Dev& d, const AnnealArgs& a, int wpb, cudaStream_t s)
 {
     constexpr int MC = 32 * P;
     const size_t sm = (size_t)wpb * MC * MC;
-    cudaError_t e = cudaFuncSetAttribute(k_anneal<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_anneal<P, SEQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int blocks = (a.count + wpb - 1) / wpb;
-    k_anneal<P><<<blocks, 32 * wpb, sm, s>>>(d, a);
+    k_anneal<P, SEQ><<<blocks, 32 * wpb, sm, s>>>(d, a);
     note_launch(1);
     return cudaGetLastError();
 }
 
 // Persistent launch: as many warps as fit on the GPU at once (by shared
 // memory), never more than there are subQUBOs.
-template <int PMAX>
+template <int PMAX, int SEQ>
 static cudaError_t launch_anneal_queue(const Dev& d, const AnnealArgs& a, int wpb, cudaStream_t s)
 {
     constexpr int MC = 32 * PMAX;
     const size_t per_warp = (size_t)MC * MC;
     const size_t sm = (size_t)wpb * per_warp;
-    cudaError_t e = cudaFuncSetAttribute(k_anneal_queue<PMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_anneal_queue<PMAX, SEQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int ctas_per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_anneal_queue<PMAX>, 32 * wpb, sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_anneal_queue<PMAX, SEQ>, 32 * wpb, sm);
     if (e != cudaSuccess) return e;
     if (ctas_per_sm < 1) ctas_per_sm = 1;
     int blocks = device_sm_count() * ctas_per_sm;
     const int need = (a.count + wpb - 1) / wpb;
     if (blocks > need) blocks = need;
-    k_anneal_queue<PMAX><<<blocks, 32 * wpb, sm, s>>>(d, a);
+    k_anneal_queue<PMAX, SEQ><<<blocks, 32 * wpb, sm, s>>>(d, a);
     note_launch(1);
     return cudaGetLastError();
 }
@@ -424,18 +528,27 @@ cudaError_t launch_anneal(const Dev& d, const AnnealArgs& a, cudaStream_t s)
     if (wpb <= 0) wpb = m <= 128 ? 2 : 1;
     if (m > 128 && wpb > 3) wpb = 3;
     if (wpb > 4) wpb = 4;
-    if (a.queue) {
-        if (m <= 32) return launch_anneal_queue<1>(d, a, wpb, s);
-        if (m <= 64) return launch_anneal_queue<2>(d, a, wpb, s);
-        if (m <= 128) return launch_anneal_queue<4>(d, a, wpb, s);
-        if (m <= 256) return launch_anneal_queue<8>(d, a, wpb, s);
-        return cudaErrorInvalidValue;
-    }
-    if (m <= 32) return launch_anneal_p<1>(d, a, wpb, s);
-    if (m <= 64) return launch_anneal_p<2>(d, a, wpb, s);
-    if (m <= 128) return launch_anneal_p<4>(d, a, wpb, s);
-    if (m <= 256) return launch_anneal_p<8>(d, a, wpb, s);
+    const int seq = a.scheme == 0 ? 3 : a.scheme - 1;
+#define ICD2S_ANNEAL_SEQ(SQ)                                           \
+    if (a.queue) {                                                     \
+        if (m <= 32) return launch_anneal_queue<1, SQ>(d, a, wpb, s);  \
+        if (m <= 64) return launch_anneal_queue<2, SQ>(d, a, wpb, s);  \
+        if (m <= 128) return launch_anneal_queue<4, SQ>(d, a, wpb, s); \
+        if (m <= 256) return launch_anneal_queue<8, SQ>(d, a, wpb, s); \
+        return cudaErrorInvalidValue;                                  \
+    }                                                                  \
+    if (m <= 32) return launch_anneal_p<1, SQ>(d, a, wpb, s);          \
+    if (m <= 64) return launch_anneal_p<2, SQ>(d, a, wpb, s);          \
+    if (m <= 128) return launch_anneal_p<4, SQ>(d, a, wpb, s);         \
+    if (m <= 256) return launch_anneal_p<8, SQ>(d, a, wpb, s);         \
     return cudaErrorInvalidValue;
+    switch (seq) {
+        case 0: { ICD2S_ANNEAL_SEQ(0) }
+        case 1: { ICD2S_ANNEAL_SEQ(1) }
+        case 2: { ICD2S_ANNEAL_SEQ(2) }
+        default: { ICD2S_ANNEAL_SEQ(3) }
+    }
+#undef ICD2S_ANNEAL_SEQ
 }
 
 }  // namespace icd2s

@@ -342,6 +342,10 @@ static cudaError_t launch_tabu_w(const Dev& d, int alpha, int c, int sh, cudaStr
     auto kern = k_tabu<W, MAXT, ASP, CK, SR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+    // as little shared memory as the block needs: the rest of the SM's 256 KB
+    // is L1, which holds the recently moved rows of Q
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxL1);
+    if (e != cudaSuccess) return e;
     kern<<<d.R, nt, sm, s>>>(d, alpha, c, sh);
     note_launch(1);
     return cudaGetLastError();

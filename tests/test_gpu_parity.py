@@ -313,15 +313,20 @@ def test_control_parameters_and_selection(L, orc, n, R, K, m_min, m_max):
 SIZES = [1, 5, 16, 31, 32, 33, 64, 65, 100, 128, 129, 200, 256]
 
 
+@pytest.mark.parametrize("scheme", [1, 2, 3, 4])
 @pytest.mark.parametrize("sweeps,T_max,density", [(1, 50.0, 1.0), (7, 400.0, 1.0), (64, 2000.0, 1.0),
                                                    (64, 3000.0, 0.05), (32, 800.0, 0.2)])
-def test_anneal(L, orc, sweeps, T_max, density):
-    """Dense subQUBOs take one accept per round; sparse ones (5 %, 20 %)
-    exercise the rounds of several uncoupled accepts."""
+def test_anneal(L, orc, sweeps, T_max, density, scheme):
+    """Every sweep scheme (rounds of decisions, position by position,
+    position by position with both outcomes of the next test, and the choice
+    per sweep) gives the sequential Metropolis sweep.  Dense subQUBOs take one accept per round;
+    sparse ones (5 %, 20 %) exercise the rounds of several uncoupled
+    accepts."""
     torch = torch_cuda()
     n, R, it = 2000, 3, 17
     K = len(SIZES) // R + 1
     P = Problem(n, density, 21, R=R, state_seed=1234)
+    I.icd2s_set_tuning(P.st, anneal_scheme=scheme)
     X0 = random_solutions(n, R, 2)
     P.load(X0)
     groups, offs = [], [0]

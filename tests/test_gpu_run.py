@@ -93,6 +93,29 @@ def test_run_batched_uneven_subqubos(L, orc):
     _compare_runs(orc, Q, lp, 11)
 
 
+@pytest.mark.parametrize("scheme", [1, 2, 3, 4])
+def test_run_uneven_subqubos_in_every_sweep_scheme(L, orc, scheme):
+    """The persistent uneven-batch kernel (subQUBOs of 20..250 variables, all
+    four lane layouts) in each sweep scheme: the whole run equals the
+    oracle's."""
+    n = 1200
+    Q = make_qubo(n, 0.3, 9)
+    lp = lib_params(I, n, z=3, K=4, m_min=20, m_max=250, m_init=100, alpha=n, c=4, sweeps=20, T_max=3000.0,
+                    mut_mode=0, patience=0, max_iters=4)
+    q = I.icd2s_qubo_create(Q)
+    st = I.icd2s_state_create(q, lp.z, 13)
+    try:
+        I.icd2s_set_tuning(st, anneal_scheme=scheme)
+        g = I.icd2s_state_run(st, n, lp, trace=True, want_S=True)
+    finally:
+        I.icd2s_state_destroy(st)
+        I.icd2s_qubo_destroy(q)
+    o = orc.run(Q, orc_params(orc, lp), 13)
+    assert g["iters"] == o["iters"] and np.array_equal(g["trace"], o["trace"])
+    assert np.array_equal(g["S"], o["S"])
+    assert g["best_E"] == o["best_E"] and np.array_equal(g["best_x"], o["best_x"])
+
+
 def test_run_tiny_instances_reach_the_optimum(L, orc):
     import itertools
     for n, seed in [(12, 1), (16, 2)]:
