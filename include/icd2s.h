@@ -404,8 +404,9 @@ typedef struct icd2s_tuning {
     int32_t anneal_scheme;    /* sweep of the Ising-machine kernel (every scheme gives the same
                                  trajectory): 0 = default (4), 1 = rounds of decisions, 2 =
                                  position by position, 3 = position by position with the next
-                                 test taken for both outcomes, 4 = 1 or 3 per sweep, whichever
-                                 the previous sweep's accepts predict cheaper */
+                                 test taken for both outcomes, 4 = per sweep either 1 or by
+                                 position (2 up to 64 variables, 3 beyond), whichever the
+                                 previous sweep's accepts predict cheaper */
     int32_t reserved[1];
 } icd2s_tuning;
 int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t);

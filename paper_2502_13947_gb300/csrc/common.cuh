@@ -143,7 +143,8 @@ struct AnnealArgs {
     int32_t* queue;                       // non-null: persistent kernel, subQUBOs taken in `order`
     const int32_t* order;
     int scheme;                           // sweep scheme: 0 default (4), 1 rounds, 2 by position, 3 by
-                                          // position with both outcomes of the next test, 4 per sweep 1 or 3
+                                          // position with both outcomes of the next test, 4 per sweep 1 or
+                                          // by position
 };
 int device_sm_count();
 bool tabu_variant_fits(int variant, int n);

@@ -70,7 +70,8 @@ __device__ __forceinline__ int accept_limit(uint32_t thr, uint32_t beta)
 // SEQ: 0 = rounds (multi-accept for P <= 4, first accept for P = 8);
 // 1 = position by position; 2 = position by position with the next
 // position's decision taken for both outcomes of the current one; 3 = per
-// sweep, rounds or 2, whichever the previous sweep's accepts predict cheaper.
+// sweep, rounds or by position (1 for P <= 2, 2 beyond), whichever the
+// previous sweep's accepts predict cheaper.
 template <int P, int SEQ>
 __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, int s, int lane, int8_t* Qs)
 {
@@ -209,19 +210,27 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
             const int8_t* base = Qs + (size_t)(32 * q) * MC + lane * P;
             Seg rn = *reinterpret_cast<const Seg*>(base);
             bool t = sg[q] * h[q] <= lim[q];  // the decision input of position 32 q
+            // x of position 32 q + L only changes at step L, so the block-start
+            // values give every step's factor; the flips of the block are
+            // collected apart and applied to X at its end (no chain through X)
+            const unsigned xs = X[q];
+            unsigned fl = 0u;
 #pragma unroll(P <= 4 ? 32 : 8)
             for (int L = 0; L < 32; ++L) {
-                if (32 * q + L >= m) break;
+                // positions past m (checked every 8) are harmless: their test
+                // fails (limit INT_MIN) and their tile rows are in bounds
+                if ((L & 7) == 0 && 32 * q + L >= m) break;
                 const Seg rb = rn;
                 if (L < 31) rn = *reinterpret_cast<const Seg*>(base + (size_t)(L + 1) * MC);
-                const int fx = ((X[q] >> L) & 1u) ? -2 : 2;  // 2 (1 - 2 x_b)
-                if constexpr (SEQ == 1) {
+                const int fx = ((xs >> L) & 1u) ? -2 : 2;  // 2 (1 - 2 x_b)
+                // the simple form for up to 64 positions, both outcomes beyond (measured)
+                if constexpr (SEQ == 1 || (SEQ == 3 && P <= 2)) {
                     const bool acc = (__ballot_sync(0xffffffffu, t) >> L) & 1u;
                     const int f = acc ? fx : 0;
 #pragma unroll
                     for (int q2 = 0; q2 < P; ++q2) h[q2] += f * (int)(int8_t)(uint8_t)(rb >> (8 * q2));
                     if (acc && lane == L) { dE += sg[q] * h[q]; sg[q] = -sg[q]; }
-                    X[q] ^= (unsigned)acc << L;
+                    fl |= (unsigned)acc << L;
                     t = sg[q] * h[q] <= lim[q];
                 } else {
                     // fields if b flips, and the next position's test for either outcome
@@ -233,10 +242,11 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
 #pragma unroll
                     for (int q2 = 0; q2 < P; ++q2) h[q2] = acc ? hp[q2] : h[q2];
                     if (acc && lane == L) { dE += sg[q] * h[q]; sg[q] = -sg[q]; }
-                    X[q] ^= (unsigned)acc << L;
+                    fl |= (unsigned)acc << L;
                     t = acc ? tA : tR;
                 }
             }
+            X[q] ^= fl;
         }
     };
 
