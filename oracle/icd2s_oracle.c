@@ -527,6 +527,10 @@ typedef struct {
     int32_t ablation;    /* 0: the method; 1: No_IM (no Ising-machine call); 2: No_SM (no control
                             parameters: a random ranking and flip probability 1/2) */
     int32_t aspiration;  /* Tabu search with the aspiration criterion (reading S4) */
+    int32_t im_order;    /* K > 1 subQUBOs of a solution: 0 = every one built from the state before
+                            the call (Jacobi merge, reading S16); 1 = one after the other, each built
+                            from the state the previous ones left (Gauss-Seidel, the order in which
+                            Section 3 describes Call_IM_Solution_Set) */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -725,10 +729,12 @@ int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t see
         msel[p] = 0;
         for (int32_t k = 0; k < K; ++k) {
             int32_t m = sizes[k];
-            /* every subQUBO of this call is built from the state before
-             * the call (Jacobi merge, reading S16) */
-            orc_subqubo(Q, n, S_pre, idx + off, m, Qs, NULL);
-            for (int32_t a = 0; a < m; ++a) xs[a] = S_pre[idx[off + a]];
+            /* Jacobi (reading S16): every subQUBO of this call is built
+             * from the state before the call; Gauss-Seidel: from the state
+             * with the earlier subQUBOs' results written back */
+            const uint8_t* base = prm->im_order == 1 ? x : S_pre;
+            orc_subqubo(Q, n, base, idx + off, m, Qs, NULL);
+            for (int32_t a = 0; a < m; ++a) xs[a] = base[idx[off + a]];
             if (prm->im_mode == 1)
                 orc_exact_subqubo(Qs, m, xs);
             else

@@ -48,7 +48,7 @@ class Params(C.Structure):
         ("w1", C.c_int64), ("w2", C.c_int64), ("w3", C.c_int64),
         ("mut_mode", C.c_int32), ("mut_rate", C.c_double),
         ("patience", C.c_int32), ("max_iters", C.c_int32), ("select_mode", C.c_int32), ("im_mode", C.c_int32),
-        ("ablation", C.c_int32), ("aspiration", C.c_int32),
+        ("ablation", C.c_int32), ("aspiration", C.c_int32), ("im_order", C.c_int32),
     ]
 
 

@@ -561,3 +561,61 @@ def test_tabu_without_aspiration_is_algorithm_1(orc):
     b = orc.tabu_asp(Q, x0, 200, 5, aspiration=False)
     assert np.array_equal(a[0], b[0]) and a[1] == b[1]
     assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+
+
+# ----------------------------------------------------------------------------- Gauss-Seidel multi-IM order
+def _im_phase_by_pieces(orc, Q, prm, seed, t, S, gauss_seidel):
+    """The Ising-machine phase of one step rebuilt from the pinned pieces:
+    Tabu search, gamma / delta / A, the subQUBO sizes and groups, then each
+    group's subQUBO (Eq. 4) annealed and written back -- built from the state
+    before the call (Jacobi) or from the state the earlier groups left
+    (Gauss-Seidel)."""
+    n, z, K = Q.shape[0], prm.z, prm.K
+    eh = orc.eta_hat(orc.eta(Q))
+    tab = [orc.tabu(Q, S[p], prm.alpha, prm.c) for p in range(z)]
+    X = np.stack([r[0] for r in tab])
+    gam = orc.gamma(X)
+    beta, nlog = orc.beta_table(prm.sweeps, prm.T_max, prm.T_min), orc.nlog_table()
+    out = X.copy()
+    for p in range(z):
+        A = orc.aggregate(eh, gam, orc.delta(tab[p][2]))
+        sizes = orc.subqubo_sizes(K, prm.m_min, prm.m_max, seed, p, t)
+        idx = orc.select(A, sizes)
+        pre, off = X[p].copy(), 0
+        for k, m in enumerate(sizes):
+            grp = idx[off:off + m]
+            base = out[p] if gauss_seidel else pre
+            Qs, _ = orc.subqubo(Q, base, grp)
+            xs, _, _ = orc.anneal(Qs, base[grp], beta, nlog, seed, p * K + k, t)
+            out[p, grp] = xs
+            off += m
+    return out
+
+
+def test_gauss_seidel_order_of_the_subqubos(orc):
+    """im_order 1: group k's subQUBO is built from the solution with groups
+    0..k-1 already written back; im_order 0 builds every group from the
+    solution before the call.  Both equal the step rebuilt from its pinned
+    pieces (the mutation is switched off so the step ends with the IM phase),
+    they differ on some solution, and with K = 1 they are the same step."""
+    Q = make_qubo(70, 0.6, 17)
+    n, z, seed, t = 70, 5, 23, 2
+    # a short Tabu search leaves the solutions far from a local minimum, so the
+    # Ising machine changes many variables and the two orders part
+    prm = orc.default_params(n, z=z, K=4, m_min=5, m_max=12, m_init=10, alpha=5, c=3, sweeps=24,
+                             T_max=120.0, mut_mode=1, mut_rate=0.0, max_iters=3)
+    S = random_solutions(n, z, 31)
+    res = {}
+    for order in (0, 1):
+        prm.im_order = order
+        r = orc.step(Q, prm, seed, t, S)
+        want = _im_phase_by_pieces(orc, Q, prm, seed, t, S, order == 1)
+        assert np.array_equal(r["S"], want), order
+        assert np.array_equal(r["E"], orc.energy_batch(Q, want))
+        res[order] = r["S"]
+    assert not np.array_equal(res[0], res[1])
+    prm.K, prm.m_min, prm.m_max = 1, 12, 12
+    prm.im_order = 0
+    a = orc.step(Q, prm, seed, t, S)["S"]
+    prm.im_order = 1
+    assert np.array_equal(orc.step(Q, prm, seed, t, S)["S"], a)
