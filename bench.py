@@ -473,14 +473,18 @@ def run_gpu(args, w):
 # iteration budget is spent (a miss, censored at the budget).
 TTT_INSTANCES = {"n5000-d0.5": dict(n=5000, density=0.5, qseed=0),
                  "n10000-d0.5": dict(n=10000, density=0.5, qseed=0)}
-TTT_METHODS = {  # (K, m_min, m_max, select_mode, ablation)
-    "plain": (1, 64, 64, 0, 0),
-    "batched": (16, 32, 256, 0, 0),
-    "learned": (1, 64, 64, 1, 0),
-    "learned+batched": (16, 32, 256, 1, 0),
-    "hybrid+batched": (16, 32, 256, 2, 0),
-    "No_IM": (1, 64, 64, 0, 1),      # the simplified versions of Section 4
-    "No_SM": (1, 64, 64, 0, 2),
+TTT_METHODS = {  # (K, m_min, m_max, select_mode, ablation, im_order, alpha / n)
+    "plain": (1, 64, 64, 0, 0, 0, 5),
+    "batched": (16, 32, 256, 0, 0, 0, 5),
+    "learned": (1, 64, 64, 1, 0, 0, 5),
+    "learned+batched": (16, 32, 256, 1, 0, 0, 5),
+    "hybrid+batched": (16, 32, 256, 2, 0, 0, 5),
+    "batched GS": (16, 32, 256, 0, 0, 1, 5),          # Gauss-Seidel order of the 16 subQUBOs
+    "learned+batched GS": (16, 32, 256, 1, 0, 1, 5),
+    "No_IM": (1, 64, 64, 0, 1, 0, 5),      # the simplified versions of Section 4
+    "No_SM": (1, 64, 64, 0, 2, 0, 5),
+    "Tabu-only a=20n": (1, 64, 64, 0, 1, 0, 20),  # classical comparator: Tabu + mutation at the
+                                                  # alpha = 20n the paper gives the Tabu-only solver
 }
 # improvement logs of the plain method for training: shapes of the n = 64
 # dense, n = 2500 sparse and n = 5000 batched workloads, instance seeds 200+
@@ -549,11 +553,11 @@ def run_ttt(args):
             longs.append(r["best_E"])
         E_star = min(longs)
         res = dict(target_E=E_star, target_runs=longs, budget_iters=args.ttt_budget)
-        for meth, (K, m_min, m_max, mode, ablation) in TTT_METHODS.items():
+        for meth, (K, m_min, m_max, mode, ablation, order, amul) in TTT_METHODS.items():
             per = []
             for seed in range(args.ttt_seeds):
                 p = ttt_params(I, n, K, m_min, m_max, mode, args.ttt_budget)
-                p.ablation = ablation
+                p.ablation, p.im_order, p.alpha = ablation, order, amul * n
                 p.stop_at_target, p.target_E = 1, E_star
                 st = I.icd2s_state_create(q, p.z, seed)
                 if mode:
@@ -575,7 +579,8 @@ def run_ttt(args):
     line = {"metric": "time-to-target energy", "unit": "ms", "higher_is_better": False, "n_gpus": 1,
             "data": "synthetic", "dtype": "int32/int64 (network: bf16 weights, f32)",
             "config": {"workload": "time-to-target, z=32, alpha=5n, c=n/150, 256 sweeps, T 2000->1, Eq. 5 mutation",
-                       "methods": {k: dict(K=v[0], m_min=v[1], m_max=v[2], select_mode=v[3], ablation=v[4])
+                       "methods": {k: dict(K=v[0], m_min=v[1], m_max=v[2], select_mode=v[3], ablation=v[4],
+                                           im_order=v[5], alpha=f"{v[6]}n")
                                    for k, v in TTT_METHODS.items()}},
             "train": train_info, "results": results, "wall_s": round(time.time() - t0, 1)}
     print(json.dumps(line), flush=True)

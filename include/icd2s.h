@@ -95,7 +95,12 @@ typedef struct icd2s_params {
                               admissible when it would beat the best objective visited so far; a
                               variable moved while tabu keeps c more iterations of tabu memory, and
                               when every move is tabu the unmasked arg-min is taken */
-    int32_t reserved[3];
+    int32_t im_order;      /* K > 1 subQUBOs per solution (Algorithm 4 on a multi-IM fabric): 0 =
+                              each built from the solution before the call and the flips merged
+                              (Jacobi, reading S16); 1 = one after the other, each built from the
+                              solution the earlier ones left (Gauss-Seidel, the order Section 3
+                              gives Call_IM_Solution_Set) */
+    int32_t reserved[2];
 } icd2s_params;
 
 /* Per-call anneal parameters (the emulated Ising machine). */

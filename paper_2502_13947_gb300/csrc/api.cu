@@ -283,6 +283,7 @@ static int check_params(const icd2s_state* st, const icd2s_params* p)
     REQ(p->ablation >= 0 && p->ablation <= 2, ICD2S_ERR_ARG, "ablation=%d outside 0..2", p->ablation);
     REQ(p->ablation == 0 || p->select_mode == 0, ICD2S_ERR_ARG, "the ablations use the paper's selection rule");
     REQ(p->aspiration == 0 || p->aspiration == 1, ICD2S_ERR_ARG, "aspiration must be 0 or 1");
+    REQ(p->im_order == 0 || p->im_order == 1, ICD2S_ERR_ARG, "im_order must be 0 or 1");
     return ICD2S_OK;
 }
 
@@ -598,7 +599,7 @@ int icd2s_select_subqubos(icd2s_state* st, const icd2s_select_params* sp, int32_
 static int anneal_impl(icd2s_state* st, const int32_t* idx, const int32_t* off, int count, int per_replica,
                        int m_max, int block_m, int block_base, int sweeps, double T_max, double T_min, uint32_t iter,
                        uint8_t* mask, int ldm, int64_t* dE, cudaStream_t s, bool queued = false,
-                       const int32_t* iter_dev = nullptr, int im_mode = 0)
+                       const int32_t* iter_dev = nullptr, int im_mode = 0, int group_k = -1)
 {
     int rc = ensure_beta(st, sweeps, T_max, T_min, s);
     if (rc) return rc;
@@ -609,6 +610,7 @@ static int anneal_impl(icd2s_state* st, const int32_t* idx, const int32_t* off, 
     a.warps_per_cta = st->tune.anneal_warps_per_cta;
     a.scheme = st->tune.anneal_scheme;
     a.iter_dev = iter_dev;
+    if (group_k >= 0) { a.group_stride = per_replica; a.group_k = group_k; }  // count = replicas
     if (im_mode == 1) {  // exact Ising machine (m <= 24)
         CK(launch_exact(st->d, a, s));
         return ICD2S_OK;
@@ -823,7 +825,15 @@ static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* tra
     if (rc) return rc;
     mark(st, 1, 1, s);
     mark(st, 2, 0, s);
-    if (p->ablation != 1) {                                                                 // No_IM skips the IM
+    if (p->ablation != 1 && p->im_order == 1 && p->K > 1) {
+        // Gauss-Seidel: group k of every replica, written back before group k + 1 is built
+        for (int k = 0; k < p->K; ++k) {
+            rc = anneal_impl(st, st->idx, st->off, R, p->K, p->m_max, 0, 0, p->sweeps, p->T_max, p->T_min,
+                             (uint32_t)t, nullptr, 0, nullptr, s, false, it_dev, p->im_mode, k);
+            if (rc) return rc;
+            if (k + 1 < p->K) CK(launch_apply(st->d, s));
+        }
+    } else if (p->ablation != 1) {                                                          // No_IM skips the IM
         rc = anneal_impl(st, st->idx, st->off, R * p->K, p->K, p->m_max, 0, 0, p->sweeps, p->T_max, p->T_min,
                          (uint32_t)t, nullptr, 0, nullptr, s, queued, it_dev, p->im_mode);  // Eq. 4, Algorithm 4
         if (rc) return rc;

@@ -142,6 +142,8 @@ struct AnnealArgs {
     const int32_t* iter_dev;              // non-null: the iteration number is read from here
     int32_t* queue;                       // non-null: persistent kernel, subQUBOs taken in `order`
     const int32_t* order;
+    int group_stride, group_k;            // group_stride > 0: launch subQUBO s is s * group_stride + group_k
+                                          // (one group of every replica, Gauss-Seidel order)
     int scheme;                           // sweep scheme: 0 default (4), 1 rounds, 2 by position, 3 by
                                           // position with both outcomes of the next test, 4 per sweep 1 or
                                           // by position

@@ -445,7 +445,8 @@ __global__ __launch_bounds__(128) void k_anneal(Dev d, AnnealArgs a)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     const int s = blockIdx.x * wpb + wib;
     if (s >= a.count) return;  // whole warp leaves; no block-level barriers below
-    anneal_one<P, SEQ>(d, a, s, lane, reinterpret_cast<int8_t*>(smem) + (size_t)wib * MC * MC);
+    const int se = a.group_stride > 0 ? s * a.group_stride + a.group_k : s;
+    anneal_one<P, SEQ>(d, a, se, lane, reinterpret_cast<int8_t*>(smem) + (size_t)wib * MC * MC);
 }
 
 // Persistent batch of subQUBOs of uneven size: every warp takes the next

@@ -37,7 +37,7 @@ __global__ __launch_bounds__(kExactThreads) void k_exact(Dev d, AnnealArgs a)
     __shared__ __align__(16) int8_t qs[kExactMaxM * kExactRow];
     __shared__ long long wbest[kExactThreads / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int s = blockIdx.x;
+    const int s = a.group_stride > 0 ? (int)blockIdx.x * a.group_stride + a.group_k : (int)blockIdx.x;
     const int p = s / a.per_replica;
     const int* S = nullptr;
     int m;

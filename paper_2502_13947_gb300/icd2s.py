@@ -54,7 +54,8 @@ class Params(C.Structure):
         ("w1", C.c_int64), ("w2", C.c_int64), ("w3", C.c_int64), ("mut_mode", C.c_int32), ("mut_rate", C.c_double),
         ("patience", C.c_int32), ("max_iters", C.c_int32), ("use_graph", C.c_int32), ("refresh_every", C.c_int32),
         ("select_mode", C.c_int32), ("stop_at_target", C.c_int32), ("target_E", C.c_int64),
-        ("im_mode", C.c_int32), ("ablation", C.c_int32), ("aspiration", C.c_int32), ("reserved", C.c_int32 * 3),
+        ("im_mode", C.c_int32), ("ablation", C.c_int32), ("aspiration", C.c_int32), ("im_order", C.c_int32),
+        ("reserved", C.c_int32 * 2),
     ]
 
 

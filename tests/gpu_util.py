@@ -28,4 +28,5 @@ def orc_params(orc, lp):
                       alpha=lp.alpha, c=lp.c, sweeps=lp.sweeps, T_max=lp.T_max, T_min=lp.T_min,
                       w1=lp.w1, w2=lp.w2, w3=lp.w3, mut_mode=lp.mut_mode, mut_rate=lp.mut_rate,
                       patience=lp.patience, max_iters=lp.max_iters, select_mode=lp.select_mode,
-                      im_mode=lp.im_mode, ablation=lp.ablation, aspiration=lp.aspiration)
+                      im_mode=lp.im_mode, ablation=lp.ablation, aspiration=lp.aspiration,
+                      im_order=lp.im_order)

@@ -197,3 +197,24 @@ def test_graph_steps_equal_plain_steps_on_a_stream(L):
     I.icd2s_qubo_destroy(q)
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("im_mode,K,m_min,m_max", [(0, 6, 8, 70), (0, 4, 20, 250), (1, 3, 6, 12)])
+def test_run_gauss_seidel_subqubos(L, orc, im_mode, K, m_min, m_max):
+    """im_order 1: a solution's subQUBOs are annealed (or solved exactly) one
+    group at a time, each built from the solution the earlier groups left;
+    the whole run (replayed as a CUDA graph) equals the oracle's."""
+    n = 1100
+    Q = make_qubo(n, 0.4, 12)
+    # a short Tabu search leaves the solutions far from a local minimum, so the
+    # Ising machine changes many variables and the order of the groups matters
+    lp = lib_params(I, n, z=3, K=K, m_min=m_min, m_max=m_max, m_init=min(m_max, 64), alpha=5, c=4,
+                    sweeps=20, T_max=2500.0, mut_mode=0, patience=0, max_iters=4, im_mode=im_mode, im_order=1)
+    g, o = _compare_runs(orc, Q, lp, 19)
+    lp.im_order = 0
+    q = I.icd2s_qubo_create(Q)
+    try:
+        j = I.icd2s_run(q, lp, 19, trace=True)
+    finally:
+        I.icd2s_qubo_destroy(q)
+    assert not np.array_equal(j["trace"], g["trace"])  # the order matters on this instance
