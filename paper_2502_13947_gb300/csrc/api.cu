@@ -165,6 +165,7 @@ struct icd2s_state {
     int32_t* H = nullptr;                    // [R][ld] hit counts
     int32_t* ACC = nullptr; unsigned* TT = nullptr;  // split write-back: partial-sum planes, tile tickets
     float* F = nullptr; float* score = nullptr; int32_t* gmax = nullptr;  // made on first use
+    uint16_t* tlog = nullptr; long long tlog_cap = 0;  // Tabu move logs beyond shared memory (on first use)
     bool have_features = false, have_scores = false;
     icd2s_mlp* mlp = nullptr;                // borrowed
     // improvement log (ring buffer)
@@ -186,7 +187,7 @@ static void free_state(icd2s_state* st)
                     st->off, st->scratch, st->counters, st->nlog, st->beta, st->limtab,
                     st->lpt, st->queue, st->ctx, st->rates, st->Xb, st->G2, st->E2, st->rflags,
                     st->H, st->F, st->score, st->gmax, st->LF, st->LY, st->lrep, st->prev_x, st->log_ctl,
-                    st->ACC, st->TT};
+                    st->ACC, st->TT, st->tlog};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (st->graph) cudaGraphExecDestroy(st->graph);
@@ -262,8 +263,6 @@ static int check_params(const icd2s_state* st, const icd2s_params* p)
     const int mi = p->m_init > 0 ? p->m_init : p->m_max;
     REQ(mi <= kMaxM && mi <= n, ICD2S_ERR_RANGE, "m_init=%d outside 1..min(256, n)", mi);
     REQ(p->alpha >= 0, ICD2S_ERR_ARG, "alpha < 0");
-    REQ(tabu_smem_bytes(n, p->alpha) <= 227 * 1024, ICD2S_ERR_RANGE,
-        "alpha=%d with n=%d needs more shared memory than a CTA has", p->alpha, n);
     REQ(p->c >= 1 && p->c <= n, ICD2S_ERR_ARG, "tenure c=%d outside 1..n", p->c);
     REQ(p->sweeps >= 1 && p->sweeps <= kMaxSweeps, ICD2S_ERR_RANGE, "sweeps=%d outside 1..%d", p->sweeps,
         kMaxSweeps);
@@ -534,13 +533,31 @@ int icd2s_get_control(icd2s_state* st, int32_t* A, int32_t* gamma, int32_t* delt
 }
 
 // ----------------------------------------------------------------------------- steps
+// Move logs in global memory for Tabu searches whose log (2 bytes a move) does
+// not fit shared memory beside the search's state: [R][alpha] uint16, made on
+// first use and kept (a captured step holds the pointer, so a new buffer bumps gen).
+static int ensure_tabu_log(icd2s_state* st, int alpha, cudaStream_t s)
+{
+    if (tabu_log_in_smem(st->q->n, alpha) || st->tlog_cap >= alpha) return ICD2S_OK;
+    CK(cudaStreamSynchronize(s));
+    if (st->tlog) { cudaFree(st->tlog); st->tlog = nullptr; st->tlog_cap = 0; }
+    cudaError_t e = dalloc(&st->tlog, (size_t)st->R * (size_t)alpha);
+    REQ(e == cudaSuccess, ICD2S_ERR_OOM, "Tabu move log of %lld bytes: %s", 2LL * st->R * alpha, cudaGetErrorString(e));
+    st->tlog_cap = alpha;
+    st->d.TL = st->tlog;
+    st->d.tl_cap = alpha;
+    ++st->gen;
+    return ICD2S_OK;
+}
+
 int icd2s_tabu(icd2s_state* st, int32_t alpha, int32_t c, void* stream)
 {
     REQ(st, ICD2S_ERR_ARG, "NULL state");
     const int n = st->q->n;
     REQ(alpha >= 0, ICD2S_ERR_ARG, "alpha < 0");
     REQ(c >= 1 && c <= n, ICD2S_ERR_ARG, "tenure c=%d outside 1..n", c);
-    REQ(tabu_smem_bytes(n, alpha) <= 227 * 1024, ICD2S_ERR_RANGE, "alpha=%d too large for n=%d", alpha, n);
+    int rc = ensure_tabu_log(st, alpha, S(stream));
+    if (rc) return rc;
     CK(launch_tabu(st->d, alpha, c, st->tune.tabu_variant, S(stream), false, st->tune.tabu_wide_keys != 0,
                    st->tune.tabu_rows));
     return ICD2S_OK;
@@ -552,7 +569,8 @@ int icd2s_tabu_aspiration(icd2s_state* st, int32_t alpha, int32_t c, void* strea
     const int n = st->q->n;
     REQ(alpha >= 0, ICD2S_ERR_ARG, "alpha < 0");
     REQ(c >= 1 && c <= n, ICD2S_ERR_ARG, "tenure c=%d outside 1..n", c);
-    REQ(tabu_smem_bytes(n, alpha) <= 227 * 1024, ICD2S_ERR_RANGE, "alpha=%d too large for n=%d", alpha, n);
+    int rc = ensure_tabu_log(st, alpha, S(stream));
+    if (rc) return rc;
     CK(launch_tabu(st->d, alpha, c, st->tune.tabu_variant, S(stream), true, st->tune.tabu_wide_keys != 0,
                    st->tune.tabu_rows));
     return ICD2S_OK;
@@ -804,6 +822,7 @@ static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* tra
     const bool queued = p->K > 1 || p->m_min != p->m_max;  // uneven batch: persistent queue kernel
     int rc = ensure_beta(st, p->sweeps, p->T_max, p->T_min, s);
     if (rc) return rc;
+    if ((rc = ensure_tabu_log(st, p->alpha, s))) return rc;  // (made before any capture by graph_step)
     const bool feats = wants_features(st, p);
     if (feats && (rc = ensure_features(st, s))) return rc;
     mark(st, 0, 0, s);
@@ -868,6 +887,7 @@ static int graph_step(icd2s_state* st, const icd2s_params* p, int t, cudaStream_
     if (rc) return rc;
     rc = ensure_rates(st, p->mut_mode, p->mut_rate, t + 1, caller);
     if (rc) return rc;
+    if ((rc = ensure_tabu_log(st, p->alpha, caller))) return rc;
     cudaStream_t s = caller;
     if (!s) {  // the legacy stream cannot be captured: run on a private stream joined to it
         if (!st->own_stream) CK(cudaStreamCreateWithFlags(&st->own_stream, cudaStreamNonBlocking));

@@ -86,6 +86,7 @@ struct Dev {
     uint32_t k0, k1; // Philox key = seed halves
     long long gain_bound;  // max_j 2 sum_i |Q_ij| >= |g_j| for every x
     const int8_t* Q2;      // [2n][ld] signed rows: row 2i + x = (1 - 2x) Q_i (null if Q has -128)
+    uint16_t* TL; long long tl_cap;  // Tabu move logs [R][tl_cap] for searches whose log exceeds shared memory
 };
 
 // Counts kernel launches (process-wide, for reporting).
@@ -114,6 +115,9 @@ cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_
 // Shift of the compact Tabu keys for n and the instance's gain bound (0: they do not apply).
 int tabu_key_shift(int n, long long gain_bound);
 size_t tabu_smem_bytes(int n, int alpha);
+constexpr size_t kTabuSmemLimit = 227 * 1024;
+// false: the Tabu move log of alpha moves goes to global memory (Dev::TL, tl_cap >= alpha)
+bool tabu_log_in_smem(int n, int alpha);
 cudaError_t launch_gamma(const Dev& d, cudaStream_t s);
 // Iteration context read by the kernels of a captured outer iteration (a CUDA
 // graph replays the same launches, so the iteration number and the mutation

@@ -77,7 +77,9 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh)
     int* nF = reinterpret_cast<int*>(smem + 512);                                     // [1]; +520: best visit
     int32_t* Ts = reinterpret_cast<int32_t*>(smem + 528);                             // [ld]
     uint32_t* undo = reinterpret_cast<uint32_t*>(smem + 528 + 4 * (size_t)d.ld);      // [ld / 32]
-    uint16_t* mlog = reinterpret_cast<uint16_t*>(smem + 528 + 4 * (size_t)d.ld + d.ld / 8);  // [alpha]
+    // [alpha]: in shared memory, or in global memory (d.TL) when a long search does not fit
+    uint16_t* mlog = d.TL ? d.TL + (size_t)blockIdx.x * (size_t)d.tl_cap
+                          : reinterpret_cast<uint16_t*>(smem + 528 + 4 * (size_t)d.ld + d.ld / 8);
 
     const int p = blockIdx.x;
     const int NT = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -332,13 +334,17 @@ size_t tabu_smem_bytes(int n, int alpha)
     return 528 + 4 * (size_t)ld + (size_t)ld / 8 + 2 * (size_t)alpha + 16;
 }
 
+bool tabu_log_in_smem(int n, int alpha) { return tabu_smem_bytes(n, alpha) <= kTabuSmemLimit; }
+
 template <int W, int MAXT, bool ASP, bool CK, bool SR>
 static cudaError_t launch_tabu_w(const Dev& d, int alpha, int c, int sh, cudaStream_t s)
 {
     int nt = (d.n + 4 * W - 1) / (4 * W);
     nt = (nt + 31) / 32 * 32;
     if (nt > MAXT) return cudaErrorInvalidConfiguration;
-    const size_t sm = tabu_smem_bytes(d.n, alpha);
+    const bool in_smem = tabu_log_in_smem(d.n, alpha);
+    if (!in_smem && (!d.TL || d.tl_cap < alpha)) return cudaErrorInvalidValue;
+    const size_t sm = tabu_smem_bytes(d.n, in_smem ? alpha : 0);
     auto kern = k_tabu<W, MAXT, ASP, CK, SR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -346,7 +352,9 @@ static cudaError_t launch_tabu_w(const Dev& d, int alpha, int c, int sh, cudaStr
     // is L1, which holds the recently moved rows of Q
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxL1);
     if (e != cudaSuccess) return e;
-    kern<<<d.R, nt, sm, s>>>(d, alpha, c, sh);
+    Dev dd = d;
+    if (tabu_log_in_smem(d.n, alpha)) dd.TL = nullptr;  // the move log stays in shared memory
+    kern<<<d.R, nt, sm, s>>>(dd, alpha, c, sh);
     note_launch(1);
     return cudaGetLastError();
 }

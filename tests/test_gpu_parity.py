@@ -144,6 +144,21 @@ def test_tabu_with_aspiration_when_every_move_is_tabu(L, orc):
         P.close()
 
 
+@pytest.mark.parametrize("asp", [0, 1])
+def test_tabu_with_a_move_log_beyond_shared_memory(L, orc, asp):
+    """alpha = 120 000 at n = 300: the move log (2 bytes a move) no longer fits
+    a CTA's shared memory and goes to global memory; the search still equals
+    the oracle's, and a later shorter search (log back in shared memory) too."""
+    n, R, c = 300, 2, 7
+    P = Problem(n, 0.5, 77, R=R)
+    X0 = random_solutions(n, R, 78)
+    for alpha in (120_000, 900):
+        P.load(X0)
+        (I.icd2s_tabu_aspiration if asp else I.icd2s_tabu)(P.st, alpha, c)
+        _check_tabu(orc, P.Q, X0, alpha, c, asp, P.state() + I.icd2s_get_tabu(P.st, R, n))
+    P.close()
+
+
 # ----------------------------------------------------------------------------- Tabu keys
 def _compact_shift(n, bound):
     """Shift of the one-reduction Tabu keys: the index field holds n itself

@@ -218,3 +218,13 @@ def test_run_gauss_seidel_subqubos(L, orc, im_mode, K, m_min, m_max):
     finally:
         I.icd2s_qubo_destroy(q)
     assert not np.array_equal(j["trace"], g["trace"])  # the order matters on this instance
+
+
+def test_run_with_a_move_log_beyond_shared_memory(L, orc):
+    """A whole run (replayed as a CUDA graph) whose Tabu searches keep their
+    move logs in global memory: alpha = 400 n at n = 300."""
+    n = 300
+    Q = make_qubo(n, 0.5, 44)
+    lp = lib_params(I, n, z=2, K=1, m_min=32, m_max=32, m_init=32, alpha=400 * n, c=5, sweeps=16,
+                    T_max=1500.0, mut_mode=0, patience=0, max_iters=2)
+    _compare_runs(orc, Q, lp, 45)
