@@ -178,13 +178,18 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh)
         constexpr int slot = decltype(slot_c)::value;
         // the chosen move: index and value (CK: no candidate is the key ~0,
         // whose index field 2^(sh-1) - 1 >= n; otherwise its index half is ~0)
-        const unsigned jx = CK ? (unsigned)key & (2u * imask + 1u) : (unsigned)key;
+        unsigned jx = CK ? (unsigned)key & (2u * imask + 1u) : (unsigned)key;
+        // Without aspiration at most c - 1 <= n - 1 variables are tabu, so a
+        // move always exists; the clamp only keeps the row read in bounds.
+        if constexpr (!ASP) jx = min(jx, 2u * (unsigned)n - 1u);
         const int i = (int)(jx >> 1);
-        if (i >= n) {  // no move at all: stop, uniformly
-            if (tid == 0) d.flags[2] = 1;
-            alpha = it;
-            stop = true;
-            return;
+        if constexpr (ASP) {
+            if (i >= n) {  // no move at all: stop, uniformly
+                if (tid == 0) d.flags[2] = 1;
+                alpha = it;
+                stop = true;
+                return;
+            }
         }
         const int si2 = (jx & 1u) ? -2 : 2;       // 2 (1 - 2 x_i)
         const int8_t* row = SR ? Q2 + (size_t)jx * ld : Q + (size_t)i * ld;
@@ -219,12 +224,20 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh)
                         fa[w][b] = max(fa[w][b], it) + c;
                     }
             }
-        if (ASP || tid == 0) {  // the objective and best visit: one thread (every thread with aspiration)
+        // the objective, best visit and move log: one thread (the objective in
+        // every thread with aspiration, whose limit needs it)
+        auto objective = [&]() {
             const int gi = CK ? (int)((unsigned)key >> sh) - (int)cbias : (int)(unsigned)(key >> 32) - (int)kKeyBias;
             OV += gi;
             if (OV < OVmin) { OVmin = OV; best_it = it; }
+        };
+        if constexpr (ASP) {
+            objective();
+            if (tid == 0) mlog[it] = (uint16_t)i;
+        } else if (tid == 0) {
+            objective();
+            mlog[it] = (uint16_t)i;
         }
-        if (tid == 0) mlog[it] = (uint16_t)i;  // the move log
         warp_argmin(it + 1, slot, ASP ? asp_limit() : 0u);
         __syncthreads();
         key = block_argmin(slot);
@@ -244,9 +257,9 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh)
     int it = 0;
     for (; it + 1 < alpha; it += 2) {
         move(it, slot_t<1>{});
-        if (stop) break;
+        if (ASP && stop) break;
         move(it + 1, slot_t<0>{});
-        if (stop) break;
+        if (ASP && stop) break;
     }
     if (!stop && it < alpha) move(it, slot_t<1>{});
 
