@@ -412,7 +412,8 @@ typedef struct icd2s_tuning {
                                  test taken for both outcomes, 4 = per sweep either 1 or by
                                  position (2 up to 64 variables, 3 beyond), whichever the
                                  previous sweep's accepts predict cheaper */
-    int32_t reserved[1];
+    int32_t refresh_cluster;  /* tensor-core refresh: 2 = pairs of CTAs share the replica tile
+                                 (TMA multicast), 1 = every CTA loads its own, 0 = default */
 } icd2s_tuning;
 int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t);
 int icd2s_get_tuning(icd2s_state* st, icd2s_tuning* t);
