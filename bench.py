@@ -586,6 +586,61 @@ def run_ttt(args):
     print(json.dumps(line), flush=True)
 
 
+SWEEP_PARAMS = {  # one parameter at a time around the plain method (z = 32, alpha = 5n, c = n/150)
+    "z": (8, 16, 32, 64),
+    "alpha/n": (1, 2, 5, 10),
+    "c*150/n": (0.5, 1, 2, 5),
+}
+
+
+def run_sweep(args):
+    """Time to target of the plain method as z, alpha and c vary (the
+    parameter studies of Section 4 on a synthetic instance)."""
+    import torch
+    from paper_2502_13947_gb300 import icd2s as I
+    if not torch.cuda.is_available():
+        raise SystemExit("the parameter sweep needs a CUDA GPU")
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    spec = TTT_INSTANCES["n5000-d0.5"]
+    n = spec["n"]
+    q = I.icd2s_qubo_create(make_qubo(n, spec["density"], spec["qseed"]))
+    longs = [I.icd2s_run(q, ttt_params(I, n, 1, 64, 64, 0, 10 * args.ttt_budget), s)["best_E"]
+             for s in (100, 101, 102)]
+    E_star = min(longs)
+    results = {}
+    for name, values in SWEEP_PARAMS.items():
+        for v in values:
+            per = []
+            for seed in range(args.ttt_seeds):
+                z = v if name == "z" else 32
+                p = ttt_params(I, n, 1, 64, 64, 0, args.ttt_budget, z=z)
+                if name == "alpha/n":
+                    p.alpha = v * n
+                if name == "c*150/n":
+                    p.c = max(2, int(v * n / 150))
+                p.stop_at_target, p.target_E = 1, E_star
+                st = I.icd2s_state_create(q, p.z, seed)
+                r = I.icd2s_state_run(st, n, p)
+                I.icd2s_state_destroy(st)
+                per.append((r["hit_iter"], r["ttt_ms"], r["device_ms"] / max(r["iters"], 1)))
+            hits = sorted(t for h, t, _ in per if h >= 0)
+            cens = hits + [float("inf")] * (len(per) - len(hits))
+            med = cens[len(cens) // 2] if len(cens) % 2 else 0.5 * (cens[len(cens) // 2 - 1] + cens[len(cens) // 2])
+            results["%s=%s" % (name, v)] = dict(success=len(hits), runs=len(per),
+                                                median_ttt_ms=None if med == float("inf") else round(med, 2),
+                                                iterations=[h for h, _, _ in per],
+                                                mean_ms_per_iter=round(statistics.mean(m for _, _, m in per), 2))
+    I.icd2s_qubo_destroy(q)
+    line = {"metric": "time-to-target energy, parameter sweep", "unit": "ms", "higher_is_better": False,
+            "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "n5000-d0.5 plain method (K=1, m=64, 256 sweeps, T 2000->1, Eq. 5 mutation)",
+                       "defaults": "z=32, alpha=5n, c=n/150", "budget_iters": args.ttt_budget,
+                       "target_E": E_star, "target_runs": longs},
+            "results": results, "wall_s": round(time.time() - t0, 1)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -601,12 +656,15 @@ def main():
     ap.add_argument("--ttt-seeds", type=int, default=10)
     ap.add_argument("--ttt-budget", type=int, default=30, help="outer iterations per measured run")
     ap.add_argument("--ttt-instances", default="n5000-d0.5,n10000-d0.5")
+    ap.add_argument("--sweep", action="store_true", help="time to target as z, alpha and c vary (n = 5000)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.only:
         run_only(args)
     elif args.ttt:
         run_ttt(args)
+    elif args.sweep:
+        run_sweep(args)
     elif args.impl == "reference":
         run_reference(args, w)
     else:

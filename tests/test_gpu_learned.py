@@ -64,15 +64,15 @@ def _net(Wf):
     return m, I.icd2s_mlp_get_weights(m)[1]
 
 
-@pytest.mark.parametrize("mode", [1, 2])
-def test_learned_steps_equal_oracle(L, orc, mode):
+@pytest.mark.parametrize("mode,order", [(1, 0), (2, 0), (1, 1)])
+def test_learned_steps_equal_oracle(L, orc, mode, order):
     """n = 200 (ragged against the 128-wide rows), 6 replicas x 2 uneven
-    subQUBOs: per step the features, scores, hit counts, solutions and
-    energies equal the oracle's."""
+    subQUBOs (merged, or in Gauss-Seidel order): per step the features,
+    scores, hit counts, solutions and energies equal the oracle's."""
     n, seed = 200, 5
     Q = make_qubo(n, 0.4, 77)
     lp = lib_params(I, n, z=6, K=2, m_min=8, m_max=20, m_init=20, alpha=2 * n, c=3, sweeps=32, T_max=400.0,
-                    mut_mode=0, patience=0, max_iters=4, select_mode=mode)
+                    mut_mode=0, patience=0, max_iters=4, select_mode=mode, im_order=order)
     op = orc_params(orc, lp)
     m, Wb = _net(_weights(3))
     steps, _ = _oracle_chain(orc, Q, op, seed, 4, W=Wb)
