@@ -740,7 +740,8 @@ int icd2s_refresh(icd2s_state* st, int32_t rebuild, int32_t* mismatches, void* s
     }
     CK(cudaMemsetAsync(st->rflags, 0, 16, s));
     CK(launch_to_bf16(st->X, false, RL, st->Xb, s));
-    if (st->timing) {
+    CK(cudaMemsetAsync(st->G2, 0, sizeof(int32_t) * RL, s));  // H accumulates split-K partial sums
+    if (st->timing) {  // the events bracket the tensor-core kernel alone
         if (!st->rev[0]) for (cudaEvent_t& e : st->rev) CK(cudaEventCreate(&e));
         CK(cudaEventRecord(st->rev[0], s));
     }

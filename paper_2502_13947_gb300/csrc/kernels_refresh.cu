@@ -390,7 +390,7 @@ cudaError_t launch_mma(const CUtensorMap& tA, const CUtensorMap& tB, int n, int 
 
 }  // namespace
 
-// H[R][ld] (int32, zeroed here) = Q X^T on the tensor cores.  Qb: bf16 [n][ld];
+// H[R][ld] (int32, zeroed by the caller) += Q X^T on the tensor cores.  Qb: bf16 [n][ld];
 // Xb: bf16 [R][ld]; ld a multiple of 128.  err: device flag raised on a
 // timed-out wait.  bn: replicas per tile (128 / 256; 0 picks by R);
 // splits: K splits (0: as many as keep every tile's CTAs in one wave).
@@ -401,8 +401,6 @@ cudaError_t launch_refresh_mma(const void* Qb, const void* Xb, int n, int R, int
     const int BN = bn == 128 || bn == 256 ? bn : (R > 128 ? 256 : 128);
     const int CL = cluster == 2 ? 2 : 1;
     if (!make_map(&tA, Qb, n, ld, kBM) || !make_map(&tB, Xb, R, ld, BN / CL)) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(H, 0, sizeof(int32_t) * (size_t)R * ld, s);
-    if (e != cudaSuccess) return e;
     const int tiles = ((n + kBM - 1) / kBM) * ((R + BN - 1) / BN);
     const int kc_total = ld / kBK;
     if (splits <= 0) splits = device_sm_count() / tiles;  // one CTA per SM, a single wave
