@@ -726,7 +726,10 @@ int icd2s_refresh(icd2s_state* st, int32_t rebuild, int32_t* mismatches, void* s
     icd2s_qubo* q = st->q;
     const int n = q->n, ld = q->ld, R = st->R;
     const size_t RL = (size_t)R * ld;
-    if (!q->Qb) {
+    // operands: a BF16 copy of Q (default: measured faster), or Q as bytes converted
+    // in shared memory (no copy: n * ld * 2 bytes less device memory)
+    const bool bytes = st->tune.refresh_kind == 3;
+    if (!bytes && !q->Qb) {
         CK(cudaStreamSynchronize(s));
         CK(cudaMalloc(&q->Qb, (size_t)n * ld * 2));
         CK(launch_to_bf16(q->Q, true, (size_t)n * ld, q->Qb, s));
@@ -734,6 +737,9 @@ int icd2s_refresh(icd2s_state* st, int32_t rebuild, int32_t* mismatches, void* s
     if (!st->Xb) {
         CK(cudaStreamSynchronize(s));
         CK(cudaMalloc(&st->Xb, RL * 2));
+    }
+    if (!st->G2) {
+        CK(cudaStreamSynchronize(s));
         CK(dalloc(&st->G2, RL));
         CK(dalloc(&st->E2, (size_t)R));
         CK(dalloc(&st->rflags, 4));
@@ -745,8 +751,12 @@ int icd2s_refresh(icd2s_state* st, int32_t rebuild, int32_t* mismatches, void* s
         if (!st->rev[0]) for (cudaEvent_t& e : st->rev) CK(cudaEventCreate(&e));
         CK(cudaEventRecord(st->rev[0], s));
     }
-    CK(launch_refresh_mma(q->Qb, st->Xb, n, R, ld, st->G2, st->rflags, st->tune.refresh_bn,
-                          st->tune.refresh_splits, st->tune.refresh_cluster, s));  // H into G2
+    if (bytes)
+        CK(launch_refresh_i8(q->Q, st->Xb, n, R, ld, st->G2, st->rflags, st->tune.refresh_bn,
+                             st->tune.refresh_splits, s));  // H into G2
+    else
+        CK(launch_refresh_mma(q->Qb, st->Xb, n, R, ld, st->G2, st->rflags, st->tune.refresh_bn,
+                              st->tune.refresh_splits, st->tune.refresh_kind == 2 ? 2 : 1, s));
     if (st->timing) {
         CK(cudaEventRecord(st->rev[1], s));
         st->timed_refresh = true;
@@ -986,8 +996,8 @@ int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t)
         "refresh_bn=%d must be 0, 128 or 256", t->refresh_bn);
     REQ(t->refresh_splits >= 0 && t->refresh_splits <= 256, ICD2S_ERR_ARG, "refresh_splits=%d outside 0..256",
         t->refresh_splits);
-    REQ(t->refresh_cluster >= 0 && t->refresh_cluster <= 2, ICD2S_ERR_ARG, "refresh_cluster=%d outside 0..2",
-        t->refresh_cluster);
+    REQ(t->refresh_kind >= 0 && t->refresh_kind <= 3, ICD2S_ERR_ARG, "refresh_kind=%d outside 0..3",
+        t->refresh_kind);
     REQ(t->anneal_warps_per_cta >= 0 && t->anneal_warps_per_cta <= 4, ICD2S_ERR_ARG,
         "anneal_warps_per_cta=%d outside 0..4", t->anneal_warps_per_cta);
     REQ(t->tabu_wide_keys == 0 || t->tabu_wide_keys == 1, ICD2S_ERR_ARG, "tabu_wide_keys=%d must be 0 or 1",

@@ -172,6 +172,9 @@ cudaError_t launch_to_bf16(const void* src, bool is_signed, size_t count, void* 
 // cluster: 2 = pairs of CTAs share the replica tile through TMA multicast, else 1
 cudaError_t launch_refresh_mma(const void* Qb, const void* Xb, int n, int R, int ld, int32_t* H, int* err, int bn,
                                int splits, int cluster, cudaStream_t s);
+// the same with Q read as int8 bytes and converted to BF16 in shared memory
+cudaError_t launch_refresh_i8(const void* Q8, const void* Xb, int n, int R, int ld, int32_t* H, int* err, int bn,
+                              int splits, cudaStream_t s);
 cudaError_t launch_finish_gains(const int32_t* diag, int n, int ld, const uint8_t* X, int32_t* G, int64_t* E, int R,
                                 cudaStream_t s);
 // learned selection (kernels_mlp.cu)

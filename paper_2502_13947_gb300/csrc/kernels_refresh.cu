@@ -284,6 +284,181 @@ __global__ __launch_bounds__(128, 1) void k_refresh_mma(const __grid_constant__ 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// The same product with Q read as bytes: TMA brings int8 tiles of Q (half the
+// bytes of BF16, and no BF16 copy of Q) beside BF16 tiles of X; four
+// converter warps write the Q tiles as BF16 in the 128-byte-swizzled layout
+// the MMA reads, and the MMA issuer takes them with the X tiles straight from
+// the TMA stage.  Exact as above: every int8 value is a BF16 integer.  Warp 0
+// lane 0 issues the TMA loads into SI stages, warp 1 lane 0 the MMAs from SC
+// converted buffers, warps 2..5 convert and then run the epilogue (warp w
+// reads accumulator lanes 32 (w mod 4) ..).  Every wait is bounded as above.
+// ---------------------------------------------------------------------------
+namespace {
+
+// bf16 of 8 signed bytes (two words): b + 128 placed in the mantissa of 2^23
+// and 2^23 + 128 subtracted gives the exact float b, whose top 16 bits are its bf16
+__device__ __forceinline__ uint4 bf16x8_from_s8(uint2 w)
+{
+    const uint32_t u0 = w.x ^ 0x80808080u, u1 = w.y ^ 0x80808080u;
+    uint32_t h[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        h[k] = __float_as_uint(__uint_as_float(__byte_perm(u0, 0x4B000000u, 0x7540u + k)) - 8388736.0f);
+        h[4 + k] = __float_as_uint(__uint_as_float(__byte_perm(u1, 0x4B000000u, 0x7540u + k)) - 8388736.0f);
+    }
+    return make_uint4(__byte_perm(h[0], h[1], 0x7632u), __byte_perm(h[2], h[3], 0x7632u),
+                      __byte_perm(h[4], h[5], 0x7632u), __byte_perm(h[6], h[7], 0x7632u));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+}  // namespace
+
+template <int BN, int SI, int SC>
+__global__ __launch_bounds__(192, 1) void k_refresh_i8(const __grid_constant__ CUtensorMap tA8,
+                                                      const __grid_constant__ CUtensorMap tB, int n, int R,
+                                                      int kc_total, int kc_per_split, int32_t* __restrict__ H,
+                                                      int ldh, int* err)
+{
+    constexpr uint32_t kA8 = kBM * kBK, kA16 = kBM * kBK * 2, kB16 = BN * kBK * 2;
+    constexpr uint32_t kIdesc = idesc_bf16_f32(kBM, BN);
+    constexpr int kConv = 128;  // converter threads (warps 2..5)
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* tB16 = smem;               // SI x kB16 (TMA stages of X, BF16, swizzled)
+    unsigned char* cA = tB16 + SI * kB16;     // SC x kA16 (converted Q)
+    unsigned char* tA8b = cA + SC * kA16;     // SI x kA8 (TMA stages of Q, bytes)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tA8b + SI * kA8);  // ifull, iempty, cfull, cempty, done
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SI + 2 * SC + 1);
+    const uint32_t ifull0 = smem_u32(bars), iempty0 = ifull0 + 8 * SI, cfull0 = iempty0 + 8 * SI,
+                   cempty0 = cfull0 + 8 * SC, done = cempty0 + 8 * SC;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int kc0 = blockIdx.z * kc_per_split;
+    const int kc1 = min(kc0 + kc_per_split, kc_total);
+    const int nk = kc1 > kc0 ? kc1 - kc0 : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < SI; ++s) {
+            mbar_init(ifull0 + 8 * s, 1);
+            mbar_init(iempty0 + 8 * s, kConv + 1);  // the converters (Q bytes) and the MMAs (X tile)
+        }
+        for (int s = 0; s < SC; ++s) {
+            mbar_init(cfull0 + 8 * s, kConv);
+            mbar_init(cempty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0 && lane == 0 && nk > 0) {
+        // producer: byte tiles of Q[m0 ..][k], BF16 tiles of X[n0 ..][k]
+        int issued = 0;
+        for (int i = 0; i < nk && ok; ++i) {
+            const int s = i % SI, u = i / SI;
+            if (u > 0) ok = mbar_wait(iempty0 + 8 * s, (uint32_t)((u - 1) & 1), err);
+            if (!ok) break;
+            const uint32_t fb = ifull0 + 8 * s;
+            mbar_expect_tx(fb, kA8 + kB16);
+            const int kx = (kc0 + i) * kBK;  // element column, a multiple of 64
+            tma_load_2d(smem_u32(tA8b + s * kA8), &tA8, kx, m0, fb);
+            tma_load_2d(smem_u32(tB16 + s * kB16), &tB, kx, n0, fb);
+            ++issued;
+        }
+        for (int i = issued - SI > 0 ? issued - SI : 0; i < issued; ++i)
+            mbar_wait(ifull0 + 8 * (i % SI), (uint32_t)((i / SI) & 1), err);
+    } else if (warp == 1 && lane == 0 && nk > 0) {
+        // MMA issuer: converted Q from buffer i mod SC (its stage's X tile has landed
+        // before the converters released the buffer), X from TMA stage i mod SI
+        for (int i = 0; i < nk && ok; ++i) {
+            const int sc = i % SC, si = i % SI;
+            ok = mbar_wait(cfull0 + 8 * sc, (uint32_t)((i / SC) & 1), err) &&
+                 mbar_wait(ifull0 + 8 * si, (uint32_t)((i / SI) & 1), err);  // the X tile, observed directly
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a = smem_u32(cA + sc * kA16), b = smem_u32(tB16 + si * kB16);
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk)
+                mma_bf16(tmem, smem_desc_sw128(a + 32 * kk), smem_desc_sw128(b + 32 * kk), kIdesc,
+                         (i > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(cempty0 + 8 * sc);  // the converted buffer ...
+            mma_commit(iempty0 + 8 * si);  // ... and the X tile of the stage are free again
+        }
+        mma_commit(done);
+    } else if (warp >= 2 && nk > 0) {
+        // converters: 8 bytes -> one 16-byte BF16 chunk, stored at its swizzled place
+        // (chunk c of row r at c ^ (r mod 8) within the row's 128 bytes)
+        const int c = threadIdx.x - 64;
+        for (int i = 0; i < nk && ok; ++i) {
+            const int si = i % SI, sc = i % SC, uc = i / SC;
+            ok = mbar_wait(ifull0 + 8 * si, (uint32_t)((i / SI) & 1), err);
+            if (ok && uc > 0) ok = mbar_wait(cempty0 + 8 * sc, (uint32_t)((uc - 1) & 1), err);
+            if (!ok) break;
+            const unsigned char* a8 = tA8b + si * kA8;
+            unsigned char* a16 = cA + sc * kA16;
+#pragma unroll
+            for (int j = 0; j < kBM * 8 / kConv; ++j) {
+                const int q = c + kConv * j, r = q >> 3, cc = q & 7;
+                const uint2 w = *reinterpret_cast<const uint2*>(a8 + r * kBK + cc * 8);
+                *reinterpret_cast<uint4*>(a16 + r * 128 + ((cc ^ (r & 7)) << 4)) = bf16x8_from_s8(w);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+            mbar_arrive(iempty0 + 8 * si);
+            mbar_arrive(cfull0 + 8 * sc);
+        }
+    }
+    __syncwarp();
+
+    // epilogue: warps 2..5; warp w owns accumulator lanes (rows) 32 (w mod 4) ..
+    if (warp >= 2 && nk > 0 && mbar_wait(done, 0u, err)) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int quad = warp & 3;
+        const int row = m0 + quad * 32 + lane;
+        const uint32_t tw = tmem + ((uint32_t)(quad * 32) << 16);
+#pragma unroll 1
+        for (int cb = 0; cb < BN; cb += 16) {
+            uint32_t v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(tw + (uint32_t)cb));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < n) {
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int p = n0 + cb + t;
+                    if (p < R) {
+                        const int h = __float2int_rn(__uint_as_float(v[t]));
+                        if (h != 0) atomicAdd(H + (size_t)p * ldh + row, h);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+}
+
 // int8 Q [n][ld] -> bf16 [n][ld]; uint8 X [R][ld] -> bf16 [R][ld]
 __global__ void k_to_bf16_i8(const int8_t* __restrict__ src, size_t count, __nv_bfloat16_raw* __restrict__ dst)
 {
@@ -354,6 +529,37 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int ld, int box_rows)
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2-D byte tensor [rows][ld], box = 64 columns x box_rows, no swizzle
+bool make_map_u8(CUtensorMap* m, const void* base, int rows, int ld, int box_rows)
+{
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int SI, int SC>
+cudaError_t launch_i8(const CUtensorMap& tA, const CUtensorMap& tB, int n, int R, int ld, int splits, int32_t* H,
+                      int* err, cudaStream_t s)
+{
+    const size_t sm = 1024 + (size_t)SI * (kBM + 2 * BN) * kBK + (size_t)SC * kBM * kBK * 2 +
+                      (2 * SI + 2 * SC + 1) * 8 + 16;
+    auto kern = k_refresh_i8<BN, SI, SC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int kc_total = ld / kBK;
+    const int kcps = (kc_total + splits - 1) / splits;
+    dim3 grid((n + kBM - 1) / kBM, (R + BN - 1) / BN, (kc_total + kcps - 1) / kcps);
+    kern<<<grid, 192, sm, s>>>(tA, tB, n, R, kc_total, kcps, H, ld, err);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
 template <int BN, int STAGES, int CL>
 cudaError_t launch_mma(const CUtensorMap& tA, const CUtensorMap& tB, int n, int R, int ld, int splits, int32_t* H,
                        int* err, cudaStream_t s)
@@ -412,6 +618,23 @@ cudaError_t launch_refresh_mma(const void* Qb, const void* Xb, int n, int R, int
     }
     if (BN == 256) return launch_mma<256, 4, 1>(tA, tB, n, R, ld, splits, H, err, s);
     return launch_mma<128, 6, 1>(tA, tB, n, R, ld, splits, H, err, s);
+}
+
+// H[R][ld] (int32, zeroed by the caller) += Q X^T with Q read as bytes:
+// Q8 int8 [n][ld], Xb bf16 [R][ld]; ld a multiple of 128.
+cudaError_t launch_refresh_i8(const void* Q8, const void* Xb, int n, int R, int ld, int32_t* H, int* err, int bn,
+                              int splits, cudaStream_t s)
+{
+    CUtensorMap tA, tB;
+    const int BN = bn == 128 || bn == 256 ? bn : (R > 128 ? 256 : 128);
+    if (!make_map_u8(&tA, Q8, n, ld, kBM) || !make_map(&tB, Xb, R, ld, BN)) return cudaErrorInvalidValue;
+    const int tiles = ((n + kBM - 1) / kBM) * ((R + BN - 1) / BN);
+    const int kc_total = ld / kBK;
+    if (splits <= 0) splits = device_sm_count() / tiles;
+    if (splits < 1) splits = 1;
+    if (splits > kc_total) splits = kc_total;
+    if (BN == 256) return launch_i8<256, 4, 3>(tA, tB, n, R, ld, splits, H, err, s);
+    return launch_i8<128, 6, 3>(tA, tB, n, R, ld, splits, H, err, s);
 }
 
 // Counts entries where two gain/energy sets differ (the drift check).

@@ -465,21 +465,21 @@ def icd2s_apply_flips_static(Q_dev: int, n: int, ld: int, replicas: int, flips_d
 class Tuning(C.Structure):
     _fields_ = [("tabu_variant", C.c_int32), ("anneal_warps_per_cta", C.c_int32), ("refresh_bn", C.c_int32),
                 ("refresh_splits", C.c_int32), ("tabu_wide_keys", C.c_int32),
-                ("tabu_rows", C.c_int32), ("anneal_scheme", C.c_int32), ("refresh_cluster", C.c_int32)]
+                ("tabu_rows", C.c_int32), ("anneal_scheme", C.c_int32), ("refresh_kind", C.c_int32)]
 
 
 def _tuning_dict(t):
     return dict(tabu_variant=t.tabu_variant, anneal_warps_per_cta=t.anneal_warps_per_cta,
                 refresh_bn=t.refresh_bn, refresh_splits=t.refresh_splits, tabu_wide_keys=t.tabu_wide_keys,
-                tabu_rows=t.tabu_rows, anneal_scheme=t.anneal_scheme, refresh_cluster=t.refresh_cluster)
+                tabu_rows=t.tabu_rows, anneal_scheme=t.anneal_scheme, refresh_kind=t.refresh_kind)
 
 
 def icd2s_set_tuning(st, tabu_variant: int = -1, anneal_warps_per_cta: int = 0, refresh_bn: int = 0,
                      refresh_splits: int = 0, tabu_wide_keys: int = 0, tabu_rows: int = 0,
-                     anneal_scheme: int = 0, refresh_cluster: int = 0) -> None:
+                     anneal_scheme: int = 0, refresh_kind: int = 0) -> None:
     t = Tuning(tabu_variant=tabu_variant, anneal_warps_per_cta=anneal_warps_per_cta, refresh_bn=refresh_bn,
                refresh_splits=refresh_splits, tabu_wide_keys=tabu_wide_keys, tabu_rows=tabu_rows,
-               anneal_scheme=anneal_scheme, refresh_cluster=refresh_cluster)
+               anneal_scheme=anneal_scheme, refresh_kind=refresh_kind)
     _check(lib().icd2s_set_tuning(st, C.byref(t)))
 
 

@@ -21,19 +21,20 @@ def L():
     return I.lib()
 
 
-@pytest.mark.parametrize("cluster", [1, 2])
+@pytest.mark.parametrize("kind", [1, 2, 3])
 @pytest.mark.parametrize("n,R,density", [(1, 1, 1.0), (64, 8, 1.0), (200, 16, 0.5), (300, 5, 0.3),
                                          (1000, 33, 1.0), (2500, 130, 0.1), (4097, 3, 1.0)])
-def test_refresh_equals_the_definition(L, orc, n, R, density, cluster):
-    """Both tile schedules: every CTA loading its own replica tile, and pairs
-    of CTAs sharing it through TMA multicast (an odd row-tile count leaves a
-    CTA of zero rows)."""
+def test_refresh_equals_the_definition(L, orc, n, R, density, kind):
+    """Every operand path: BF16 copies with every CTA loading its own replica
+    tile, BF16 copies with pairs of CTAs sharing it through TMA multicast (an
+    odd row-tile count leaves a CTA of zero rows), and bytes converted to
+    BF16 in shared memory."""
     Q = make_qubo(n, density, n + R)
     X = random_solutions(n, R, 4)
     q = I.icd2s_qubo_create(Q)
     st = I.icd2s_state_create(q, R, 1)
     try:
-        I.icd2s_set_tuning(st, refresh_cluster=cluster)
+        I.icd2s_set_tuning(st, refresh_kind=kind)
         I.icd2s_state_load(st, X)
         assert I.icd2s_refresh(st) == 0          # tracked (dp4a recompute) == tensor-core recompute
         assert I.icd2s_refresh(st, rebuild=True) == 0
@@ -60,10 +61,10 @@ def test_refresh_after_steps_dense_n7000_R256(L, orc):
     try:
         for t in range(2):
             I.icd2s_step(st, lp, t)
-        for cluster in (1, 2):
+        for kind in (1, 2, 3):
             for bn, splits in ((256, 0), (128, 1), (256, 3)):
-                I.icd2s_set_tuning(st, refresh_bn=bn, refresh_splits=splits, refresh_cluster=cluster)
-                assert I.icd2s_refresh(st) == 0, (cluster, bn, splits)
+                I.icd2s_set_tuning(st, refresh_bn=bn, refresh_splits=splits, refresh_kind=kind)
+                assert I.icd2s_refresh(st) == 0, (kind, bn, splits)
         x, g, E = I.icd2s_get_state(st, R, n)
     finally:
         I.icd2s_state_destroy(st)
