@@ -199,13 +199,16 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh)
             const int j0 = 4 * (tid + w * NT);
             rv[w] = j0 < ld ? __ldg(reinterpret_cast<const int*>(row + j0)) : 0;
         }
+        // + 2 (1 - 2 x_i) Q_ij: one dp4a per variable with the byte 2 (1 - 2 x_i)
+        // in the variable's lane (the masks depend on the move only, so they are
+        // warp-uniform; signed rows already carry the sign)
+        unsigned msk[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) msk[b] = (SR || !(jx & 1u) ? 0x02u : 0xFEu) << (8 * b);
 #pragma unroll
         for (int w = 0; w < W; ++w)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                if constexpr (SR) gf[w][b] = __dp4a(rv[w], 2 << (8 * b), gf[w][b]);  // + 2 (1 - 2 x_i) Q_ij
-                else gf[w][b] += (int)(int8_t)(rv[w] >> (8 * b)) * si2;
-            }
+            for (int b = 0; b < 4; ++b) gf[w][b] = __dp4a(rv[w], (int)msk[b], gf[w][b]);
         // the moved variable keeps its folded gain, flips, and becomes tabu
         const int rel = (i >> 2) - tid;  // the owner has rel = w NT for its group w
         const int bi = i & 3;
