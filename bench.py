@@ -479,6 +479,8 @@ TTT_METHODS = {  # (K, m_min, m_max, select_mode, ablation, im_order, alpha / n)
     "learned": (1, 64, 64, 1, 0, 0, 5),
     "learned+batched": (16, 32, 256, 1, 0, 0, 5),
     "hybrid+batched": (16, 32, 256, 2, 0, 0, 5),
+    "batched K=4": (4, 32, 256, 0, 0, 0, 5),           # fewer subQUBOs per solution: a larger mutation
+    "learned+batched K=4": (4, 32, 256, 1, 0, 0, 5),
     "batched GS": (16, 32, 256, 0, 0, 1, 5),          # Gauss-Seidel order of the 16 subQUBOs
     "learned+batched GS": (16, 32, 256, 1, 0, 1, 5),
     "No_IM": (1, 64, 64, 0, 1, 0, 5),      # the simplified versions of Section 4
