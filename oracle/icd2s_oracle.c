@@ -774,32 +774,43 @@ int32_t orc_step(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t see
 /* Call_IM_Solution_Set (Algorithm 2): floor(n / m) disjoint blocks of m
  * consecutive variables per solution, each solved with the bias of the
  * current values of the others and written back before the next block
- * (Gauss-Seidel).  E[z] receives the energies. */
+ * (Gauss-Seidel).  With K > 1 Ising machines per solution and the Jacobi
+ * order (im_order 0), K consecutive blocks are solved at once (reading S24:
+ * Section 3 notes that several IMs address several subQUBOs concurrently):
+ * each block of a group is built from the solution before the group, and the
+ * group's results are written back together.  E[z] receives the energies. */
 void orc_initial_pass(const int8_t* Q, int32_t n, const orc_params* prm, uint64_t seed, uint8_t* S, int64_t* E)
 {
     const int32_t m = prm->m_init;
+    const int32_t G = (prm->K > 1 && prm->im_order == 0) ? prm->K : 1;  /* blocks solved at once */
     int32_t* Qs = (int32_t*)malloc(sizeof(int32_t) * (size_t)m * m);
     uint8_t* xs = (uint8_t*)malloc((size_t)m);
     int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)m);
+    uint8_t* pre = (uint8_t*)malloc((size_t)n);
     uint32_t* beta = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(prm->sweeps > 0 ? prm->sweeps : 1));
     uint32_t nlog[4096];
     orc_beta_table(prm->sweeps, prm->T_max, prm->T_min, beta);
     orc_nlog_table(nlog);
+    const int32_t nb = prm->ablation == 1 ? 0 : n / m;  /* No_IM: no IM call at all */
     for (int32_t p = 0; p < prm->z; ++p) {
         uint8_t* x = S + (int64_t)p * n;
-        for (int32_t l = 0; l < (prm->ablation == 1 ? 0 : n / m); ++l) {  /* No_IM: no IM call at all */
-            for (int32_t a = 0; a < m; ++a) idx[a] = l * m + a;
-            orc_subqubo(Q, n, x, idx, m, Qs, NULL);
-            for (int32_t a = 0; a < m; ++a) xs[a] = x[idx[a]];
-            if (prm->im_mode == 1)
-                orc_exact_subqubo(Qs, m, xs);
-            else
-                orc_anneal(Qs, m, xs, prm->sweeps, beta, nlog, seed, (uint32_t)p, 0x80000000u | (uint32_t)l, NULL);
-            for (int32_t a = 0; a < m; ++a) x[idx[a]] = xs[a];
+        for (int32_t l0 = 0; l0 < nb; l0 += G) {
+            memcpy(pre, x, (size_t)n);  /* the solution before the group */
+            for (int32_t l = l0; l < l0 + G && l < nb; ++l) {
+                for (int32_t a = 0; a < m; ++a) idx[a] = l * m + a;
+                orc_subqubo(Q, n, pre, idx, m, Qs, NULL);
+                for (int32_t a = 0; a < m; ++a) xs[a] = pre[idx[a]];
+                if (prm->im_mode == 1)
+                    orc_exact_subqubo(Qs, m, xs);
+                else
+                    orc_anneal(Qs, m, xs, prm->sweeps, beta, nlog, seed, (uint32_t)p, 0x80000000u | (uint32_t)l,
+                               NULL);
+                for (int32_t a = 0; a < m; ++a) x[idx[a]] = xs[a];
+            }
         }
         E[p] = orc_energy(Q, n, x);
     }
-    free(Qs); free(xs); free(idx); free(beta);
+    free(Qs); free(xs); free(idx); free(pre); free(beta);
 }
 
 /* Runs Algorithm 2 from Generate_Initial_Solution_Set.  Outputs: best_x[n],

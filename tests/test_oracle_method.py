@@ -619,3 +619,42 @@ def test_gauss_seidel_order_of_the_subqubos(orc):
     a = orc.step(Q, prm, seed, t, S)["S"]
     prm.im_order = 1
     assert np.array_equal(orc.step(Q, prm, seed, t, S)["S"], a)
+
+
+def _initial_pass_by_pieces(orc, Q, prm, seed, S, G):
+    """Call_IM_Solution_Set rebuilt from the pinned pieces: blocks of m_init
+    consecutive variables, G at a time, each built from the solution before
+    its group (G = 1: before the block itself)."""
+    n, m = Q.shape[0], prm.m_init
+    nb = n // m
+    beta, nlog = orc.beta_table(prm.sweeps, prm.T_max, prm.T_min), orc.nlog_table()
+    out = S.copy()
+    for p in range(prm.z):
+        x = out[p]
+        for l0 in range(0, nb, G):
+            pre = x.copy()
+            for l in range(l0, min(l0 + G, nb)):
+                grp = np.arange(l * m, (l + 1) * m, dtype=np.int32)
+                Qs, _ = orc.subqubo(Q, pre, grp)
+                xs, _, _ = orc.anneal(Qs, pre[grp], beta, nlog, seed, p, 0x80000000 | l)
+                x[grp] = xs
+    return out
+
+
+def test_initial_pass_with_several_ising_machines(orc):
+    """K > 1 IMs per solution (Jacobi order): Call_IM_Solution_Set solves K
+    consecutive blocks at once, each from the solution before the group
+    (reading S24); K = 1, or the Gauss-Seidel order, keeps one block at a
+    time.  Both equal the pass rebuilt from its pieces, and they differ."""
+    n, z, seed = 70, 3, 41
+    Q = make_qubo(n, 0.6, 43)
+    S = random_solutions(n, z, 44)
+    prm = orc.default_params(n, z=z, K=3, m_min=4, m_max=8, m_init=8, sweeps=20, T_max=150.0)
+    grouped, _ = orc.initial_pass(Q, prm, seed, S)
+    assert np.array_equal(grouped, _initial_pass_by_pieces(orc, Q, prm, seed, S, 3))
+    prm.im_order = 1
+    seq, _ = orc.initial_pass(Q, prm, seed, S)
+    assert np.array_equal(seq, _initial_pass_by_pieces(orc, Q, prm, seed, S, 1))
+    prm.im_order, prm.K = 0, 1
+    assert np.array_equal(orc.initial_pass(Q, prm, seed, S)[0], seq)
+    assert not np.array_equal(grouped, seq)
