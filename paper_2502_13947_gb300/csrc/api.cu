@@ -792,9 +792,15 @@ int icd2s_initial_pass(icd2s_state* st, const icd2s_params* p, void* stream)
     cudaStream_t s = S(stream);
     const int m = p->m_init > 0 ? p->m_init : p->m_max;
     if (p->ablation == 1) return ICD2S_OK;  // No_IM: no Ising-machine call at all
-    for (int l = 0; l < st->q->n / m; ++l) {
-        rc = anneal_impl(st, nullptr, nullptr, st->R, 1, m, m, l * m, p->sweeps, p->T_max, p->T_min,
-                         0x80000000u | (uint32_t)l, nullptr, 0, nullptr, s, false, nullptr, p->im_mode);
+    // one block at a time (Gauss-Seidel); with K Ising machines per solution and the
+    // Jacobi order, K consecutive blocks at once, each from the solution before the
+    // group (reading S24)
+    const int nb = st->q->n / m;
+    const int G = (p->K > 1 && p->im_order == 0) ? p->K : 1;
+    for (int l0 = 0; l0 < nb; l0 += G) {
+        const int g = nb - l0 < G ? nb - l0 : G;
+        rc = anneal_impl(st, nullptr, nullptr, st->R * g, g, m, m, l0 * m, p->sweeps, p->T_max, p->T_min,
+                         0x80000000u | (uint32_t)l0, nullptr, 0, nullptr, s, false, nullptr, p->im_mode);
         if (rc) return rc;
         CK(launch_apply(st->d, s));
     }

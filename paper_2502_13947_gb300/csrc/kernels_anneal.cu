@@ -77,17 +77,26 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
 {
     using Seg = typename RowSeg<P>::T;
     constexpr int MC = 32 * P;  // row length (bytes) of the staged Q'
-    const uint32_t iter = a.iter_dev ? (uint32_t)*a.iter_dev : a.iter;
+    uint32_t iter = a.iter_dev ? (uint32_t)*a.iter_dev : a.iter;
 
     const int p = s / a.per_replica;
     const int* S = nullptr;
     int m;
+    int bbase = a.block_base;
+    uint32_t slot = a.slot_base + (uint32_t)s;
     if (a.idx) {
         const int b0 = a.off[s];
         m = a.off[s + 1] - b0;
         S = a.idx + b0;
     } else {
+        // contiguous blocks: block k = s mod per_replica of the launch's group for
+        // replica p starts k blocks after block_base and counts as iteration iter + k
+        // of Call_IM_Solution_Set; its random stream is the replica's (slot p)
         m = a.block_m;
+        const int k = s - p * a.per_replica;
+        bbase += k * a.block_m;
+        iter += (uint32_t)k;
+        slot = a.slot_base + (uint32_t)p;
     }
     const int ld = d.ld;
 
@@ -97,7 +106,7 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
     for (int q = 0; q < P; ++q) {
         const int b = lane + 32 * q;
         valid[q] = b < m;
-        col[q] = valid[q] ? (S ? __ldg(S + b) : a.block_base + b) : 0;
+        col[q] = valid[q] ? (S ? __ldg(S + b) : bbase + b) : 0;
     }
     // gather Q[S, S] into the permuted layout, diagonal as 0; for P <= 4 also
     // the coupling masks of the owned positions: bit L of nz[q][q2] is set
@@ -111,7 +120,7 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
         for (int q2 = 0; q2 < (kSparse ? P : 1); ++q2) nz[q][q2] = 0u;
 #pragma unroll 4
     for (int r = 0; r < m; ++r) {
-        const int ir = S ? __ldg(S + r) : a.block_base + r;
+        const int ir = S ? __ldg(S + r) : bbase + r;
         const int8_t* row = d.Q + (size_t)ir * ld;
         Seg packed = 0;
 #pragma unroll
@@ -152,7 +161,6 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
         x0 |= (unsigned)xv << q;
         X[q] = __ballot_sync(0xffffffffu, xv != 0);
     }
-    const uint32_t slot = a.slot_base + (uint32_t)s;
     int dE = 0;  // |f_sub| <= m (200 n + 100) + 100 m^2 < 2^30, so the running change fits int32
 
     // acceptance limits of 4 consecutive sweeps: Philox block k4/4 of every owned

@@ -41,15 +41,17 @@ __global__ __launch_bounds__(kExactThreads) void k_exact(Dev d, AnnealArgs a)
     const int p = s / a.per_replica;
     const int* S = nullptr;
     int m;
+    int bbase = a.block_base;
     if (a.idx) {
         const int b0 = a.off[s];
         m = a.off[s + 1] - b0;
         S = a.idx + b0;
     } else {
         m = a.block_m;
+        bbase += (s - p * a.per_replica) * a.block_m;  // block s mod per_replica of the group
     }
     const int ld = d.ld;
-    auto var = [&](int r) { return S ? __ldg(S + r) : a.block_base + r; };
+    auto var = [&](int r) { return S ? __ldg(S + r) : bbase + r; };
 
     // stage Q' with a zero diagonal and zero padding
     for (int e = tid; e < kExactMaxM * kExactRow; e += kExactThreads) {

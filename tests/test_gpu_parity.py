@@ -533,10 +533,16 @@ def test_mutate_before_select_is_an_error(L):
 
 
 # ----------------------------------------------------------------------------- Call_IM_Solution_Set
-@pytest.mark.parametrize("n,z,m", [(64, 8, 16), (300, 3, 40), (1000, 2, 64)])
-def test_initial_pass(L, orc, n, z, m):
+@pytest.mark.parametrize("n,z,m,K,order,im_mode", [(64, 8, 16, 1, 0, 0), (300, 3, 40, 1, 0, 0), (1000, 2, 64, 1, 0, 0),
+                                                   (1000, 3, 64, 4, 0, 0), (1000, 3, 64, 4, 1, 0),
+                                                   (2500, 5, 64, 16, 0, 0), (300, 3, 20, 3, 0, 1)])
+def test_initial_pass(L, orc, n, z, m, K, order, im_mode):
+    """One block at a time, and K blocks at once with K Ising machines per
+    solution (the last group shorter: 15 blocks in groups of 4, 39 in groups
+    of 16), annealed or solved exactly."""
     P = Problem(n, 1.0, 8, R=z, state_seed=5)
-    lp = lib_params(I, n, z=z, m_min=m, m_max=m, m_init=m, sweeps=32, T_max=500.0)
+    lp = lib_params(I, n, z=z, K=K, m_min=m, m_max=m, m_init=m, sweeps=32, T_max=500.0, im_order=order,
+                    im_mode=im_mode)
     I.icd2s_initial_pass(P.st, lp)
     x, g, E = P.state()
     S0 = orc.init_solutions(n, z, 5)
