@@ -271,8 +271,12 @@ int icd2s_best_update(icd2s_state* st, void* stream);
 int icd2s_refresh(icd2s_state* st, int32_t rebuild, int32_t* mismatches, void* stream);
 
 /* Call_IM_Solution_Set (Algorithm 2): for each replica, floor(n / m_init)
- * disjoint blocks of m_init consecutive variables are annealed and written
- * back one after the other (each sees the previous ones' result). */
+ * disjoint blocks of m_init consecutive variables are annealed (or solved
+ * exactly, im_mode 1) and written back one after the other (each sees the
+ * previous ones' result).  With p->K > 1 Ising machines per solution and
+ * p->im_order 0, K consecutive blocks are solved at once, each from the
+ * solution before its group (Section 3: several IMs address several
+ * subQUBOs concurrently). */
 int icd2s_initial_pass(icd2s_state* st, const icd2s_params* p, void* stream);
 
 /* One whole outer iteration t of Algorithm 2 on the device: Tabu, control
