@@ -398,18 +398,18 @@ int icd2s_get_apply_ms(icd2s_state* st, double* ms);
  * 0 = default.  The Tabu search packs a move into one 32-bit key (one
  * reduction per warp and per block) when every gain of the instance fits
  * beside the index: 2 max_j sum_i |Q_ij| + 1 < 2^(30 - b), b = bits of n;
- * tabu_wide_keys = 1 keeps the two-reduction 64-bit keys anyway.  An
- * instance without entries -128 also keeps its rows negated (2 n ld bytes
- * more), so a move can read the row already multiplied by (1 - 2x_i):
- * tabu_rows = 0 uses these signed rows for n > 4096 only, 1 never (the sign
- * is applied per variable), 2 wherever the instance has them. */
+ * tabu_wide_keys = 1 keeps the two-reduction 64-bit keys anyway.  tabu_rows
+ * = 2 makes (once per instance, 2 n ld bytes beside Q) and uses the rows of Q
+ * negated as well, so a move reads its row already multiplied by (1 - 2x_i);
+ * not for instances with entries -128.  0 and 1 apply the sign per variable
+ * (the default: as fast or faster on the measured sizes). */
 typedef struct icd2s_tuning {
     int32_t tabu_variant;
     int32_t anneal_warps_per_cta;
     int32_t refresh_bn;       /* tensor-core refresh: replicas per tile (128 or 256; 0 = default) */
     int32_t refresh_splits;   /* tensor-core refresh: K splits (0 = about one CTA per SM) */
     int32_t tabu_wide_keys;   /* 0 = compact Tabu keys where they apply, 1 = never */
-    int32_t tabu_rows;        /* 0 = default, 1 = plain rows, 2 = signed row pairs */
+    int32_t tabu_rows;        /* 0 = default (plain rows), 1 = plain rows, 2 = signed row pairs */
     int32_t anneal_scheme;    /* sweep of the Ising-machine kernel (every scheme gives the same
                                  trajectory): 0 = default (4), 1 = rounds of decisions, 2 =
                                  position by position, 3 = position by position with the next

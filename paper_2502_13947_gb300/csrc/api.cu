@@ -99,7 +99,8 @@ struct icd2s_qubo {
     int32_t* eta = nullptr;
     int32_t* etahat = nullptr;
     long long gain_bound = 0;  // 2 max_j sum_i |Q_ij|: bounds every gain of every solution
-    int8_t* Q2 = nullptr;      // signed row pairs for the Tabu search (null when Q has -128)
+    int8_t* Q2 = nullptr;      // signed row pairs for the Tabu search (made when a state asks for them)
+    bool has_m128 = false;     // an entry is -128: no signed rows (its negation is not an int8)
     // scratch of icd2s_energy (grown on demand)
     int cap = 0;
     uint8_t* xpad = nullptr;
@@ -350,13 +351,7 @@ int icd2s_qubo_create(const int8_t* Q_host, int32_t n, icd2s_qubo** out)
         mism = nullptr;
         const int bad = got[0];
         q->gain_bound = 2LL * got[1];
-        if (!bad && got[2] == 0) {  // signed row pairs: 2 n ld bytes beside Q
-            if ((e = dalloc(&q->Q2, 2 * (size_t)n * q->ld)) != cudaSuccess)
-                return bail(fail(ICD2S_ERR_OOM, "device allocation failed: %s", cudaGetErrorString(e)));
-            if ((e = launch_signed_rows(q->Q, n, q->ld, q->Q2, 0)) != cudaSuccess ||
-                (e = cudaDeviceSynchronize()) != cudaSuccess)
-                return bail(fail(ICD2S_ERR_CUDA, "qubo_create: %s", cudaGetErrorString(e)));
-        }
+        q->has_m128 = got[2] != 0;
         if (bad) return bail(fail(ICD2S_ERR_ASYMMETRIC, "Q is not symmetric (%d mismatched entries)", bad));
         *out = q;
         return ICD2S_OK;
@@ -407,7 +402,7 @@ int icd2s_energy(icd2s_qubo* q, const uint8_t* x_dev, int32_t count, int64_t* E_
     Dev d{};
     d.Q = q->Q; d.diag = q->diag; d.etahat = q->etahat; d.n = q->n; d.ld = q->ld; d.R = count;
     d.gain_bound = q->gain_bound;
-    d.Q2 = q->Q2;
+    d.Q2 = nullptr;  // signed rows only once the state asks for them
     CK(launch_pad_rows(x_dev, q->n, count, q->xpad, q->ld, s));
     CK(launch_recompute(d, q->xpad, q->ld, count, q->hpad, E_dev, s));
     return ICD2S_OK;
@@ -439,7 +434,7 @@ int icd2s_state_create(icd2s_qubo* q, int32_t replicas, uint64_t seed, icd2s_sta
     Dev& d = st->d;
     d.Q = q->Q; d.diag = q->diag; d.etahat = q->etahat; d.n = q->n; d.ld = q->ld; d.R = replicas;
     d.gain_bound = q->gain_bound;
-    d.Q2 = q->Q2;
+    d.Q2 = nullptr;  // signed rows only once the state asks for them
     d.X = st->X; d.G = st->G; d.E = st->E; d.T = st->T; d.C = st->C; d.gamma = st->gamma; d.A = st->A;
     d.delta = st->delta; d.order = st->order; d.sel = st->sel; d.FL = st->FL; d.FCNT = st->FCNT;
     d.DEACC = st->DEACC; d.DONE = st->DONE; d.best_x = st->best_x; d.best_E = st->best_E; d.flags = st->flags;
@@ -529,6 +524,26 @@ int icd2s_get_control(icd2s_state* st, int32_t* A, int32_t* gamma, int32_t* delt
     if (delta)
         CK(cudaMemcpy2D(delta, (size_t)n * 4, st->delta, (size_t)ld * 4, (size_t)n * 4, R, cudaMemcpyDeviceToHost));
     if (gamma) CK(cudaMemcpy(gamma, st->gamma, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    return ICD2S_OK;
+}
+
+// Signed row pairs of the instance (2 n ld bytes beside Q), made the first time
+// a state asks for them; none when Q has an entry -128.  The state's view is
+// updated (a captured step holds the pointer, so gen moves on).
+static int ensure_signed_rows(icd2s_state* st)
+{
+    icd2s_qubo* q = st->q;
+    if (!q->Q2 && !q->has_m128) {
+        CK(cudaDeviceSynchronize());
+        cudaError_t e = dalloc(&q->Q2, 2 * (size_t)q->n * q->ld);
+        REQ(e == cudaSuccess, ICD2S_ERR_OOM, "signed rows: %s", cudaGetErrorString(e));
+        CK(launch_signed_rows(q->Q, q->n, q->ld, q->Q2, 0));
+        CK(cudaDeviceSynchronize());
+    }
+    if (st->d.Q2 != q->Q2) {
+        st->d.Q2 = q->Q2;
+        ++st->gen;
+    }
     return ICD2S_OK;
 }
 
@@ -1009,6 +1024,10 @@ int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t)
     REQ(t->tabu_wide_keys == 0 || t->tabu_wide_keys == 1, ICD2S_ERR_ARG, "tabu_wide_keys=%d must be 0 or 1",
         t->tabu_wide_keys);
     REQ(t->tabu_rows >= 0 && t->tabu_rows <= 2, ICD2S_ERR_ARG, "tabu_rows=%d must be 0, 1 or 2", t->tabu_rows);
+    if (t->tabu_rows == 2) {
+        const int rc = ensure_signed_rows(st);
+        if (rc) return rc;
+    }
     REQ(t->anneal_scheme >= 0 && t->anneal_scheme <= 4, ICD2S_ERR_ARG, "anneal_scheme=%d outside 0..4",
         t->anneal_scheme);
     st->tune = *t;
@@ -1064,7 +1083,7 @@ int icd2s_autotune(icd2s_state* st, const icd2s_params* p, icd2s_tuning* chosen,
     float best_ms = 1e30f;
     for (int v = 0; v < tabu_num_variants(); ++v) {
         if (!tabu_variant_fits(v, n)) continue;
-        for (int rows = 1; rows <= (st->q->Q2 ? 2 : 1); ++rows) {  // plain rows, then signed rows
+        for (int rows = 1; rows <= (st->d.Q2 ? 2 : 1); ++rows) {  // plain rows, then signed rows (if made)
             float vbest = 1e30f;
             for (int rep = 0; rep < 2; ++rep) {
                 if ((rc = restore())) return rc;

@@ -85,7 +85,7 @@ struct Dev {
     int32_t* ACC; unsigned* TT; int apply_splits;     // split write-back: partial sums, tile tickets
     uint32_t k0, k1; // Philox key = seed halves
     long long gain_bound;  // max_j 2 sum_i |Q_ij| >= |g_j| for every x
-    const int8_t* Q2;      // [2n][ld] signed rows: row 2i + x = (1 - 2x) Q_i (null if Q has -128)
+    const int8_t* Q2;      // [2n][ld] signed rows: row 2i + x = (1 - 2x) Q_i (null unless asked for)
     uint16_t* TL; long long tl_cap;  // Tabu move logs [R][tl_cap] for searches whose log exceeds shared memory
 };
 

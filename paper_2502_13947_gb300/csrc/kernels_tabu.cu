@@ -430,17 +430,16 @@ int tabu_key_shift(int n, long long gain_bound)
 
 // variant: index into kTabuVariants; < 0 picks the default.  Compact keys are
 // used when the instance's gain bound allows them, unless wide_keys is set.
-// rows: 0 = signed rows for n > 4096 (where a replica's rows no longer stay in
-// L1: at n = 2500 the two signs of a row halve the L1 hits and cost 8 %, at
-// n = 5000 the one-instruction update gains 5 %), 1 = plain rows, 2 = signed
-// rows; signed rows only where the instance has them.
+// rows: 0 or 1 = plain rows (each variable's update is one dp4a with the move's
+// sign in its byte lane; measured as fast as or faster than signed rows from
+// n = 1000 to 13 001), 2 = signed rows where the state has them.
 cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_t s, bool aspiration, bool wide_keys,
                         int rows)
 {
     if (variant < 0) variant = tabu_default_variant(d.n);
     if (!tabu_variant_fits(variant, d.n)) return cudaErrorInvalidConfiguration;
     const int sh = wide_keys ? 0 : tabu_key_shift(d.n, d.gain_bound);
-    const bool sr = d.Q2 != nullptr && (rows == 2 || (rows == 0 && d.n > 4096));
+    const bool sr = d.Q2 != nullptr && rows == 2;
     // the 1024-thread shapes with 12 and 16 variables per thread would spill the
     // per-variable key constants: they keep the wide keys
     switch (variant) {

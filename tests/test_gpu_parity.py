@@ -226,8 +226,9 @@ def test_tabu_compact_and_wide_keys(L, orc, n, density, variant, asp):
 
 @pytest.mark.parametrize("n,asp", [(300, 0), (300, 1), (2500, 0)])
 def test_tabu_with_entries_of_minus_128(L, orc, n, asp):
-    """-128 has no int8 negation, so such an instance keeps no signed rows:
-    the search still equals the oracle, through the plain rows."""
+    """-128 has no int8 negation, so such an instance makes no signed rows
+    even when asked for them: the search still equals the oracle, through the
+    plain rows."""
     Q = make_qubo(n, 0.3, 50 + n).astype(np.int16)
     rng = np.random.Generator(np.random.PCG64(51))
     for i, j in rng.integers(0, n, size=(25, 2)):
@@ -239,6 +240,7 @@ def test_tabu_with_entries_of_minus_128(L, orc, n, asp):
     assert I.icd2s_qubo_gain_bound(q) == 2 * int(np.abs(Q.astype(np.int64)).sum(axis=0).max())
     X0 = random_solutions(n, R, 52)
     try:
+        I.icd2s_set_tuning(st, tabu_rows=2)
         I.icd2s_state_load(st, X0)
         (I.icd2s_tabu_aspiration if asp else I.icd2s_tabu)(st, alpha, c)
         res = I.icd2s_get_state(st, R, n) + I.icd2s_get_tabu(st, R, n)
