@@ -30,10 +30,10 @@
 // each take their arg-min with a single redux.sync and the key carries x_i.
 // The bound |g_j| <= |Q_jj| + 2 sum_{i != j} |Q_ij| <= 2 sum_i |Q_ij| holds for
 // every x, so it is computed once per instance.
-// Signed rows (SR): when Q has no entry -128 the instance also keeps the
-// rows (1 - 2x) Q_i interleaved, row 2i + x; the move (i, x_i) then reads row
-// 2i + x_i (the key's low bits, no decoding) and each variable's update is
-// one dp4a of the row word with the constant byte 2 in its lane.
+// Each variable's update is one dp4a of the row word with the byte
+// 2 (1 - 2 x_i) in the variable's lane.  Signed rows (SR, on request; not for
+// Q with an entry -128): the rows (1 - 2x) Q_i interleaved, row 2i + x, so the
+// move (i, x_i) reads row 2i + x_i (the key's low bits) and the byte is 2.
 // The objective OV is tracked in int64 by thread 0, which also keeps the
 // move log and publishes the best visit at the end; the toggle counts are
 // counted from the move log after the search.  The move log (uint16 per
