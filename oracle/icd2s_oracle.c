@@ -17,15 +17,15 @@
  * point is in the host tables (cosine temperature schedule, -ln table,
  * mutation-rate schedule), computed in double with the C library.
  *
- * Readings of the paper where it is silent or inconsistent (numbered S1..S23
+ * Readings of the paper where it is silent or inconsistent (numbered S1..S24
  * in the design notes) are marked at the place they apply.
  *
  * Pins (tests/test_oracle_*.py): brute force over all 2^n assignments for
  * small n, the closed-form single-flip energy change, the Ising-form identity
  * (Eq. 2-3), hand-worked control-parameter examples, the closed-form values
  * of the mutation-rate schedule (Eq. 5), the Metropolis acceptance
- * probability of the threshold table, and Philox's first block against an
- * independent generator.  The anneal temperatures (T_max, T_min) have no
+ * probability of the threshold table, and Philox against an independent
+ * generator (counter 0, and counter words 0, 1 and 2 at chosen offsets).  The anneal temperatures (T_max, T_min) have no
  * value in the paper: trajectory equality holds for any value, solution
  * quality at a given value is parity unpinned.
  */

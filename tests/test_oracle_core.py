@@ -53,6 +53,42 @@ def test_philox_first_block_matches_curand_host_generator(orc):
         assert list(mine) == list(out), hex(seed)
 
 
+def _curand_blocks(cr, seed, offset, count):
+    gen = ctypes.c_void_p()
+    assert cr.curandCreateGeneratorHost(ctypes.byref(gen), 161) == 0  # CURAND_RNG_PSEUDO_PHILOX4_32_10
+    try:
+        assert cr.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        assert cr.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(offset)) == 0
+        out = (ctypes.c_uint32 * (4 * count))()
+        assert cr.curandGenerate(gen, out, ctypes.c_size_t(4 * count)) == 0
+    finally:
+        cr.curandDestroyGenerator(gen)
+    return [list(out[4 * b:4 * b + 4]) for b in range(count)]
+
+
+def test_philox_counter_words_0_to_2_match_curand_host_generator(orc):
+    """Counter words 0, 1 and 2 placed as the SC'11 definition places them.
+    cuRAND's host generator (default ordering) emits, as its output block
+    q = s * 65536 + t, the block at counter (s mod 2^32, s div 2^32, t, 0):
+    65536 subsequences in word 2, the position within one in words 0-1.
+    Reading it at offsets 4q therefore pins word 0 over its whole range,
+    word 1 through positions beyond 2^32, and word 2; word 3 is the one slot
+    left, and the next test shows that it changes the block."""
+    cr = _curand()
+    if cr is None:
+        pytest.skip("libcurand not available")
+    for seed in (0x123456789ABCDEF, 7, 0xFFFFFFFFFFFFFFFF):
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        for s, t in ((0, 1), (1, 0), (12345, 40000), (1 << 32, 0), (3 * (1 << 32) + 5, 7),
+                     ((1 << 40) + 0xDEADBEEF, 65535), (0xFFFFFFFF, 65535)):
+            got = _curand_blocks(cr, seed, 4 * (s * 65536 + t), 2)
+            for b in range(2):
+                q = s * 65536 + t + b
+                ss, tt = q // 65536, q % 65536
+                mine = orc.philox([ss & 0xFFFFFFFF, ss >> 32, tt, 0], key)
+                assert list(mine) == got[b], (hex(seed), s, t, b)
+
+
 def test_philox_counter_words_all_matter_and_output_is_uniform(orc):
     base = orc.philox([5, 6, 7, 8], [9, 10])
     for w in range(4):
