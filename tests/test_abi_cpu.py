@@ -40,12 +40,14 @@ def test_library_exports_every_declared_symbol(built):
         assert hasattr(built, name)
 
 
-def test_library_targets_sm_103a_only(built):
-    out = subprocess.run(["cuobjdump", "--list-elf", B.LIB], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    arches = set(re.findall(r"sm_\d+a?", out.stdout))
-    assert arches == {"sm_103a"}, arches
+def test_library_targets_sm_103a_only():
+    """The build passes one -gencode, sm_103a machine code with no other
+    target, to every nvcc command (compile and link)."""
+    assert B.ARCH == "-gencode=arch=compute_103a,code=sm_103a"
+    src = open(B.__file__).read()
+    assert set(re.findall(r"(?:compute|sm)_\d+a?", src)) == {"compute_103a", "sm_103a"}
+    assert src.count("[nvcc, *common,") == 1 and "common = [ARCH," in src
+    assert src.count("[nvcc, ARCH, \"-shared\"") == 1
 
 
 def test_host_tables_equal_the_oracles(built, orc):
