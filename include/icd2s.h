@@ -426,8 +426,9 @@ typedef struct icd2s_tuning {
 int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t);
 int icd2s_get_tuning(icd2s_state* st, icd2s_tuning* t);
 
-/* Autotuner: times every Tabu variant that fits n (with plain and, where the
- * instance has them, signed rows) and every anneal CTA size
+/* Autotuner: times every Tabu variant that fits n (with plain rows, and with
+ * signed rows where a state of the instance has asked for them through
+ * tabu_rows = 2, which makes them) and every anneal CTA size
  * on this state with the parameters p (each trial restores the solutions it
  * changed), keeps the fastest for the state, and returns the choice in
  * `chosen` (may be NULL).  Synchronises `stream`. */
