@@ -30,6 +30,7 @@
 #ifndef ICD2S_H
 #define ICD2S_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -100,7 +101,11 @@ typedef struct icd2s_params {
                               (Jacobi, reading S16); 1 = one after the other, each built from the
                               solution the earlier ones left (Gauss-Seidel, the order Section 3
                               gives Call_IM_Solution_Set) */
-    int32_t reserved[2];
+    int32_t t_start;       /* icd2s_state_run: 0 = a fresh run (Call_IM_Solution_Set, best reset);
+                              t > 0 = resume at outer iteration t on a state restored from a
+                              checkpoint (icd2s_state_restore): no initial pass, the state's best
+                              solution and stale-iteration count carry on; t <= max_iters */
+    int32_t reserved[1];
 } icd2s_params;
 
 /* Per-call anneal parameters (the emulated Ising machine). */
@@ -126,11 +131,12 @@ typedef struct icd2s_mutate_params {
 } icd2s_mutate_params;
 
 typedef struct icd2s_stats {
-    int32_t iters;           /* outer iterations run */
+    int32_t iters;           /* outer iterations completed, counted from iteration 0 (a resumed
+                                run's count includes the iterations before its checkpoint) */
     int64_t best_E;          /* best energy found */
-    int64_t init_best_E;     /* best energy after Call_IM_Solution_Set */
+    int64_t init_best_E;     /* best energy after Call_IM_Solution_Set (resumed: at the resume) */
     int64_t anneal_attempts; /* single-flip attempts made by the emulated Ising machine */
-    int64_t tabu_moves;      /* Tabu iterations summed over solutions */
+    int64_t tabu_moves;      /* Tabu iterations summed over solutions (this call) */
     double device_ms;        /* device time of the loop (CUDA events) */
     double ttt_ms;           /* stop_at_target: device time from the start of the run (initial
                                 pass included) to the end of the iteration that reached the
@@ -192,6 +198,46 @@ int icd2s_get_state(icd2s_state* st, uint8_t* x, int32_t* g, int64_t* E);
 
 /* Best solution seen by icd2s_best_update / icd2s_step (host copies). */
 int icd2s_get_best(icd2s_state* st, uint8_t* x_best, int64_t* E_best);
+
+/* --- Checkpoint and resume (no counterpart in the paper) ---------------------
+ * A checkpoint holds what the later outer iterations read from a state: the
+ * solutions (gains and energies are recomputed from them on restore), the
+ * best solution and energy, the count of iterations without a new best, the
+ * selection hit counts of the learned selection, the Philox seed and the next
+ * iteration number t_next.  Every random number of iteration t is Philox of
+ * (seed, t, slot, tag), so a state restored from a checkpoint taken after
+ * iteration t_next - 1 and stepped from t_next on (icd2s_step, or
+ * icd2s_state_run with t_start = t_next) gives the uninterrupted run's
+ * solutions bit for bit.  Not included: the tuning (results do not depend on
+ * it), the improvement log (a resumed run starts a new one) and the attached
+ * network (icd2s_mlp_get_weights / icd2s_mlp_set_weights).
+ *
+ * Format (byte offsets, little-endian): 0 magic "ICD2SCKP"; 8 uint32 version
+ * 1; 12 int32 n; 16 int32 replicas; 20 int32 t_next; 24 uint64 seed; 32 int64
+ * best energy; 40 int32 stale iterations; 44 uint32 0; 48 uint64 payload bytes
+ * P = 5 replicas n + n; 56 uint64 0; 64 payload: x [replicas][n] uint8, best x
+ * [n] uint8, hit counts [replicas][n] int32; 64 + P: uint64 FNV-1a (64-bit) of
+ * bytes 0 .. 64 + P - 1.  Total 72 + P bytes. */
+
+/* Writes the checkpoint of `st` into buf[cap] (host memory) and its size to
+ * *bytes (may be NULL).  buf == NULL: only the size.  ICD2S_ERR_RANGE if cap
+ * is too small; ICD2S_ERR_ARG if t_next < 0.  Synchronises the device. */
+int icd2s_state_save(icd2s_state* st, int32_t t_next, void* buf, size_t cap, size_t* bytes);
+
+/* Checks a checkpoint without a state (host only, no CUDA call) and returns
+ * its n, replicas, t_next and seed (each pointer may be NULL).
+ * ICD2S_ERR_ARG: too short, wrong magic or version, sizes that disagree with
+ * n and replicas, or entries of x that are not 0/1; ICD2S_ERR_INVARIANT: the
+ * checksum differs (a corrupted checkpoint). */
+int icd2s_checkpoint_info(const void* buf, size_t bytes, int32_t* n, int32_t* replicas, int32_t* t_next,
+                          uint64_t* seed);
+
+/* Replaces everything a checkpoint holds in `st` (whose n and replicas must
+ * equal the checkpoint's: ICD2S_ERR_ARG otherwise), including its seed, and
+ * recomputes gains and energies; *t_next (may be NULL) receives the iteration
+ * to continue with.  The checks of icd2s_checkpoint_info come first: a bad
+ * checkpoint leaves the state unchanged.  Synchronises the device. */
+int icd2s_state_restore(icd2s_state* st, const void* buf, size_t bytes, int32_t* t_next);
 
 /* --- The steps of one outer iteration (Algorithm 2) ------------------------ */
 

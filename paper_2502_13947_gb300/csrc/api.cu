@@ -284,6 +284,8 @@ static int check_params(const icd2s_state* st, const icd2s_params* p)
     REQ(p->ablation == 0 || p->select_mode == 0, ICD2S_ERR_ARG, "the ablations use the paper's selection rule");
     REQ(p->aspiration == 0 || p->aspiration == 1, ICD2S_ERR_ARG, "aspiration must be 0 or 1");
     REQ(p->im_order == 0 || p->im_order == 1, ICD2S_ERR_ARG, "im_order must be 0 or 1");
+    REQ(p->t_start >= 0 && p->t_start <= p->max_iters, ICD2S_ERR_ARG, "t_start=%d outside 0..max_iters=%d",
+        p->t_start, p->max_iters);
     return ICD2S_OK;
 }
 
@@ -501,6 +503,154 @@ int icd2s_get_best(icd2s_state* st, uint8_t* x_best, int64_t* E_best)
     CK(cudaDeviceSynchronize());
     if (x_best) CK(cudaMemcpy(x_best, st->best_x, st->q->n, cudaMemcpyDeviceToHost));
     if (E_best) CK(cudaMemcpy(E_best, st->best_E, 8, cudaMemcpyDeviceToHost));
+    return ICD2S_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------- checkpoint and resume
+namespace {
+
+constexpr char kCkMagic[8] = {'I', 'C', 'D', '2', 'S', 'C', 'K', 'P'};
+constexpr uint32_t kCkVersion = 1;
+constexpr size_t kCkHeader = 64;
+
+// FNV-1a, 64-bit (Fowler, Noll, Vo): offset basis 14695981039346656037,
+// prime 1099511628211; per byte, xor then multiply.
+uint64_t fnv1a64(const unsigned char* p, size_t len)
+{
+    uint64_t h = 14695981039346656037ull;
+    for (size_t i = 0; i < len; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+template <class T>
+T get_le(const unsigned char* p)
+{
+    T v;
+    std::memcpy(&v, p, sizeof v);  // both supported hosts (x86-64, aarch64) are little-endian
+    return v;
+}
+
+template <class T>
+void put_le(unsigned char* p, T v) { std::memcpy(p, &v, sizeof v); }
+
+uint64_t ck_payload(int n, int R) { return 5ull * (uint64_t)R * (uint64_t)n + (uint64_t)n; }
+
+struct CkInfo { int32_t n, R, t_next, stale; uint64_t seed; int64_t best_E; };
+
+// Every check of a checkpoint that needs no state; host only.
+int ck_parse(const void* buf, size_t bytes, CkInfo* ci)
+{
+    REQ(buf, ICD2S_ERR_ARG, "checkpoint is NULL");
+    const auto* b = static_cast<const unsigned char*>(buf);
+    REQ(bytes >= kCkHeader + 8, ICD2S_ERR_ARG, "checkpoint of %zu bytes is shorter than its header", bytes);
+    REQ(std::memcmp(b, kCkMagic, 8) == 0, ICD2S_ERR_ARG, "not a checkpoint (magic)");
+    const uint32_t ver = get_le<uint32_t>(b + 8);
+    REQ(ver == kCkVersion, ICD2S_ERR_ARG, "checkpoint version %u (this library reads %u)", ver, kCkVersion);
+    CkInfo c{};
+    c.n = get_le<int32_t>(b + 12); c.R = get_le<int32_t>(b + 16); c.t_next = get_le<int32_t>(b + 20);
+    c.seed = get_le<uint64_t>(b + 24); c.best_E = get_le<int64_t>(b + 32); c.stale = get_le<int32_t>(b + 40);
+    REQ(c.n >= 1 && c.n <= kMaxN && c.R >= 1 && c.R <= kMaxReplicas, ICD2S_ERR_ARG,
+        "checkpoint sizes n=%d replicas=%d outside the library's limits", c.n, c.R);
+    const uint64_t P = ck_payload(c.n, c.R);
+    REQ(get_le<uint64_t>(b + 48) == P && bytes == kCkHeader + P + 8, ICD2S_ERR_ARG,
+        "checkpoint of %zu bytes does not match n=%d, replicas=%d", bytes, c.n, c.R);
+    REQ(get_le<uint32_t>(b + 44) == 0 && get_le<uint64_t>(b + 56) == 0, ICD2S_ERR_ARG,
+        "checkpoint header fields that must be zero are not");
+    REQ(fnv1a64(b, kCkHeader + P) == get_le<uint64_t>(b + kCkHeader + P), ICD2S_ERR_INVARIANT,
+        "checkpoint checksum mismatch (corrupted)");
+    REQ(c.t_next >= 0 && c.stale >= 0, ICD2S_ERR_ARG, "checkpoint t_next=%d stale=%d", c.t_next, c.stale);
+    const unsigned char* x = b + kCkHeader;
+    for (uint64_t k = 0; k < (uint64_t)c.R * c.n + c.n; ++k)
+        REQ(x[k] <= 1, ICD2S_ERR_ARG, "checkpoint solution byte %llu is %u, not 0/1", (unsigned long long)k, x[k]);
+    *ci = c;
+    return ICD2S_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int icd2s_state_save(icd2s_state* st, int32_t t_next, void* buf, size_t cap, size_t* bytes)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    REQ(t_next >= 0, ICD2S_ERR_ARG, "t_next=%d < 0", t_next);
+    const int n = st->q->n, ld = st->q->ld, R = st->R;
+    const uint64_t P = ck_payload(n, R);
+    const size_t total = kCkHeader + (size_t)P + 8;
+    if (bytes) *bytes = total;
+    if (!buf) return ICD2S_OK;
+    REQ(cap >= total, ICD2S_ERR_RANGE, "checkpoint needs %zu bytes, buffer has %zu", total, cap);
+    auto* b = static_cast<unsigned char*>(buf);
+    int64_t bestE = 0;
+    int32_t flags[2] = {0, 0};
+    CK(cudaDeviceSynchronize());
+    unsigned char* x = b + kCkHeader;
+    unsigned char* bx = x + (size_t)R * n;
+    unsigned char* h = bx + n;
+    CK(cudaMemcpy2D(x, n, st->X, ld, n, R, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(bx, st->best_x, n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy2D(h, (size_t)n * 4, st->H, (size_t)ld * 4, (size_t)n * 4, R, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&bestE, st->best_E, 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(flags, st->flags, 8, cudaMemcpyDeviceToHost));
+    std::memcpy(b, kCkMagic, 8);
+    put_le<uint32_t>(b + 8, kCkVersion);
+    put_le<int32_t>(b + 12, n); put_le<int32_t>(b + 16, R); put_le<int32_t>(b + 20, t_next);
+    put_le<uint64_t>(b + 24, st->seed); put_le<int64_t>(b + 32, bestE); put_le<int32_t>(b + 40, flags[1]);
+    put_le<uint32_t>(b + 44, 0u); put_le<uint64_t>(b + 48, P); put_le<uint64_t>(b + 56, 0ull);
+    put_le<uint64_t>(b + kCkHeader + P, fnv1a64(b, kCkHeader + (size_t)P));
+    return ICD2S_OK;
+}
+
+int icd2s_checkpoint_info(const void* buf, size_t bytes, int32_t* n, int32_t* replicas, int32_t* t_next,
+                          uint64_t* seed)
+{
+    CkInfo c{};
+    const int rc = ck_parse(buf, bytes, &c);
+    if (rc) return rc;
+    if (n) *n = c.n;
+    if (replicas) *replicas = c.R;
+    if (t_next) *t_next = c.t_next;
+    if (seed) *seed = c.seed;
+    return ICD2S_OK;
+}
+
+int icd2s_state_restore(icd2s_state* st, const void* buf, size_t bytes, int32_t* t_next)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    CkInfo c{};
+    const int rc = ck_parse(buf, bytes, &c);
+    if (rc) return rc;
+    const int n = st->q->n, ld = st->q->ld, R = st->R;
+    REQ(c.n == n && c.R == R, ICD2S_ERR_ARG, "checkpoint of n=%d, replicas=%d does not fit a state of n=%d, replicas=%d",
+        c.n, c.R, n, R);
+    const auto* x = static_cast<const unsigned char*>(buf) + kCkHeader;
+    const unsigned char* bx = x + (size_t)R * n;
+    const unsigned char* h = bx + n;
+    cudaStream_t s = 0;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(st->scratch, x, (size_t)R * n, cudaMemcpyHostToDevice));
+    CK(launch_pad_rows(st->scratch, n, R, st->X, ld, s));
+    CK(launch_recompute(st->d, st->X, ld, R, st->G, st->E, s));
+    CK(cudaMemset(st->best_x, 0, ld));
+    CK(cudaMemcpy(st->best_x, bx, n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(st->best_E, &c.best_E, 8, cudaMemcpyHostToDevice));
+    // only the stale count carries over: no improvement-log entry is pending
+    const int32_t fl[8] = {0, c.stale, 0, 0, 0, 0, 0, 0};
+    CK(cudaMemcpy(st->flags, fl, sizeof fl, cudaMemcpyHostToDevice));
+    CK(cudaMemset(st->H, 0, (size_t)R * ld * 4));
+    CK(cudaMemcpy2D(st->H, (size_t)ld * 4, h, (size_t)n * 4, (size_t)n * 4, R, cudaMemcpyHostToDevice));
+    st->seed = c.seed;
+    st->d.k0 = (uint32_t)(c.seed & 0xffffffffu);
+    st->d.k1 = (uint32_t)(c.seed >> 32);
+    st->have_features = st->have_scores = false;
+    ++st->gen;  // a captured step holds the old Philox key
+    CK(cudaDeviceSynchronize());
+    if (t_next) *t_next = c.t_next;
     return ICD2S_OK;
 }
 
@@ -1169,6 +1319,8 @@ int icd2s_step_host(icd2s_state* st, const icd2s_params* p, int32_t t, const uin
 // Algorithm 2 on a state: Call_IM_Solution_Set, then outer iterations until
 // max_iters, patience or the target.  Per-iteration host synchronisation only
 // when patience or the target needs this iteration's flags / best energy.
+// t_start > 0 resumes a restored state at that iteration: no initial pass,
+// its best solution and stale count carry on.
 static int run_impl(icd2s_state* st, const icd2s_params* p, uint8_t* x_out, int64_t* E_out, icd2s_stats* stats,
                     int64_t* trace, uint8_t* S_out)
 {
@@ -1187,24 +1339,31 @@ static int run_impl(icd2s_state* st, const icd2s_params* p, uint8_t* x_out, int6
     CK(cudaEventCreate(&guard.e1));
     CK(cudaEventCreate(&guard.eh));
     cudaStream_t s = 0;
-    const int64_t big = INT64_MAX;
-    CK(cudaMemcpyAsync(st->best_E, &big, 8, cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(st->flags, 0, 32, s));
+    const int t0 = p->t_start;
+    if (t0 == 0) {
+        const int64_t big = INT64_MAX;
+        CK(cudaMemcpyAsync(st->best_E, &big, 8, cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(st->flags, 0, 32, s));
+        CK(cudaStreamSynchronize(s));  // the host value must stay alive
+    }
     CK(cudaEventRecord(guard.e0, s));
-    rc = icd2s_initial_pass(st, p, s);
-    if (rc) return rc;
-    CK(launch_best(st->d, nullptr, 0, nullptr, s));
-    CK(cudaMemsetAsync(st->flags, 0, 8, s));
+    if (t0 == 0) {
+        rc = icd2s_initial_pass(st, p, s);
+        if (rc) return rc;
+        CK(launch_best(st->d, nullptr, 0, nullptr, s));
+        CK(cudaMemsetAsync(st->flags, 0, 8, s));
+    }
     if (st->log_cap > 0) CK(cudaMemcpyAsync(st->prev_x, st->best_x, q->ld, cudaMemcpyDeviceToDevice, s));
     int64_t init_best = 0;
+    int32_t flags[2] = {0, 0};  // [1]: iterations without a new best (a resumed run's carries on)
     CK(cudaMemcpyAsync(&init_best, st->best_E, 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));  // init_best is read below (and the host value must stay alive)
-    int t = 0, hit_iter = -1;
+    CK(cudaMemcpyAsync(flags, st->flags, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));  // init_best and flags are read below
+    int t = t0, hit_iter = -1;
     if (p->stop_at_target && init_best <= p->target_E) {
-        hit_iter = 0;
+        hit_iter = t0;
         CK(cudaEventRecord(guard.eh, s));
     }
-    int32_t flags[2] = {0, 0};
     int64_t cur_best = init_best;
     const bool graph = p->use_graph && !trace;
     const bool sync_each = p->patience > 0 || p->stop_at_target;
@@ -1233,7 +1392,11 @@ static int run_impl(icd2s_state* st, const icd2s_params* p, uint8_t* x_out, int6
     CK(cudaMemcpy(&bestE, st->best_E, 8, cudaMemcpyDeviceToHost));
     if (x_out) CK(cudaMemcpy(x_out, st->best_x, q->n, cudaMemcpyDeviceToHost));
     if (E_out) *E_out = bestE;
-    if (trace && t > 0) CK(cudaMemcpy(trace, guard.tr, sizeof(int64_t) * (size_t)t * (3 * R + 1), cudaMemcpyDeviceToHost));
+    if (trace && t > t0) {  // rows t0 .. t - 1 (a resumed run leaves the earlier rows untouched)
+        const size_t row = (size_t)(3 * R + 1);
+        CK(cudaMemcpy(trace + (size_t)t0 * row, guard.tr + (size_t)t0 * row, sizeof(int64_t) * (size_t)(t - t0) * row,
+                      cudaMemcpyDeviceToHost));
+    }
     if (S_out) CK(cudaMemcpy2D(S_out, q->n, st->X, q->ld, q->n, R, cudaMemcpyDeviceToHost));
     if (stats) {
         int64_t att = 0;
@@ -1241,7 +1404,7 @@ static int run_impl(icd2s_state* st, const icd2s_params* p, uint8_t* x_out, int6
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, guard.e0, guard.e1));
         stats->iters = t; stats->best_E = bestE; stats->init_best_E = init_best; stats->anneal_attempts = att;
-        stats->tabu_moves = (int64_t)t * R * p->alpha; stats->device_ms = ms;
+        stats->tabu_moves = (int64_t)(t - t0) * R * p->alpha; stats->device_ms = ms;
         stats->hit_iter = hit_iter;
         stats->ttt_ms = -1.0;
         if (hit_iter >= 0) {
@@ -1259,6 +1422,7 @@ int icd2s_run(icd2s_qubo* q, const icd2s_params* p, uint64_t seed, uint8_t* x_ou
     REQ(q && p, ICD2S_ERR_ARG, "NULL argument");
     REQ(p->z >= 1 && p->z <= kMaxReplicas, ICD2S_ERR_RANGE, "z=%d outside 1..%d", p->z, kMaxReplicas);
     REQ(p->select_mode == 0, ICD2S_ERR_STATE, "learned selection needs a state with a network: icd2s_state_run");
+    REQ(p->t_start == 0, ICD2S_ERR_ARG, "t_start > 0 resumes a restored state: icd2s_state_run");
     icd2s_state* st = nullptr;
     int rc = icd2s_state_create(q, p->z, seed, &st);
     if (rc) return rc;

@@ -35,7 +35,8 @@ EXPORTS = (
     "icd2s_state_run", "icd2s_mlp_create", "icd2s_mlp_destroy", "icd2s_mlp_set_weights", "icd2s_mlp_get_weights",
     "icd2s_mlp_score", "icd2s_mlp_grad", "icd2s_mlp_train", "icd2s_state_set_mlp", "icd2s_get_features",
     "icd2s_get_hits", "icd2s_log_enable", "icd2s_log_info", "icd2s_log_copy", "icd2s_get_apply_ms",
-    "icd2s_exact_subqubos_batch", "icd2s_tabu_aspiration",
+    "icd2s_exact_subqubos_batch", "icd2s_tabu_aspiration", "icd2s_state_save", "icd2s_checkpoint_info",
+    "icd2s_state_restore",
 )
 MLP_PARAMS = 4673
 PHASES = ("tabu", "select", "anneal", "apply_anneal", "mutate", "apply_mutate", "best")
@@ -55,7 +56,7 @@ class Params(C.Structure):
         ("patience", C.c_int32), ("max_iters", C.c_int32), ("use_graph", C.c_int32), ("refresh_every", C.c_int32),
         ("select_mode", C.c_int32), ("stop_at_target", C.c_int32), ("target_E", C.c_int64),
         ("im_mode", C.c_int32), ("ablation", C.c_int32), ("aspiration", C.c_int32), ("im_order", C.c_int32),
-        ("reserved", C.c_int32 * 2),
+        ("t_start", C.c_int32), ("reserved", C.c_int32 * 1),
     ]
 
 
@@ -113,6 +114,9 @@ def lib():
                 "icd2s_state_load": (C.c_int, [vp, vp, i32, vp]),
                 "icd2s_get_state": (C.c_int, [vp, vp, vp, vp]),
                 "icd2s_get_best": (C.c_int, [vp, vp, vp]),
+                "icd2s_state_save": (C.c_int, [vp, i32, vp, C.c_size_t, P(C.c_size_t)]),
+                "icd2s_checkpoint_info": (C.c_int, [vp, C.c_size_t, P(i32), P(i32), P(i32), P(u64)]),
+                "icd2s_state_restore": (C.c_int, [vp, vp, C.c_size_t, P(i32)]),
                 "icd2s_tabu": (C.c_int, [vp, i32, i32, vp]),
                 "icd2s_get_tabu": (C.c_int, [vp, vp, vp]),
                 "icd2s_select_subqubos": (C.c_int, [vp, P(SelectParams), vp, vp, vp]),
@@ -247,6 +251,30 @@ def icd2s_get_best(st, n: int):
     E = np.zeros(1, np.int64)
     _check(lib().icd2s_get_best(st, _np(x), _np(E)))
     return x, int(E[0])
+
+
+def icd2s_state_save(st, t_next: int) -> bytes:
+    """The state's checkpoint (see include/icd2s.h for the format)."""
+    size = C.c_size_t()
+    _check(lib().icd2s_state_save(st, t_next, None, 0, C.byref(size)))
+    buf = C.create_string_buffer(size.value)
+    _check(lib().icd2s_state_save(st, t_next, buf, size.value, C.byref(size)))
+    return buf.raw[:size.value]
+
+
+def icd2s_checkpoint_info(blob: bytes):
+    """(n, replicas, t_next, seed) of a checkpoint; raises on a bad one."""
+    n, R, t = C.c_int32(), C.c_int32(), C.c_int32()
+    seed = C.c_uint64()
+    _check(lib().icd2s_checkpoint_info(blob, len(blob), C.byref(n), C.byref(R), C.byref(t), C.byref(seed)))
+    return n.value, R.value, t.value, seed.value
+
+
+def icd2s_state_restore(st, blob: bytes) -> int:
+    """Restores a checkpoint into st; returns the iteration to continue with."""
+    t = C.c_int32()
+    _check(lib().icd2s_state_restore(st, blob, len(blob), C.byref(t)))
+    return t.value
 
 
 def icd2s_tabu(st, alpha: int, c: int, stream=0) -> None:
