@@ -483,6 +483,14 @@ int icd2s_autotune(icd2s_state* st, const icd2s_params* p, icd2s_tuning* chosen,
 /* Number of kernel launches the library has made in this process. */
 int icd2s_kernel_launches(uint64_t* count);
 
+/* Testing aid for the error paths: after `count` more device allocations of
+ * the library succeed, every later one fails as out of memory (the call that
+ * needed it returns ICD2S_ERR_OOM) until a count < 0 switches the hook off
+ * (the default).  Process-wide.  A handle stays usable after such a failure:
+ * buffers that belong together are made all or none, and a later call makes
+ * what is missing. */
+int icd2s_debug_fail_allocations_after(int32_t count);
+
 /* Flip write-back that allocates nothing.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- code
  * whose device memory is owned and handed out by someone else (a host

@@ -82,13 +82,39 @@ void make_nlog(uint32_t* nlog)
 // Mutation rate of the MRAnnealer, Eq. 5: r_t = 0.3 (1 + cos(pi t / 15)) 0.99^t.
 double mutation_rate(int t) { return 0.3 * (1.0 + std::cos(M_PI * (double)t / 15.0)) * std::pow(0.99, (double)t); }
 
+// Allocations that may still succeed before the forced-failure hook makes the
+// rest fail (icd2s_debug_fail_allocations_after; < 0: off).
+std::atomic<long long> g_alloc_left{-1};
+
+// Every device allocation of the library.  A failed one leaves *p null and no
+// pending runtime error (which a later launch check would otherwise report).
+cudaError_t dmalloc(void** p, size_t bytes)
+{
+    *p = nullptr;
+    for (long long left = g_alloc_left.load(); left >= 0; left = g_alloc_left.load()) {
+        if (left == 0) return cudaErrorMemoryAllocation;
+        if (g_alloc_left.compare_exchange_weak(left, left - 1)) break;
+    }
+    const cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        (void)cudaGetLastError();
+    }
+    return e;
+}
+
 template <class T>
 cudaError_t dalloc(T** p, size_t count)
 {
-    *p = nullptr;
-    if (count == 0) count = 1;
-    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+    void* v = nullptr;
+    const cudaError_t e = dmalloc(&v, (count ? count : 1) * sizeof(T));
+    *p = static_cast<T*>(v);
+    return e;
 }
+
+// Frees every non-null pointer of a group and nulls it.
+template <class... T>
+void free_group(T**... p) { ((*p ? (void)cudaFree(*p) : (void)0, *p = nullptr), ...); }
 
 }  // namespace
 
@@ -685,10 +711,13 @@ static int ensure_signed_rows(icd2s_state* st)
     icd2s_qubo* q = st->q;
     if (!q->Q2 && !q->has_m128) {
         CK(cudaDeviceSynchronize());
-        cudaError_t e = dalloc(&q->Q2, 2 * (size_t)q->n * q->ld);
+        int8_t* q2 = nullptr;
+        cudaError_t e = dalloc(&q2, 2 * (size_t)q->n * q->ld);
         REQ(e == cudaSuccess, ICD2S_ERR_OOM, "signed rows: %s", cudaGetErrorString(e));
-        CK(launch_signed_rows(q->Q, q->n, q->ld, q->Q2, 0));
-        CK(cudaDeviceSynchronize());
+        if ((e = launch_signed_rows(q->Q, q->n, q->ld, q2, 0)) == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) cudaFree(q2);
+        CK(e);
+        q->Q2 = q2;  // only once it holds the rows
     }
     if (st->d.Q2 != q->Q2) {
         st->d.Q2 = q->Q2;
@@ -705,7 +734,12 @@ static int ensure_tabu_log(icd2s_state* st, int alpha, cudaStream_t s)
 {
     if (tabu_log_in_smem(st->q->n, alpha) || st->tlog_cap >= alpha) return ICD2S_OK;
     CK(cudaStreamSynchronize(s));
-    if (st->tlog) { cudaFree(st->tlog); st->tlog = nullptr; st->tlog_cap = 0; }
+    if (st->tlog) {
+        cudaFree(st->tlog);
+        st->tlog = nullptr; st->tlog_cap = 0;
+        st->d.TL = nullptr; st->d.tl_cap = 0;  // no launch may see the freed log
+        ++st->gen;
+    }
     cudaError_t e = dalloc(&st->tlog, (size_t)st->R * (size_t)alpha);
     REQ(e == cudaSuccess, ICD2S_ERR_OOM, "Tabu move log of %lld bytes: %s", 2LL * st->R * alpha, cudaGetErrorString(e));
     st->tlog_cap = alpha;
@@ -896,18 +930,25 @@ int icd2s_refresh(icd2s_state* st, int32_t rebuild, int32_t* mismatches, void* s
     const bool bytes = st->tune.refresh_kind == 3;
     if (!bytes && !q->Qb) {
         CK(cudaStreamSynchronize(s));
-        CK(cudaMalloc(&q->Qb, (size_t)n * ld * 2));
-        CK(launch_to_bf16(q->Q, true, (size_t)n * ld, q->Qb, s));
+        void* qb = nullptr;
+        CK(dmalloc(&qb, (size_t)n * ld * 2));
+        const cudaError_t e = launch_to_bf16(q->Q, true, (size_t)n * ld, qb, s);
+        if (e != cudaSuccess) cudaFree(qb);
+        CK(e);
+        q->Qb = qb;  // only once it holds the converted matrix
     }
     if (!st->Xb) {
         CK(cudaStreamSynchronize(s));
-        CK(cudaMalloc(&st->Xb, RL * 2));
+        CK(dmalloc(&st->Xb, RL * 2));
     }
-    if (!st->G2) {
+    if (!st->G2 || !st->E2 || !st->rflags) {  // all three or none
         CK(cudaStreamSynchronize(s));
-        CK(dalloc(&st->G2, RL));
-        CK(dalloc(&st->E2, (size_t)R));
-        CK(dalloc(&st->rflags, 4));
+        free_group(&st->G2, &st->E2, &st->rflags);
+        cudaError_t e = dalloc(&st->G2, RL);
+        if (e == cudaSuccess) e = dalloc(&st->E2, (size_t)R);
+        if (e == cudaSuccess) e = dalloc(&st->rflags, 4);
+        if (e != cudaSuccess) free_group(&st->G2, &st->E2, &st->rflags);
+        CK(e);
     }
     CK(cudaMemsetAsync(st->rflags, 0, 16, s));
     CK(launch_to_bf16(st->X, false, RL, st->Xb, s));
@@ -976,12 +1017,15 @@ int icd2s_initial_pass(icd2s_state* st, const icd2s_params* p, void* stream)
 // first use; a captured step holds the pointers, so a new buffer bumps gen).
 static int ensure_features(icd2s_state* st, cudaStream_t s)
 {
-    if (st->F) return ICD2S_OK;
+    if (st->F && st->score && st->gmax) return ICD2S_OK;
     const size_t RL = (size_t)st->R * st->q->ld;
     CK(cudaStreamSynchronize(s));
-    CK(dalloc(&st->F, RL * 6));
-    CK(dalloc(&st->score, RL));
-    CK(dalloc(&st->gmax, (size_t)st->R));
+    free_group(&st->F, &st->score, &st->gmax);  // all three or none
+    cudaError_t e = dalloc(&st->F, RL * 6);
+    if (e == cudaSuccess) e = dalloc(&st->score, RL);
+    if (e == cudaSuccess) e = dalloc(&st->gmax, (size_t)st->R);
+    if (e != cudaSuccess) free_group(&st->F, &st->score, &st->gmax);
+    CK(e);
     st->d.F = st->F;
     st->d.score = st->score;
     ++st->gen;
@@ -1286,6 +1330,12 @@ int icd2s_kernel_launches(uint64_t* count)
     return ICD2S_OK;
 }
 
+int icd2s_debug_fail_allocations_after(int32_t count)
+{
+    g_alloc_left.store(count < 0 ? -1 : (long long)count);
+    return ICD2S_OK;
+}
+
 int icd2s_step(icd2s_state* st, const icd2s_params* p, int32_t t, void* stream)
 {
     REQ(st && p, ICD2S_ERR_ARG, "NULL argument");
@@ -1466,7 +1516,7 @@ int icd2s_mlp_create(uint64_t seed, icd2s_mlp** out)
     m->seed = seed;
     cudaError_t e = cudaSuccess;
     if ((e = dalloc(&m->master, kNPar)) != cudaSuccess || (e = dalloc(&m->mom, kNPar)) != cudaSuccess ||
-        (e = dalloc(&m->vel, kNPar)) != cudaSuccess || (e = cudaMalloc(&m->Wb, 2 * kNPar)) != cudaSuccess) {
+        (e = dalloc(&m->vel, kNPar)) != cudaSuccess || (e = dmalloc(&m->Wb, 2 * kNPar)) != cudaSuccess) {
         free_mlp(m);
         return fail(ICD2S_ERR_OOM, "device allocation failed: %s", cudaGetErrorString(e));
     }

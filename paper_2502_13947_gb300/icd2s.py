@@ -36,7 +36,7 @@ EXPORTS = (
     "icd2s_mlp_score", "icd2s_mlp_grad", "icd2s_mlp_train", "icd2s_state_set_mlp", "icd2s_get_features",
     "icd2s_get_hits", "icd2s_log_enable", "icd2s_log_info", "icd2s_log_copy", "icd2s_get_apply_ms",
     "icd2s_exact_subqubos_batch", "icd2s_tabu_aspiration", "icd2s_state_save", "icd2s_checkpoint_info",
-    "icd2s_state_restore",
+    "icd2s_state_restore", "icd2s_debug_fail_allocations_after",
 )
 MLP_PARAMS = 4673
 PHASES = ("tabu", "select", "anneal", "apply_anneal", "mutate", "apply_mutate", "best")
@@ -133,6 +133,7 @@ def lib():
                 "icd2s_set_timing": (C.c_int, [vp, i32]),
                 "icd2s_get_phase_ms": (C.c_int, [vp, vp]),
                 "icd2s_kernel_launches": (C.c_int, [P(u64)]),
+                "icd2s_debug_fail_allocations_after": (C.c_int, [i32]),
                 "icd2s_apply_flips_static": (C.c_int, [vp, i32, i32, i32, vp, vp, vp, vp, vp]),
                 "icd2s_set_tuning": (C.c_int, [vp, vp]),
                 "icd2s_get_tuning": (C.c_int, [vp, vp]),
@@ -275,6 +276,12 @@ def icd2s_state_restore(st, blob: bytes) -> int:
     t = C.c_int32()
     _check(lib().icd2s_state_restore(st, blob, len(blob), C.byref(t)))
     return t.value
+
+
+def icd2s_debug_fail_allocations_after(count: int) -> None:
+    """Testing aid: every device allocation after the next `count` fails
+    (ICD2S_ERR_OOM) until count < 0 switches the hook off."""
+    _check(lib().icd2s_debug_fail_allocations_after(count))
 
 
 def icd2s_tabu(st, alpha: int, c: int, stream=0) -> None:

@@ -80,6 +80,19 @@ def test_argument_errors_are_reported_without_a_gpu(built):
     assert L.icd2s_qubo_destroy(None) == I.OK and L.icd2s_state_destroy(None) == I.OK
 
 
+def test_forced_allocation_failure_is_reported_without_a_gpu(built):
+    """With the allocation hook at 0 the first device allocation of
+    icd2s_qubo_create fails before any CUDA call: ICD2S_ERR_OOM, no handle."""
+    Q = np.zeros((8, 8), np.int8)
+    h = ctypes.c_void_p(1)
+    I.icd2s_debug_fail_allocations_after(0)
+    try:
+        assert built.icd2s_qubo_create(Q.ctypes.data_as(ctypes.c_void_p), 8, ctypes.byref(h)) == I.ERR_OOM
+    finally:
+        I.icd2s_debug_fail_allocations_after(-1)
+    assert not h.value and b"allocation" in built.icd2s_last_error()
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(I, "LIB_PATH", str(tmp_path / "nope.so"))
     monkeypatch.setattr(I, "_lib", None)
