@@ -9,6 +9,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/icd2s.h"
 #include "common.cuh"
 
@@ -187,6 +189,7 @@ struct icd2s_state {
     // phase timing of icd2s_step: events [2 * phase] / [2 * phase + 1]
     bool timing = false, timed_step = false;
     cudaEvent_t ev[2 * ICD2S_PHASES] = {};
+    nvtxRangeId_t nvtx[ICD2S_PHASES] = {};  // the open NVTX range of each phase
     unsigned long long graph_kernels = 0;  // kernels in one replay of the captured step
     // learned selection
     int32_t* H = nullptr;                    // [R][ld] hit counts
@@ -201,9 +204,18 @@ struct icd2s_state {
     int32_t* log_ctl = nullptr;              // {entries, capacity}
 };
 
-// Records the start (which == 0) or end (which == 1) event of a phase.
+// Opens (which == 0) or closes (which == 1) a phase of icd2s_step: an NVTX
+// range named for it (host side; a profiler can filter kernels by it) and,
+// when timing, a CUDA event on the stream.
 static void mark(icd2s_state* st, int phase, int which, cudaStream_t s)
 {
+    static const char* const kPhaseName[ICD2S_PHASES] = {
+        "icd2s.tabu", "icd2s.select", "icd2s.anneal", "icd2s.apply_anneal", "icd2s.mutate", "icd2s.apply_mutate",
+        "icd2s.best"};
+    // start/end ranges (not a push/pop stack): a step that fails between the two
+    // leaves one range open instead of unbalancing every later one
+    if (which == 0) st->nvtx[phase] = nvtxRangeStartA(kPhaseName[phase]);
+    else nvtxRangeEnd(st->nvtx[phase]);
     if (st->timing) cudaEventRecord(st->ev[2 * phase + which], s);
 }
 
