@@ -424,6 +424,35 @@ def test_run_patience_stops_and_is_deterministic(orc):
     assert np.all(tr[-3:] == tr[-4]) if len(tr) >= 4 else True
 
 
+def test_run_is_the_chain_of_its_steps_from_what_a_checkpoint_holds(orc):
+    """Resuming a run needs only the solutions, the best solution and energy,
+    the hit counts, the stale count, the seed and t: Algorithm 2 run whole
+    equals its initial pass followed by single steps that receive exactly
+    those quantities (and the chain stops by patience where the run does)."""
+    n, seed = 90, 11
+    Q = make_qubo(n, 0.6, 21)
+    for patience, iters in ((0, 10), (2, 200)):
+        prm = orc.default_params(n, z=4, K=2, m_min=6, m_max=12, m_init=12, max_iters=iters, patience=patience,
+                                 sweeps=16, T_max=300.0, alpha=n)
+        r = orc.run(Q, prm, seed)
+        S = orc.init_solutions(n, prm.z, seed)
+        S, E = orc.initial_pass(Q, prm, seed, S)
+        b = int(np.argmin(E))
+        best_E, best_x = int(E[b]), S[b].copy()
+        assert best_E == r["init_best_E"]
+        H = np.zeros((prm.z, n), np.int32)
+        stale, rows, t = 0, [], 0
+        while t < iters and (patience <= 0 or stale < patience):
+            st = orc.step(Q, prm, seed, t, S, best_E, best_x, H=H)
+            stale = 0 if st["best_E"] < best_E else stale + 1
+            S, best_E, best_x, H = st["S"], st["best_E"], st["best_x"], st["H"]
+            rows.append(np.concatenate([st["trace3"], [best_E]]))
+            t += 1
+        assert t == r["iters"] and (patience == 0 or t < iters)
+        assert np.array_equal(np.stack(rows), r["trace"])
+        assert np.array_equal(S, r["S"]) and best_E == r["best_E"] and np.array_equal(best_x, r["best_x"])
+
+
 def test_run_batched_uneven_subqubos(orc):
     n = 200
     Q = make_qubo(n, 0.5, 4)
