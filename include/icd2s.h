@@ -19,7 +19,7 @@
  *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
  *    default stream.  Calls that return host data synchronise that stream.
  *  - Handles are not thread-safe: one thread at a time per handle.
- *  - All energies are exact int64; gains are exact int32 (|g| <= 200 n + 100).
+ *  - All energies are exact int64; gains are exact int32 (|g| <= 128 + 256 (n - 1)).
  *  - Limits: 1 <= n <= 16384, entries of Q are int8, 1 <= replicas <= 4096,
  *    subQUBO size 1..256, sweeps 1..16384.  Violations return ICD2S_ERR_RANGE /
  *    ICD2S_ERR_ARG.

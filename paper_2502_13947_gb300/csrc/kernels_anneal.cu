@@ -161,7 +161,7 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
         x0 |= (unsigned)xv << q;
         X[q] = __ballot_sync(0xffffffffu, xv != 0);
     }
-    int dE = 0;  // |f_sub| <= m (200 n + 100) + 100 m^2 < 2^30, so the running change fits int32
+    int dE = 0;  // |f_sub| <= 256 m n - 128 m^2 < 2^30 (int8 Q), so the running change fits int32
 
     // acceptance limits of 4 consecutive sweeps: Philox block k4/4 of every owned
     // position, looked up in the schedule's table (issued one block ahead, so

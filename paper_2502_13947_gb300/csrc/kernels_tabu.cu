@@ -51,7 +51,7 @@ namespace icd2s {
 
 namespace {
 
-constexpr unsigned kKeyBias = 1u << 26;  // |g| <= 200 n + 100 < 2^22, so g + bias < 2^27
+constexpr unsigned kKeyBias = 1u << 26;  // |g| <= 128 + 256 (n - 1) < 2^22, so g + bias < 2^27
 constexpr int kKeyShift = 5;             // local index 4 w + b < 32 (W <= 8); (g + bias) << 5 < 2^32
 
 __device__ __forceinline__ unsigned long long pack_key(unsigned hi, unsigned lo)
