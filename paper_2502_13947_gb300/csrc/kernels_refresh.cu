@@ -7,9 +7,9 @@
 // drift (and to rebuild them).
 //
 // tcgen05 (5th-generation tensor cores) with BF16 operands and FP32
-// accumulators in tensor memory.  Exact: |Q_ij| <= 100 and x in {0, 1} are
+// accumulators in tensor memory.  Exact: |Q_ij| <= 128 and x in {0, 1} are
 // BF16 integers, every product is exact, and every partial sum is an integer
-// of magnitude <= 100 n < 2^24, which FP32 represents exactly whatever the
+// of magnitude <= 128 n <= 2^21 < 2^24, which FP32 represents exactly whatever the
 // summation order.  (The int8 MMA kind is not available for sm_103a.)
 //
 // Tiles: 128 rows of Q (M) x BN replicas (N), K in chunks of 64 (128 bytes,
