@@ -24,7 +24,8 @@
 // L1-resident load and one compare.  Each lane draws one Philox block per
 // owned position every 4 sweeps, so no random words are wasted or exchanged.
 //
-// A sweep runs as rounds.  In a round every lane tests its unvisited
+// Rounds (one form of a sweep; the others are at anneal_one, whose per-sweep
+// choice picks between them).  In a round every lane tests its unvisited
 // positions against the current gains (P ballots).  For m <= 128 the warp
 // also knows which positions are coupled (Q'_ab != 0; one bit mask per owned
 // position, built from ballots during the gather): a tentative decision is
