@@ -372,6 +372,9 @@ def icd2s_run(q, p: Params, seed: int, trace: bool = False, want_S: bool = False
 
 
 def icd2s_state_run(state, n: int, p: Params, trace: bool = False, want_S: bool = False):
+    """Algorithm 2 on an existing state (see icd2s_run for the outputs).  With
+    p.t_start > 0 (a state restored from a checkpoint) the run continues at
+    that iteration and the trace rows before it are left zero."""
     x = np.zeros(n, np.uint8)
     E = np.zeros(1, np.int64)
     st = Stats()
