@@ -363,9 +363,9 @@ void orc_subqubo_sizes(int32_t K, int32_t m_min, int32_t m_max, uint64_t seed, u
 }
 
 /* ------------------------------------------------------------------------ */
-/* Eq. 4 / Algorithm 4: the subQUBO Q' of the variables S (m of them) with  */
-/* them) with the boundary bias b_i = sum_{j not in S} 2 Q_ij x_j added on   */
-/* bias on its diagonal.  The pair sum of Eq. 4 is read over i != j (S8).    */
+/* Eq. 4 / Algorithm 4: the subQUBO Q' of the variables S (m of them), with */
+/* the boundary bias b_i = sum_{j not in S} 2 Q_ij x_j added on its          */
+/* diagonal.  The pair sum of Eq. 4 is read over i != j (S8).                */
 /* Qs is m x m int32; b (optional) receives the bias.                       */
 /* ------------------------------------------------------------------------ */
 void orc_subqubo(const int8_t* Q, int32_t n, const uint8_t* x, const int32_t* S, int32_t m,

@@ -27,7 +27,12 @@ TAG_INIT, TAG_ANNEAL, TAG_MUT, TAG_SIZE = 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library (idempotent)."""
+    """Compile the oracle shared library (idempotent).  ICD2S_ORACLE_LIB, when
+    set, names an already built library to load instead: the planted-mistake
+    test points the oracle's pins at mutated builds this way."""
+    override = os.environ.get("ICD2S_ORACLE_LIB")
+    if override:
+        return override
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):

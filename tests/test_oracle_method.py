@@ -94,6 +94,19 @@ def test_tabu_single_iteration_takes_the_best_move(orc):
             assert np.array_equal(x, x0) and E == E0
 
 
+def test_tabu_ties_go_to_the_lowest_index(orc):
+    """Reading S6: among equal move values the lowest index moves.  With Q
+    diagonal and all Q_ii equal every free variable has the same gain, so the
+    search moves 0, 1, 2, ... in turn (each stays tabu with c = n) and every
+    move lowers the energy: x_min holds ones at the first alpha indices."""
+    n = 7
+    Q = np.diag([-5] * n).astype(np.int8)
+    for alpha in range(1, n + 1):
+        x, E, T, C = orc.tabu(Q, np.zeros(n, np.uint8), alpha, n)
+        assert x.tolist() == [1] * alpha + [0] * (n - alpha), alpha
+        assert E == -5 * alpha and T.tolist() == x.tolist()
+
+
 def test_tabu_long_tenure_never_repeats_and_never_worsens(orc):
     Q = make_qubo(60, 0.3, 2)
     x0 = random_solutions(60, 1, 2)[0]
