@@ -4,9 +4,12 @@ index, constant or comparison, an off-by-one -- builds it, and runs the
 oracle's pin tests (test_oracle_core, test_oracle_method,
 test_oracle_learned) against that build: at least one pin must fail.  The
 unmodified copy, built the same way, passes them all, so a failure is the
-planted mistake's and not the harness's.  (The layout of the random streams
-is a convention both implementations share, not arithmetic the paper fixes;
-GPU parity covers it.)  CPU only."""
+planted mistake's and not the harness's.  The double-precision network
+reference (oracle/mlp_ref.py) gets the same treatment against the
+learned-selection pins, its mutated copy preloaded by a one-line pytest
+plugin.  (The layout of the random streams is a convention both
+implementations share, not arithmetic the paper fixes; GPU parity covers
+it.)  CPU only."""
 import concurrent.futures as cf
 import os
 import subprocess
@@ -103,6 +106,55 @@ MISTAKES = [
 ]
 
 
+NET_SRC = os.path.join(ROOT, "oracle", "mlp_ref.py")
+
+# the same for the double-precision network reference (oracle/mlp_ref.py),
+# checked by the learned-selection pins
+NET_MISTAKES = [
+    ("ReLU derivative of the second layer dropped",
+     "d2 = np.outer(ds, w3) * (a2 > 0)", "d2 = np.outer(ds, w3)"),
+    ("first-layer backpropagation through W2 transposed",
+     "d1 = (d2 @ W2) * (a1 > 0)", "d1 = (d2 @ W2.T) * (a1 > 0)"),
+    ("output bias gradient averaged twice", "gb3 = ds.sum()", "gb3 = ds.mean()"),
+    ("loss derivative with the wrong sign on positives",
+     "ds = (pos_weight * y * (sg - 1.0) + (1.0 - y) * sg) / B",
+     "ds = (pos_weight * y * (1.0 - sg) + (1.0 - y) * sg) / B"),
+    ("positive-class weight applied to the negatives",
+     "ds = (pos_weight * y * (sg - 1.0) + (1.0 - y) * sg) / B",
+     "ds = (y * (sg - 1.0) + pos_weight * (1.0 - y) * sg) / B"),
+    ("loss derivative not divided by the batch",
+     "ds = (pos_weight * y * (sg - 1.0) + (1.0 - y) * sg) / B",
+     "ds = (pos_weight * y * (sg - 1.0) + (1.0 - y) * sg)"),
+    ("second-layer bias missing in the forward pass", "a2 = h1 @ W2.T + b2", "a2 = h1 @ W2.T"),
+    ("softplus without its stable branch", "np.log1p(np.exp(-np.abs(v)))", "np.log1p(np.exp(-v))"),
+    ("sigmoid at twice the slope", "0.5 * (1.0 + np.tanh(0.5 * v))", "0.5 * (1.0 + np.tanh(v))"),
+    ("Adam without the first-moment bias correction", "mh = m / (1.0 - beta1 ** step)", "mh = m"),
+    ("Adam second moment of |g| instead of g^2", "(1.0 - beta2) * g * g", "(1.0 - beta2) * np.abs(g)"),
+    ("BF16 rounding with ties away from zero",
+     "((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16", "((b + 0x8000) >> 16) << 16"),
+]
+
+PLUGIN = """import importlib.util, os, sys
+_spec = importlib.util.spec_from_file_location("oracle.mlp_ref", os.path.join(os.path.dirname(__file__), "mlp_ref.py"))
+_mod = importlib.util.module_from_spec(_spec)
+_spec.loader.exec_module(_mod)
+sys.modules["oracle.mlp_ref"] = _mod
+"""
+
+
+def _net_pins(src_text, out_dir):
+    os.makedirs(out_dir)
+    with open(os.path.join(out_dir, "mlp_ref.py"), "w") as f:
+        f.write(src_text)
+    with open(os.path.join(out_dir, "planted_netref.py"), "w") as f:
+        f.write(PLUGIN)
+    env = dict(os.environ, PYTHONPATH=out_dir + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-p", "planted_netref",
+                        "tests/test_oracle_learned.py"], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    return r.returncode, r.stdout[-2000:]
+
+
 def _build(src_text, out_dir, name):
     src = os.path.join(out_dir, name + ".c")
     lib = os.path.join(out_dir, name + ".so")
@@ -134,6 +186,25 @@ def test_planted_mistakes_fail_a_pin(tmp_path):
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
         results = list(ex.map(one, range(len(MISTAKES))))
+    missed = [what for what, (rc, _) in results if rc == 0]
+    errors = [(what, out) for what, (rc, out) in results if rc not in (0, 1)]
+    assert not errors, errors
+    assert not missed, "no pin fails with: " + "; ".join(missed)
+
+
+def test_planted_mistakes_in_the_network_reference_fail_a_pin(tmp_path):
+    text = open(NET_SRC).read()
+    for what, old, new in NET_MISTAKES:
+        assert text.count(old) == 1, "the network reference changed near: " + what
+    rc, out = _net_pins(text, str(tmp_path / "unchanged"))
+    assert rc == 0, out
+
+    def one(k):
+        what, old, new = NET_MISTAKES[k]
+        return what, _net_pins(text.replace(old, new), str(tmp_path / ("mistake%02d" % k)))
+
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+        results = list(ex.map(one, range(len(NET_MISTAKES))))
     missed = [what for what, (rc, _) in results if rc == 0]
     errors = [(what, out) for what, (rc, out) in results if rc not in (0, 1)]
     assert not errors, errors
