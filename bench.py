@@ -167,6 +167,14 @@ def oracle_sample(w, z_sample, seed=9):
     return dt, z_sample * w["K"] * w["sweeps"] * (w["m_min"] + w["m_max"]) // 2
 
 
+def n_core_ideal(single_core_rate):
+    """The single-core oracle rate times the host's cores: an upper bound for a
+    parallel CPU run, since the replicas of a phase are independent."""
+    cores = os.cpu_count() or 1
+    return {"n_core_ideal": {"value": single_core_rate * cores, "cores": cores,
+                             "note": "upper bound: cores x the single-core rate (replicas are independent)"}}
+
+
 def run_reference(args, w):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -189,7 +197,8 @@ def run_reference(args, w):
             "config": dict(workload=args.workload, **{k: w[k] for k in ("n", "density", "z", "K", "m_min", "m_max",
                                                                           "sweeps", "alpha", "c", "mut_rate")},
                            replicas_per_sample_step=z_s, l2="n/a (CPU)"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": dict({"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                                 **n_core_ideal(value)),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -438,6 +447,7 @@ def run_gpu(args, w):
         cpu = {"value": a / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "one whole outer iteration of the workload (all %d replicas), single-threaded C oracle, "
                          "%.1f s" % (z, dt)}
+        cpu.update(n_core_ideal(a / dt))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
