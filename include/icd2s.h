@@ -463,8 +463,7 @@ typedef struct icd2s_tuning {
                                  position (2 up to 64 variables, 3 beyond), whichever the
                                  previous sweep's accepts predict cheaper */
     int32_t refresh_kind;     /* tensor-core refresh operands: 1 = a BF16 copy of Q (0 =
-                                 default: 1); 2 = the BF16 copy with pairs of CTAs sharing the
-                                 replica tile through TMA multicast; 3 = int8 Q read as bytes
+                                 default: 1); 2 is not a valid value (ICD2S_ERR_ARG); 3 = int8 Q read as bytes
                                  and converted to BF16 in shared memory (no copy of Q:
                                  2 n ld bytes less device memory, 0.049 against 0.041 ms at
                                  n = 7000, R = 256) */

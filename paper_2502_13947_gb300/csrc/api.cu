@@ -974,7 +974,7 @@ int icd2s_refresh(icd2s_state* st, int32_t rebuild, int32_t* mismatches, void* s
                              st->tune.refresh_splits, s));  // H into G2
     else
         CK(launch_refresh_mma(q->Qb, st->Xb, n, R, ld, st->G2, st->rflags, st->tune.refresh_bn,
-                              st->tune.refresh_splits, st->tune.refresh_kind == 2 ? 2 : 1, s));
+                              st->tune.refresh_splits, s));
     if (st->timing) {
         CK(cudaEventRecord(st->rev[1], s));
         st->timed_refresh = true;
@@ -1223,8 +1223,8 @@ int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t)
         "refresh_bn=%d must be 0, 128 or 256", t->refresh_bn);
     REQ(t->refresh_splits >= 0 && t->refresh_splits <= 256, ICD2S_ERR_ARG, "refresh_splits=%d outside 0..256",
         t->refresh_splits);
-    REQ(t->refresh_kind >= 0 && t->refresh_kind <= 3, ICD2S_ERR_ARG, "refresh_kind=%d outside 0..3",
-        t->refresh_kind);
+    REQ(t->refresh_kind == 0 || t->refresh_kind == 1 || t->refresh_kind == 3, ICD2S_ERR_ARG,
+        "refresh_kind=%d must be 0, 1 or 3", t->refresh_kind);
     REQ(t->anneal_warps_per_cta >= 0 && t->anneal_warps_per_cta <= 4, ICD2S_ERR_ARG,
         "anneal_warps_per_cta=%d outside 0..4", t->anneal_warps_per_cta);
     REQ(t->tabu_wide_keys == 0 || t->tabu_wide_keys == 1, ICD2S_ERR_ARG, "tabu_wide_keys=%d must be 0 or 1",

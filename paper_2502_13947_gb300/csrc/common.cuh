@@ -169,9 +169,8 @@ cudaError_t launch_best(const Dev& d, int64_t* trace_slot, int iter_end, int32_t
 cudaError_t launch_set_iter(int32_t* iter_dev, int t, cudaStream_t s);
 // dense refresh on the tensor cores (kernels_refresh.cu)
 cudaError_t launch_to_bf16(const void* src, bool is_signed, size_t count, void* dst, cudaStream_t s);
-// cluster: 2 = pairs of CTAs share the replica tile through TMA multicast, else 1
 cudaError_t launch_refresh_mma(const void* Qb, const void* Xb, int n, int R, int ld, int32_t* H, int* err, int bn,
-                               int splits, int cluster, cudaStream_t s);
+                               int splits, cudaStream_t s);
 // the same with Q read as int8 bytes and converted to BF16 in shared memory
 cudaError_t launch_refresh_i8(const void* Q8, const void* Xb, int n, int R, int ld, int32_t* H, int* err, int bn,
                               int splits, cudaStream_t s);

@@ -126,46 +126,9 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
                  : "memory");
 }
 
-// TMA load whose tile lands at the same shared-memory offset in every CTA of
-// `mask` (this GPU's own memory only), each CTA's barrier at `bar` counting the bytes
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar,
-                                               uint16_t mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
-        "[%0], [%1, {%2, %3}], [%4], %5;"
-        ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(bar), "h"(mask)
-        : "memory");
-}
-
-// commit whose arrive lands on the barrier at `bar` in every CTA of `mask`
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-        ::"r"(bar), "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 }  // namespace
 
-// CL > 1: the CL CTAs of a cluster take CL consecutive row tiles of the same
-// replicas and K range; each loads 1/CL of the shared X tile and multicasts it
-// to all of them (L2 reads of X fall by CL), and each releases a stage in
-// every CTA of the cluster once its MMAs have read it.
-template <int BN, int STAGES, int CL>
+template <int BN, int STAGES>
 __global__ __launch_bounds__(128, 1) void k_refresh_mma(const __grid_constant__ CUtensorMap tA,
                                                        const __grid_constant__ CUtensorMap tB, int n, int R,
                                                        int kc_total, int kc_per_split, int32_t* __restrict__ H,
@@ -183,8 +146,6 @@ __global__ __launch_bounds__(128, 1) void k_refresh_mma(const __grid_constant__ 
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-    const uint32_t rank = CL > 1 ? cluster_rank() : 0u;
-    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
     const int kc0 = blockIdx.z * kc_per_split;
     const int kc1 = min(kc0 + kc_per_split, kc_total);
     const int nk = kc1 > kc0 ? kc1 - kc0 : 0;
@@ -192,7 +153,7 @@ __global__ __launch_bounds__(128, 1) void k_refresh_mma(const __grid_constant__ 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, CL);  // one release from every CTA of the cluster
+            mbar_init(empty0 + 8 * s, 1);
         }
         mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -204,7 +165,6 @@ __global__ __launch_bounds__(128, 1) void k_refresh_mma(const __grid_constant__ 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     __syncthreads();
-    if constexpr (CL > 1) cluster_sync();  // every CTA's barriers exist before any multicast lands
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
@@ -220,11 +180,7 @@ __global__ __launch_bounds__(128, 1) void k_refresh_mma(const __grid_constant__ 
             mbar_expect_tx(fb, kABytes + kBBytes);
             const int kx = (kc0 + i) * kBK;  // element column, a multiple of 64
             tma_load_2d(smem_u32(sA + s * kABytes), &tA, kx, m0, fb);
-            if constexpr (CL > 1)  // this CTA's 1/CL of the X tile, to every CTA of the cluster
-                tma_load_2d_mc(smem_u32(sB + s * kBBytes + rank * (kBBytes / CL)), &tB, kx,
-                               n0 + (int)rank * (BN / CL), fb, kMask);
-            else
-                tma_load_2d(smem_u32(sB + s * kBBytes), &tB, kx, n0, fb);
+            tma_load_2d(smem_u32(sB + s * kBBytes), &tB, kx, n0, fb);
             ++issued;
         }
         // every load this thread issued has landed before the CTA can leave
@@ -242,8 +198,7 @@ __global__ __launch_bounds__(128, 1) void k_refresh_mma(const __grid_constant__ 
             for (int kk = 0; kk < kBK / 16; ++kk)  // K = 16 per instruction: 32 bytes along the row
                 mma_bf16(tmem, smem_desc_sw128(a + 32 * kk), smem_desc_sw128(b + 32 * kk), kIdesc,
                          (i > 0 || kk > 0) ? 1u : 0u);
-            if constexpr (CL > 1) mma_commit_mc(empty0 + 8 * s, kMask);  // frees the stage in every CTA
-            else mma_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
+            mma_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
         }
         mma_commit(done);
     }
@@ -279,7 +234,6 @@ __global__ __launch_bounds__(128, 1) void k_refresh_mma(const __grid_constant__ 
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if constexpr (CL > 1) cluster_sync();  // no CTA leaves while a peer may still signal or fill its memory
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
 }
@@ -560,36 +514,18 @@ cudaError_t launch_i8(const CUtensorMap& tA, const CUtensorMap& tB, int n, int R
     return cudaGetLastError();
 }
 
-template <int BN, int STAGES, int CL>
+template <int BN, int STAGES>
 cudaError_t launch_mma(const CUtensorMap& tA, const CUtensorMap& tB, int n, int R, int ld, int splits, int32_t* H,
                        int* err, cudaStream_t s)
 {
     const size_t sm = 1024 + (size_t)STAGES * (kBM + BN) * kBK * 2 + (2 * STAGES + 1) * 8 + 16;
-    auto kern = k_refresh_mma<BN, STAGES, CL>;
+    auto kern = k_refresh_mma<BN, STAGES>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int kc_total = ld / kBK;
     const int kcps = (kc_total + splits - 1) / splits;
-    const int mt = ((n + kBM - 1) / kBM + CL - 1) / CL * CL;  // row tiles, whole clusters (extra rows read as 0)
-    dim3 grid(mt, (R + BN - 1) / BN, (kc_total + kcps - 1) / kcps);
-    if constexpr (CL == 1) {
-        kern<<<grid, 128, sm, s>>>(tA, tB, n, R, kc_total, kcps, H, ld, err);
-    } else {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = grid;
-        cfg.blockDim = dim3(128, 1, 1);
-        cfg.dynamicSmemBytes = sm;
-        cfg.stream = s;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = CL;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, kern, tA, tB, n, R, kc_total, kcps, H, ld, err);
-        if (e != cudaSuccess) return e;
-    }
+    dim3 grid((n + kBM - 1) / kBM, (R + BN - 1) / BN, (kc_total + kcps - 1) / kcps);
+    kern<<<grid, 128, sm, s>>>(tA, tB, n, R, kc_total, kcps, H, ld, err);
     note_launch(1);
     return cudaGetLastError();
 }
@@ -601,23 +537,18 @@ cudaError_t launch_mma(const CUtensorMap& tA, const CUtensorMap& tB, int n, int 
 // timed-out wait.  bn: replicas per tile (128 / 256; 0 picks by R);
 // splits: K splits (0: as many as keep every tile's CTAs in one wave).
 cudaError_t launch_refresh_mma(const void* Qb, const void* Xb, int n, int R, int ld, int32_t* H, int* err, int bn,
-                               int splits, int cluster, cudaStream_t s)
+                               int splits, cudaStream_t s)
 {
     CUtensorMap tA, tB;
     const int BN = bn == 128 || bn == 256 ? bn : (R > 128 ? 256 : 128);
-    const int CL = cluster == 2 ? 2 : 1;
-    if (!make_map(&tA, Qb, n, ld, kBM) || !make_map(&tB, Xb, R, ld, BN / CL)) return cudaErrorInvalidValue;
+    if (!make_map(&tA, Qb, n, ld, kBM) || !make_map(&tB, Xb, R, ld, BN)) return cudaErrorInvalidValue;
     const int tiles = ((n + kBM - 1) / kBM) * ((R + BN - 1) / BN);
     const int kc_total = ld / kBK;
     if (splits <= 0) splits = device_sm_count() / tiles;  // one CTA per SM, a single wave
     if (splits < 1) splits = 1;
     if (splits > kc_total) splits = kc_total;
-    if (CL == 2) {
-        if (BN == 256) return launch_mma<256, 4, 2>(tA, tB, n, R, ld, splits, H, err, s);
-        return launch_mma<128, 6, 2>(tA, tB, n, R, ld, splits, H, err, s);
-    }
-    if (BN == 256) return launch_mma<256, 4, 1>(tA, tB, n, R, ld, splits, H, err, s);
-    return launch_mma<128, 6, 1>(tA, tB, n, R, ld, splits, H, err, s);
+    if (BN == 256) return launch_mma<256, 4>(tA, tB, n, R, ld, splits, H, err, s);
+    return launch_mma<128, 6>(tA, tB, n, R, ld, splits, H, err, s);
 }
 
 // H[R][ld] (int32, zeroed by the caller) += Q X^T with Q read as bytes:

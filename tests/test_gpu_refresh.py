@@ -21,14 +21,12 @@ def L():
     return I.lib()
 
 
-@pytest.mark.parametrize("kind", [1, 2, 3])
+@pytest.mark.parametrize("kind", [1, 3])
 @pytest.mark.parametrize("n,R,density", [(1, 1, 1.0), (64, 8, 1.0), (200, 16, 0.5), (300, 5, 0.3),
                                          (1000, 33, 1.0), (2500, 130, 0.1), (4097, 3, 1.0)])
 def test_refresh_equals_the_definition(L, orc, n, R, density, kind):
-    """Every operand path: BF16 copies with every CTA loading its own replica
-    tile, BF16 copies with pairs of CTAs sharing it through TMA multicast (an
-    odd row-tile count leaves a CTA of zero rows), and bytes converted to
-    BF16 in shared memory."""
+    """Both operand paths: BF16 copies of Q and X loaded by TMA, and Q's
+    bytes converted to BF16 in shared memory."""
     Q = make_qubo(n, density, n + R)
     X = random_solutions(n, R, 4)
     q = I.icd2s_qubo_create(Q)
@@ -61,7 +59,7 @@ def test_refresh_after_steps_dense_n7000_R256(L, orc):
     try:
         for t in range(2):
             I.icd2s_step(st, lp, t)
-        for kind in (1, 2, 3):
+        for kind in (1, 3):
             for bn, splits in ((256, 0), (128, 1), (256, 3)):
                 I.icd2s_set_tuning(st, refresh_bn=bn, refresh_splits=splits, refresh_kind=kind)
                 assert I.icd2s_refresh(st) == 0, (kind, bn, splits)
