@@ -500,16 +500,20 @@ int icd2s_debug_fail_allocations_after(int32_t count);
  *                                  (ld % 4 == 0, n <= ld; padding bytes unread
  *                                  for the result), 4-byte aligned
  *   flips_dev  uint8 [replicas][n] 1 = flip this variable
- *   x_dev      uint8 [replicas][ld] solutions, updated in place (4-byte aligned)
+ *   x_dev      uint8 [replicas][ld] solutions, updated in place (4-byte aligned;
+ *                                  columns n .. ld-1 are left as they are)
  *   g_dev      int32 [replicas][ld] exact gains of x_dev, updated in place
- *                                  (16-byte aligned)
+ *                                  (16-byte aligned; columns n .. ld-1 left as they are)
  *   E_dev      int64 [replicas]    energies of x_dev, updated in place
  * Its scratch (flip lists, per-replica counters, the diagonal of Q) is one
  * static device array of about 4.3 MB that every GPU loading the library
  * holds until the process exits; limits: 1 <= n <= 16384, replicas <= 4096,
- * replicas * ld <= 1048576 -- larger sizes return ICD2S_ERR_RANGE.  The
- * first call on a device (with that device current) looks up the array's
- * device address; make that first call before any stream capture.  All calls
+ * replicas * ld <= 1048576 -- larger sizes return ICD2S_ERR_RANGE.  A call
+ * made outside stream capture looks up the array's device address in the
+ * current context of the current device and caches it; a call inside a
+ * capture uses the cached address.  So make the first call on a device, and
+ * the first after a device reset or a change of context, outside any
+ * capture (a captured first call returns ICD2S_ERR_CUDA).  All calls
  * share the array: calls whose GPU work overlaps race and must be ordered by
  * the caller.  No device memory is allocated or freed. */
 int icd2s_apply_flips_static(const int8_t* Q_dev, int32_t n, int32_t ld, int32_t replicas,

@@ -183,9 +183,9 @@ __global__ __launch_bounds__(ApplyShape<COLS>::threads) void k_apply(Dev d)
                     xj ^= fl_j;
                     gout[b] = (1 - 2 * xj) * (dj + 2 * h);
                     if (fl_j) dpart += (long long)gin[b] - gout[b];
-                } else {
-                    gout[b] = 0;
-                    xj = 0;
+                } else {  // columns past n: left as they are (padding of caller-owned rows)
+                    gout[b] = gin[b];
+                    xj = (int)((xw[c4] >> (8 * b)) & 0xffu);
                 }
                 xo[c4] |= (unsigned)xj << (8 * b);
             }

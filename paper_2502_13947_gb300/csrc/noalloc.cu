@@ -11,9 +11,11 @@
 // kStaticScratchBytes, which every GPU that loads the library holds until the
 // process exits.
 //
-// Set-up: the first call on each device, with that device current, looks up
-// the device address of the array (cudaGetSymbolAddress) and caches it; make
-// that first call on a device before any stream capture.  Every call on a
+// Set-up: a call that is not being captured into a CUDA graph looks up the
+// device address of the array (cudaGetSymbolAddress) in the current context
+// of the current device and caches it per device; a captured call uses the
+// cached address, so the first call on a device, and the first after a device
+// reset or a change of context, must be made outside stream capture.  Every call on a
 // device shares the same array, and the array keeps the last call's contents,
 // so each call clears the counters it needs at zero; calls whose work
 // overlaps on the GPU (different streams, no ordering between them) race on
@@ -80,10 +82,21 @@ extern "C" int icd2s_apply_flips_static(const int8_t* Q_dev, int32_t n, int32_t 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return bad(ICD2S_ERR_CUDA, "apply_flips_static: cudaGetDevice failed");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // The array's device address belongs to the device's current context: a
+    // device reset or another context on the same device can move it.  Outside
+    // stream capture every call therefore looks it up again (a host-side table
+    // lookup) and refreshes the cache; inside a capture, where the lookup may
+    // not be allowed, the address cached by an earlier uncaptured call is used.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();  // clear the query's error so the launches below report their own
+        cap = cudaStreamCaptureStatusActive;
+    }
     unsigned char* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_addr[dev]) {  // once per device, with that device current
+        if (cap == cudaStreamCaptureStatusNone) {
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_static_scratch);
             if (e != cudaSuccess || !p) {
@@ -92,10 +105,11 @@ extern "C" int icd2s_apply_flips_static(const int8_t* Q_dev, int32_t n, int32_t 
                 return bad(ICD2S_ERR_CUDA, g_err_static);
             }
             g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+        } else if (!g_scratch_addr[dev]) {
+            return bad(ICD2S_ERR_CUDA, "apply_flips_static: first call on this device made during stream capture");
         }
         base = g_scratch_addr[dev];
     }
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Dev d{};
     d.Q = Q_dev; d.n = n; d.ld = ld; d.R = replicas;
     d.diag = reinterpret_cast<int32_t*>(base + kOffDIAG);

@@ -5,9 +5,10 @@ to a host framework or another allocator, or they must not allocate while
 running): it works on buffers the caller owns and keeps its own scratch in a
 static device array.  Here it is called through the C ABI on caller-owned
 torch buffers and must give exactly what the handle-based
-icd2s_apply_flips_update_gains gives on the same inputs, on two calls in a
-row (the static scratch keeps the previous call's contents, so the second
-call checks that it starts clean).  This file is collected last on purpose."""
+icd2s_apply_flips_update_gains gives on the same inputs, and the oracle's
+gains and energies of the new solutions, on two calls in a row (the static
+scratch keeps the previous call's contents, so the second call checks that
+it starts clean).  This file is collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -20,13 +21,19 @@ from .gpu_util import dev, torch_cuda
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("n,ld,R", [(777, 784, 5), (1000, 1000, 3), (2500, 2560, 8)])
-def test_static_write_back_equals_the_handle_based_one(n, ld, R):
+@pytest.mark.parametrize("n,ld,R", [(777, 784, 5), (777, 780, 5), (1000, 1000, 3), (2499, 2500, 8),
+                                    (2500, 2560, 8)])
+def test_static_write_back_equals_the_handle_based_one(orc, n, ld, R):
+    """Row strides that are multiples of 16 (16-byte path) and of 4 only
+    (4-byte path: 780 and 2500 also end inside a 4-column group and, at 2500,
+    span three column tiles).  The second call runs on an explicit stream.
+    The caller's padding columns of Q, x and g hold non-zero values: Q's are
+    never used for the result, x's and g's are left as they were."""
     torch = torch_cuda()
     B.build()
     Q = make_qubo(n, 0.3, n)
     X0 = random_solutions(n, R, 1)
-    rng = np.random.default_rng(n)
+    rng = np.random.default_rng(n + ld)
     M1 = (rng.random((R, n)) < 0.05).astype(np.uint8)
     M2 = (rng.random((R, n)) < 0.2).astype(np.uint8)
     M1[0] = 0                       # a replica with nothing to flip
@@ -46,20 +53,33 @@ def test_static_write_back_equals_the_handle_based_one(n, ld, R):
     I.icd2s_qubo_destroy(q)
 
     # the static entry point, on caller-owned buffers with row stride ld
-    Qp = np.zeros((n, ld), np.int8)
+    Qp = rng.integers(-100, 101, (n, ld)).astype(np.int8)
     Qp[:, :n] = Q
-    Xp = np.zeros((R, ld), np.uint8)
+    Xp = np.full((R, ld), 7, np.uint8)
     Xp[:, :n] = X0
-    Gp = np.zeros((R, ld), np.int32)
+    Gp = np.full((R, ld), -12345, np.int32)
     Gp[:, :n] = g0
     Qd, Xd, Gd, Ed = dev(Qp), dev(Xp), dev(Gp), dev(E0.copy())
-    for M_d, (wx, wg, wE) in ((M1d, want1), (M2d, want2)):
-        I.icd2s_apply_flips_static(Qd.data_ptr(), n, ld, R, M_d.data_ptr(), Xd.data_ptr(), Gd.data_ptr(),
-                                   Ed.data_ptr())
-        torch.cuda.synchronize()
-        assert np.array_equal(Xd.cpu().numpy()[:, :n], wx)
-        assert np.array_equal(Gd.cpu().numpy()[:, :n], wg)
-        assert np.array_equal(Ed.cpu().numpy(), wE)
+    side = torch.cuda.Stream()
+    for call, (M_d, (wx, wg, wE)) in enumerate(((M1d, want1), (M2d, want2))):
+        if call == 0:
+            I.icd2s_apply_flips_static(Qd.data_ptr(), n, ld, R, M_d.data_ptr(), Xd.data_ptr(), Gd.data_ptr(),
+                                       Ed.data_ptr())
+            torch.cuda.synchronize()
+        else:
+            side.wait_stream(torch.cuda.current_stream())
+            I.icd2s_apply_flips_static(Qd.data_ptr(), n, ld, R, M_d.data_ptr(), Xd.data_ptr(), Gd.data_ptr(),
+                                       Ed.data_ptr(), stream=side.cuda_stream)
+            side.synchronize()
+        x, g, E = Xd.cpu().numpy(), Gd.cpu().numpy(), Ed.cpu().numpy()
+        assert np.array_equal(x[:, :n], wx)
+        assert np.array_equal(g[:, :n], wg)
+        assert np.array_equal(E, wE)
+        assert (x[:, n:] == 7).all() and (g[:, n:] == -12345).all()
+        # and against the oracle's definition-level gains and energies (Eq. 1)
+        assert np.array_equal(E, orc.energy_batch(Q, np.ascontiguousarray(x[:, :n])))
+        for p in (0, R - 1):
+            assert np.array_equal(g[p, :n], orc.gains(Q, np.ascontiguousarray(x[p, :n])))
 
 
 def test_static_write_back_rejects_sizes_beyond_its_scratch():
