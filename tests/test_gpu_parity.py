@@ -295,6 +295,69 @@ def test_tabu_compact_keys_at_the_gain_bound(L, orc, extra):
         I.icd2s_qubo_destroy(q)
 
 
+# ----------------------------------------------------------------------------- Algorithm 1 on a cluster
+@pytest.mark.parametrize("G", [1, 2, 4])
+@pytest.mark.parametrize("n,density,asp,wide,alpha,c,R", [
+    (300, 0.5, 0, 0, 900, 3, 3),      # slices of 128 / 256 variables, the last one ragged
+    (300, 0.5, 1, 1, 900, 60, 2),     # aspiration, wide keys
+    (2500, 0.1, 0, 0, 2000, 16, 3),   # compact keys
+    (2500, 0.1, 1, 0, 3000, 40, 2),
+    (5000, 0.5, 0, 1, 2000, 33, 2),   # the time-to-target instance: wide keys
+    (5000, 0.5, 1, 1, 2000, 120, 2),
+    (700, 1.0, 1, 0, 2100, 17, 3),
+    (40, 1.0, 1, 0, 320, 40, 2),      # c = n: the all-tabu fallback; CTAs with no variables
+    (13001, 0.5, 0, 1, 150, 86, 1),
+])
+def test_tabu_split_over_a_cluster(L, orc, G, n, density, asp, wide, alpha, c, R):
+    """Algorithm 1 with every replica's variables split over a cluster of G
+    CTAs (the per-move arg-min exchanged through distributed shared memory):
+    the search equals the oracle's for every G, with and without aspiration
+    and with compact and wide keys."""
+    P = Problem(n, density, 3 * n + 1, R=R)
+    X0 = random_solutions(n, R, n + c)
+    P.load(X0)
+    I.icd2s_set_tuning(P.st, tabu_cluster=G, tabu_wide_keys=wide)
+    (I.icd2s_tabu_aspiration if asp else I.icd2s_tabu)(P.st, alpha, c)
+    _check_tabu(orc, P.Q, X0, alpha, c, asp, P.state() + I.icd2s_get_tabu(P.st, R, n))
+    P.close()
+
+
+@pytest.mark.parametrize("G,asp", [(2, 0), (4, 1)])
+def test_tabu_split_with_a_move_log_beyond_shared_memory(L, orc, G, asp):
+    """The cluster split with the move log in global memory (written by the
+    cluster's first CTA, read by all after the search)."""
+    n, R, c = 300, 2, 7
+    P = Problem(n, 0.5, 79, R=R)
+    X0 = random_solutions(n, R, 80)
+    I.icd2s_set_tuning(P.st, tabu_cluster=G)
+    for alpha in (120_000, 900):
+        P.load(X0)
+        (I.icd2s_tabu_aspiration if asp else I.icd2s_tabu)(P.st, alpha, c)
+        _check_tabu(orc, P.Q, X0, alpha, c, asp, P.state() + I.icd2s_get_tabu(P.st, R, n))
+    P.close()
+
+
+@pytest.mark.parametrize("G,variant", [(2, 4), (4, 5), (2, 1)])
+def test_tabu_split_in_other_kernel_shapes(L, orc, G, variant):
+    n, R, alpha, c = 2500, 2, 1500, 16
+    P = Problem(n, 0.1, 81, R=R)
+    X0 = random_solutions(n, R, 82)
+    P.load(X0)
+    I.icd2s_set_tuning(P.st, tabu_cluster=G, tabu_variant=variant)
+    I.icd2s_tabu(P.st, alpha, c)
+    _check_tabu(orc, P.Q, X0, alpha, c, 0, P.state() + I.icd2s_get_tabu(P.st, R, n))
+    P.close()
+
+
+def test_tabu_cluster_setting_is_checked(L):
+    P = Problem(300, 0.5, 1, R=2)
+    with pytest.raises(I.ICD2SError):
+        I.icd2s_set_tuning(P.st, tabu_cluster=3)
+    with pytest.raises(I.ICD2SError):
+        I.icd2s_set_tuning(P.st, tabu_cluster=2, tabu_variant=3)   # a one-CTA-only shape
+    P.close()
+
+
 # ----------------------------------------------------------------------------- Eq. 6-8, Alg. 3, selection
 @pytest.mark.parametrize("n,R,K,m_min,m_max", [(500, 6, 3, 8, 40), (333, 4, 1, 64, 64), (2500, 3, 16, 32, 150)])
 def test_control_parameters_and_selection(L, orc, n, R, K, m_min, m_max):
