@@ -16,8 +16,11 @@ alpha = 5n, c = 16 and a 1 % mutation rate.  Inputs are resident in HBM when
 the timed region starts; L2 is flushed (a 256 MiB write, then a 256 MiB
 read) before every timed step, outside the step's events.  `--impl reference` times the CPU oracle
 (single thread, as it stands) on a bounded sample of the same workload.
-Under torchrun every rank solves its own instance (independent problems,
-weak scaling, no collective on the data path); rank 0 prints one JSON line.
+Under torchrun the ranks solve one problem together: every rank holds 128
+replicas of a set of 128 x N (a replica shard; weak scaling), and each outer
+iteration adds the shards' column counts for gamma (one allreduce of n int32,
+Eq. 8), the only exchange the method has on its data path.  Rank 0 prints
+one JSON line.
 """
 from __future__ import annotations
 
@@ -76,7 +79,7 @@ def max_over_ranks(dist, torch, seconds_or_ms, device):
 
 
 def whole_job_rate(world, units_per_rank_step, steps, seconds):
-    """Units processed by all ranks (each rank solves its own instance:
+    """Units processed by all ranks (each holds the same number of replicas:
     weak scaling) per second of the slowest rank's time."""
     return world * units_per_rank_step * steps / seconds
 
@@ -343,25 +346,43 @@ def run_gpu(args, w):
     except Exception:
         pass
 
-    n, z = w["n"], w["z"]
-    Q = make_qubo(n, w["density"], w["qseed"] + 1000 * rank)   # every rank: its own instance
-    p = I.icd2s_default_params(n, z=z, K=w["K"], m_min=w["m_min"], m_max=w["m_max"], m_init=w["m_init"],
+    n, z = w["n"], w["z"]              # z replicas per GPU
+    z_total = z * world
+    Q = make_qubo(n, w["density"], w["qseed"])   # one problem; its replica set is sharded over the ranks
+    p = I.icd2s_default_params(n, z=z_total, K=w["K"], m_min=w["m_min"], m_max=w["m_max"], m_init=w["m_init"],
                                sweeps=w["sweeps"], alpha=w["alpha"], c=w["c"], T_max=w["T_max"], T_min=w["T_min"],
                                mut_mode=w["mut_mode"], mut_rate=w["mut_rate"], patience=0, max_iters=1 << 30)
     q = I.icd2s_qubo_create(Q)
-    st = I.icd2s_state_create(q, z, 7 + rank)
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
     flush = L2Flush(torch)
+    sharded = None
+    if world > 1:
+        from paper_2502_13947_gb300.shard import ShardedState
+        sharded = ShardedState(I, torch, dist, q, n, z_total, 7)
+        st = sharded.st
+    else:
+        st = I.icd2s_state_create(q, z, 7)
+
+    def step(t):  # enqueued on `stream` (the current stream inside the caller's context)
+        if sharded:
+            sharded.step(p, t)
+        else:
+            I.icd2s_step(st, p, t, sp)
+
     with torch.cuda.stream(stream):
-        I.icd2s_initial_pass(st, p, sp)
-        I.icd2s_best_update(st, sp)
+        if sharded:
+            sharded.initial_pass(p)
+        else:
+            I.icd2s_initial_pass(st, p, sp)
+            I.icd2s_best_update(st, sp)
     torch.cuda.synchronize()
     I.icd2s_set_timing(st, True)
     t = 0
-    for _ in range(args.warmup):
-        I.icd2s_step(st, p, t, sp)
-        t += 1
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(t)
+            t += 1
     torch.cuda.synchronize()
 
     phase_tot = dict.fromkeys(I.PHASES, 0.0)
@@ -378,7 +399,7 @@ def run_gpu(args, w):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            I.icd2s_step(st, p, t, sp)
+            step(t)
             e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -408,7 +429,13 @@ def run_gpu(args, w):
     e2e_s = 0.0
     for _ in range(e2e_steps):
         t0 = time.perf_counter()
-        I.icd2s_step_host(st, p, t, x_in, x_out, E_out, sp)
+        if sharded:   # the same copies around the shard's step: x in, then x and E out
+            with torch.cuda.stream(stream):
+                I.icd2s_state_load(st, x_in, stream=sp)
+                step(t)
+            I.icd2s_get_state(st, z, n, x=x_out, E=E_out, want_g=False)
+        else:
+            I.icd2s_step_host(st, p, t, x_in, x_out, E_out, sp)
         e2e_s += time.perf_counter() - t0
         x_in[:] = x_out
         t += 1
@@ -416,7 +443,10 @@ def run_gpu(args, w):
         e2e_s = max_over_ranks(dist, torch, e2e_s, "cuda")
     e2e_value = whole_job_rate(world, att, e2e_steps, e2e_s)
 
-    I.icd2s_state_destroy(st)
+    if sharded:
+        sharded.close()
+    else:
+        I.icd2s_state_destroy(st)
     I.icd2s_qubo_destroy(q)
     if rank != 0:
         if world > 1:
@@ -452,10 +482,13 @@ def run_gpu(args, w):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload, "n": n, "density": w["density"], "z": z, "K": w["K"],
+        "config": {"workload": args.workload, "n": n, "density": w["density"], "z": z_total, "z_per_gpu": z,
+                   "K": w["K"],
                    "m_min": w["m_min"], "m_max": w["m_max"], "sweeps": w["sweeps"], "alpha": w["alpha"],
                    "c": w["c"], "mutation_rate": w["mut_rate"], "T_max": w["T_max"], "T_min": w["T_min"],
-                   "attempts_per_step": att, "parallelism": "independent instance per GPU" if world > 1 else "1 GPU",
+                   "attempts_per_step": att,
+                   "parallelism": ("replica shards of one problem, %d per GPU; one allreduce of n int32 column "
+                                   "counts per iteration (gamma, Eq. 8)" % z) if world > 1 else "1 GPU",
                    "l2": "flushed before every timed step (256 MiB write + 256 MiB read, outside the step events)"},
         "roofline": roofline,
         "roofline_refresh": refresh,

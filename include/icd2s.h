@@ -188,6 +188,22 @@ int icd2s_energy(icd2s_qubo* q, const uint8_t* x_dev, int32_t count, int64_t* E_
 int icd2s_state_create(icd2s_qubo* q, int32_t replicas, uint64_t seed, icd2s_state** out);
 int icd2s_state_destroy(icd2s_state* st);
 
+/* A replica shard: replicas replica_base .. replica_base + replicas - 1 of a
+ * solution set of replicas_total, for running one problem over several GPUs
+ * (one shard per GPU).  Every random draw of the method (the initial
+ * solutions, the subQUBO sizes, the annealer's and the mutation's streams,
+ * the No_SM ranking) is keyed by the global replica index, so the shards
+ * together make exactly the solution set that icd2s_state_create(q,
+ * replicas_total, seed) makes.  The replicas interact only through gamma
+ * (Eq. 8: column sums over all z solutions) and the best solution
+ * (Algorithm 2): a shard steps with icd2s_step_shard_begin / _finish (the
+ * caller adds up the shards' column counts in between) and reports its best
+ * with icd2s_get_best_info.  icd2s_step, icd2s_run and icd2s_select_subqubos
+ * return ICD2S_ERR_STATE on a shard with replicas < replicas_total; params
+ * take z = replicas_total.  ERR_ARG if the shard lies outside the set. */
+int icd2s_state_create_shard(icd2s_qubo* q, int32_t replicas, int32_t replica_base, int32_t replicas_total,
+                             uint64_t seed, icd2s_state** out);
+
 /* Replaces the solutions with x[replicas][n] (0/1; on the host when
  * x_is_device == 0, else on the device) and recomputes gains and energies. */
 int icd2s_state_load(icd2s_state* st, const uint8_t* x, int32_t x_is_device, void* stream);
@@ -198,6 +214,15 @@ int icd2s_get_state(icd2s_state* st, uint8_t* x, int32_t* g, int64_t* E);
 
 /* Best solution seen by icd2s_best_update / icd2s_step (host copies). */
 int icd2s_get_best(icd2s_state* st, uint8_t* x_best, int64_t* E_best);
+
+/* The best solution's energy, its global replica index and when it was
+ * reached: stamp = 3 t + k + 1 for the k-th best update (after the Tabu
+ * search, the Ising machine, the mutation) of iteration t, 0 for
+ * icd2s_best_update; replica = stamp = -1 before any update.  Across replica
+ * shards the method's best (Algorithm 2, the lowest energy, first reached,
+ * lowest replica at that update) is the shard best with the smallest
+ * (E, stamp, replica).  Synchronises. */
+int icd2s_get_best_info(icd2s_state* st, int64_t* E_best, int32_t* replica, int32_t* stamp);
 
 /* --- Checkpoint and resume (no counterpart in the paper) ---------------------
  * A checkpoint holds what the later outer iterations read from a state: the
@@ -329,6 +354,20 @@ int icd2s_initial_pass(icd2s_state* st, const icd2s_params* p, void* stream);
  * parameters, selection, Ising machine, write-back, mutation, best update.
  * Enqueued on `stream`; no host synchronisation. */
 int icd2s_step(icd2s_state* st, const icd2s_params* p, int32_t t, void* stream);
+
+/* Outer iteration t on a replica shard, in two calls enqueued on `stream`.
+ * _begin runs the Tabu search (Algorithm 1), the best update after it, the
+ * learned selection's features and scores, and writes the shard's column
+ * counts counts_dev[j] = sum over its replicas of x_pj (int32 [n], device).
+ * The caller adds the counts of every shard (an allreduce) and passes the
+ * totals to _finish, which takes gamma from them (Eq. 8 over all
+ * replicas_total solutions) and runs the rest of the iteration: control
+ * parameters and selection (Algorithm 3-4), Ising machine, write-back,
+ * mutation (Eq. 5) and the best updates.  On a whole set (replicas ==
+ * replicas_total) begin + finish with its own counts is icd2s_step. */
+int icd2s_step_shard_begin(icd2s_state* st, const icd2s_params* p, int32_t t, int32_t* counts_dev, void* stream);
+int icd2s_step_shard_finish(icd2s_state* st, const icd2s_params* p, int32_t t, const int32_t* counts_dev,
+                            void* stream);
 
 /* icd2s_step with host buffers: loads x_in[replicas][n] (if not NULL) into
  * the state, runs iteration t, and copies the solutions to x_out (if not
@@ -467,6 +506,11 @@ typedef struct icd2s_tuning {
                                  and converted to BF16 in shared memory (no copy of Q:
                                  2 n ld bytes less device memory, 0.049 against 0.041 ms at
                                  n = 7000, R = 256) */
+    int32_t tabu_cluster;     /* Tabu search: CTAs per replica, 1, 2 or 4 (a thread-block
+                                 cluster; each CTA holds a slice of the variables and the
+                                 per-move arg-min is exchanged through distributed shared
+                                 memory); 0 = default: 4 where n >= 8192 and 4 x replicas
+                                 <= SMs, else 1.  Results are the same for every value. */
 } icd2s_tuning;
 int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t);
 int icd2s_get_tuning(icd2s_state* st, icd2s_tuning* t);

@@ -294,7 +294,8 @@ static int check_params(const icd2s_state* st, const icd2s_params* p)
 {
     const int n = st->q->n;
     REQ(p, ICD2S_ERR_ARG, "params is NULL");
-    REQ(p->z == st->R, ICD2S_ERR_ARG, "params z=%d differs from the state's %d replicas", p->z, st->R);
+    REQ(p->z == st->d.z_total, ICD2S_ERR_ARG, "params z=%d differs from the state's replica set of %d", p->z,
+        st->d.z_total);
     REQ(p->K >= 1 && p->K <= 64, ICD2S_ERR_RANGE, "K=%d outside 1..64", p->K);
     REQ(p->m_min >= 1 && p->m_min <= p->m_max && p->m_max <= kMaxM, ICD2S_ERR_RANGE,
         "subQUBO sizes m_min=%d m_max=%d outside 1..256", p->m_min, p->m_max);
@@ -451,10 +452,18 @@ int icd2s_energy(icd2s_qubo* q, const uint8_t* x_dev, int32_t count, int64_t* E_
 // ----------------------------------------------------------------------------- solutions
 int icd2s_state_create(icd2s_qubo* q, int32_t replicas, uint64_t seed, icd2s_state** out)
 {
+    return icd2s_state_create_shard(q, replicas, 0, replicas, seed, out);
+}
+
+int icd2s_state_create_shard(icd2s_qubo* q, int32_t replicas, int32_t replica_base, int32_t replicas_total,
+                             uint64_t seed, icd2s_state** out)
+{
     REQ(q && out, ICD2S_ERR_ARG, "NULL argument");
     *out = nullptr;
     REQ(replicas >= 1 && replicas <= kMaxReplicas, ICD2S_ERR_RANGE, "replicas=%d outside 1..%d", replicas,
         kMaxReplicas);
+    REQ(replica_base >= 0 && (long long)replica_base + replicas <= replicas_total, ICD2S_ERR_ARG,
+        "replicas %d..%d outside the set of %d", replica_base, replica_base + replicas - 1, replicas_total);
     auto* st = new icd2s_state();
     st->q = q; st->R = replicas; st->seed = seed;
     const size_t RL = (size_t)replicas * q->ld;
@@ -481,6 +490,7 @@ int icd2s_state_create(icd2s_qubo* q, int32_t replicas, uint64_t seed, icd2s_sta
     d.H = st->H;
     d.ACC = st->ACC; d.TT = st->TT; d.apply_splits = apply_splits_for(q->ld, replicas);
     d.k0 = (uint32_t)(seed & 0xffffffffu); d.k1 = (uint32_t)(seed >> 32);
+    d.p0 = replica_base; d.z_total = replicas_total;
     uint32_t nl[4096];
     make_nlog(nl);
     const int64_t big = INT64_MAX;
@@ -770,7 +780,7 @@ int icd2s_tabu(icd2s_state* st, int32_t alpha, int32_t c, void* stream)
     int rc = ensure_tabu_log(st, alpha, S(stream));
     if (rc) return rc;
     CK(launch_tabu(st->d, alpha, c, st->tune.tabu_variant, S(stream), false, st->tune.tabu_wide_keys != 0,
-                   st->tune.tabu_rows));
+                   st->tune.tabu_rows, st->tune.tabu_cluster));
     return ICD2S_OK;
 }
 
@@ -783,24 +793,29 @@ int icd2s_tabu_aspiration(icd2s_state* st, int32_t alpha, int32_t c, void* strea
     int rc = ensure_tabu_log(st, alpha, S(stream));
     if (rc) return rc;
     CK(launch_tabu(st->d, alpha, c, st->tune.tabu_variant, S(stream), true, st->tune.tabu_wide_keys != 0,
-                   st->tune.tabu_rows));
+                   st->tune.tabu_rows, st->tune.tabu_cluster));
     return ICD2S_OK;
 }
 
 // iter_dev: non-null when the iteration number comes from device memory (a replayed step).
+// counts: the column counts of all replica shards for gamma (null: this
+// state's own replicas, which must then be the whole set).
 static int select_impl(icd2s_state* st, int64_t w1, int64_t w2, int64_t w3, int K, int m_min, int m_max,
                        uint32_t iter, cudaStream_t s, const int32_t* iter_dev = nullptr, int mode = 0,
-                       bool count_hits = true, int ablation = 0)
+                       bool count_hits = true, int ablation = 0, const int32_t* counts = nullptr)
 {
     const int n = st->q->n;
+    REQ(counts || st->d.z_total == st->R, ICD2S_ERR_STATE,
+        "a replica shard takes gamma from the counts of every shard (icd2s_step_shard_finish)");
     REQ(K >= 1 && K <= 64, ICD2S_ERR_RANGE, "K=%d outside 1..64", K);
     REQ(m_min >= 1 && m_min <= m_max && m_max <= kMaxM, ICD2S_ERR_RANGE, "sizes %d..%d outside 1..256", m_min, m_max);
     if (ablation == 1) m_min = m_max = 0;  // No_IM: an empty subset (only A and its ranking are made)
     REQ((long long)K * m_max <= n, ICD2S_ERR_ARG, "K*m_max exceeds n");
     const int64_t wl = (int64_t)1 << 24;
     REQ(w1 >= -wl && w1 <= wl && w2 >= -wl && w2 <= wl && w3 >= -wl && w3 <= wl, ICD2S_ERR_RANGE, "|w| > 2^24");
-    CK(launch_gamma(st->d, s));
-    CK(launch_sizes(st->R, K, m_min, m_max, st->d.k0, st->d.k1, iter, iter_dev, st->off, st->lpt, st->queue, s));
+    CK(launch_gamma(st->d, counts, s));
+    CK(launch_sizes(st->R, K, m_min, m_max, st->d.k0, st->d.k1, iter, iter_dev, st->off, st->lpt, st->queue, s,
+                    st->d.p0));
     CK(launch_select(st->d, w1, w2, w3, K, st->off, st->idx, mode, count_hits, s, iter, iter_dev, ablation));
     st->have_select = true;
     st->sel_K = K;
@@ -835,7 +850,9 @@ static int anneal_impl(icd2s_state* st, const int32_t* idx, const int32_t* off, 
     AnnealArgs a{};
     a.idx = idx; a.off = off; a.count = count; a.per_replica = per_replica; a.block_m = block_m;
     a.block_base = block_base; a.limtab = st->limtab; a.sweeps = sweeps; a.iter = iter;
-    a.slot_base = 0; a.mask = mask; a.ldm = ldm; a.dE = dE; a.attempts_acc = st->counters; a.m_max = m_max;
+    // random streams by global replica: slot p K + k of a subQUBO, p of a block
+    a.slot_base = (uint32_t)(idx ? st->d.p0 * per_replica : st->d.p0);
+    a.mask = mask; a.ldm = ldm; a.dE = dE; a.attempts_acc = st->counters; a.m_max = m_max;
     a.warps_per_cta = st->tune.anneal_warps_per_cta;
     a.scheme = st->tune.anneal_scheme;
     a.iter_dev = iter_dev;
@@ -1051,13 +1068,16 @@ static bool wants_features(const icd2s_state* st, const icd2s_params* p)
 
 // One outer iteration.  dev_iter: the kernels read t (and the mutation rate)
 // from st->ctx / st->rates, and the last one advances st->ctx[0] -- the form
-// that is captured once and replayed as a CUDA graph.
-static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* trace_it, cudaStream_t s,
-                     bool dev_iter = false)
+// that is captured once and replayed as a CUDA graph.  It runs in two parts:
+// the Tabu search (and the learned selection's features and scores), then
+// everything from the selection on, which needs gamma over all replicas; a
+// replica shard runs them as icd2s_step_shard_begin / _finish with the
+// column counts of every shard added up in between.
+static int step_first(icd2s_state* st, const icd2s_params* p, int t, int64_t* trace_it, cudaStream_t s,
+                      bool dev_iter = false)
 {
     const int R = st->R;
     const int32_t* it_dev = dev_iter ? st->ctx : nullptr;
-    const bool queued = p->K > 1 || p->m_min != p->m_max;  // uneven batch: persistent queue kernel
     int rc = ensure_beta(st, p->sweeps, p->T_max, p->T_min, s);
     if (rc) return rc;
     if ((rc = ensure_tabu_log(st, p->alpha, s))) return rc;  // (made before any capture by graph_step)
@@ -1065,9 +1085,9 @@ static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* tra
     if (feats && (rc = ensure_features(st, s))) return rc;
     mark(st, 0, 0, s);
     CK(launch_tabu(st->d, p->alpha, p->c, st->tune.tabu_variant, s, p->aspiration != 0,
-                   st->tune.tabu_wide_keys != 0, st->tune.tabu_rows));  // Algorithm 1
+                   st->tune.tabu_wide_keys != 0, st->tune.tabu_rows, st->tune.tabu_cluster));  // Algorithm 1
     mark(st, 0, 1, s);
-    CK(launch_best(st->d, trace_it, 0, nullptr, s));
+    CK(launch_best(st->d, trace_it, 0, dev_iter ? st->ctx : nullptr, s, nullptr, 0, t));
     mark(st, 1, 0, s);
     if (feats) {                                                   // learned selection: features, scores
         CK(launch_features(st->d, t, it_dev, p->alpha, p->c, st->gmax, s));
@@ -1077,8 +1097,18 @@ static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* tra
             st->have_scores = true;
         }
     }
-    rc = select_impl(st, p->w1, p->w2, p->w3, p->K, p->m_min, p->m_max, (uint32_t)t, s, it_dev,
-                     p->select_mode, true, p->ablation);                                    // Eq. 6-8, Alg. 3-4
+    return ICD2S_OK;
+}
+
+// counts: gamma's column counts over every replica shard (null: this state's replicas)
+static int step_second(icd2s_state* st, const icd2s_params* p, int t, int64_t* trace_it, cudaStream_t s,
+                       bool dev_iter = false, const int32_t* counts = nullptr)
+{
+    const int R = st->R;
+    const int32_t* it_dev = dev_iter ? st->ctx : nullptr;
+    const bool queued = p->K > 1 || p->m_min != p->m_max;  // uneven batch: persistent queue kernel
+    int rc = select_impl(st, p->w1, p->w2, p->w3, p->K, p->m_min, p->m_max, (uint32_t)t, s, it_dev,
+                         p->select_mode, true, p->ablation, counts);                        // Eq. 6-8, Alg. 3-4
     if (rc) return rc;
     mark(st, 1, 1, s);
     mark(st, 2, 0, s);
@@ -1099,7 +1129,7 @@ static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* tra
     mark(st, 3, 0, s);
     CK(launch_apply(st->d, s));
     mark(st, 3, 1, s);
-    CK(launch_best(st->d, trace_it ? trace_it + R : nullptr, 0, nullptr, s));
+    CK(launch_best(st->d, trace_it ? trace_it + R : nullptr, 0, dev_iter ? st->ctx : nullptr, s, nullptr, 1, t));
     const double r = p->mut_mode == 0 ? mutation_rate(t) : p->mut_rate;        // Eq. 5
     mark(st, 4, 0, s);
     CK(launch_mutate(st->d, st->sel_K, st->off, r, (uint32_t)t, it_dev, st->rates, nullptr, st->q->n, s,
@@ -1110,11 +1140,19 @@ static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* tra
     mark(st, 5, 1, s);
     mark(st, 6, 0, s);
     CK(launch_best(st->d, trace_it ? trace_it + 2 * R : nullptr, 1, dev_iter ? st->ctx : nullptr, s,
-                   st->log_cap > 0 ? st->log_ctl : nullptr));
+                   st->log_cap > 0 ? st->log_ctl : nullptr, 2, t));
     if (st->log_cap > 0) CK(launch_log(st->d, st->prev_x, st->LF, st->LY, st->lrep, s));
     mark(st, 6, 1, s);
     st->timed_step = st->timing;
     return ICD2S_OK;
+}
+
+static int step_impl(icd2s_state* st, const icd2s_params* p, int t, int64_t* trace_it, cudaStream_t s,
+                     bool dev_iter = false)
+{
+    int rc = step_first(st, p, t, trace_it, s, dev_iter);
+    if (rc) return rc;
+    return step_second(st, p, t, trace_it, s, dev_iter);
 }
 
 // Replays the outer iteration as one CUDA graph, capturing it first when
@@ -1217,8 +1255,11 @@ int icd2s_get_apply_ms(icd2s_state* st, double* ms)
 int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t)
 {
     REQ(st && t, ICD2S_ERR_ARG, "NULL argument");
-    REQ(t->tabu_variant < 0 || tabu_variant_fits(t->tabu_variant, st->q->n), ICD2S_ERR_ARG,
-        "Tabu variant %d does not cover n=%d", t->tabu_variant, st->q->n);
+    REQ(t->tabu_cluster == 0 || t->tabu_cluster == 1 || t->tabu_cluster == 2 || t->tabu_cluster == 4, ICD2S_ERR_ARG,
+        "tabu_cluster=%d must be 0, 1, 2 or 4", t->tabu_cluster);
+    REQ(t->tabu_variant < 0 || tabu_variant_fits(t->tabu_variant, st->q->n, t->tabu_cluster > 1 ? t->tabu_cluster : 1),
+        ICD2S_ERR_ARG, "Tabu variant %d does not cover n=%d with %d CTAs per replica", t->tabu_variant, st->q->n,
+        t->tabu_cluster > 1 ? t->tabu_cluster : 1);
     REQ(t->refresh_bn == 0 || t->refresh_bn == 128 || t->refresh_bn == 256, ICD2S_ERR_ARG,
         "refresh_bn=%d must be 0, 128 or 256", t->refresh_bn);
     REQ(t->refresh_splits >= 0 && t->refresh_splits <= 256, ICD2S_ERR_ARG, "refresh_splits=%d outside 0..256",
@@ -1287,21 +1328,33 @@ int icd2s_autotune(icd2s_state* st, const icd2s_params* p, icd2s_tuning* chosen,
     icd2s_tuning best = st->tune;
     const int alpha = p->alpha < 2000 ? p->alpha : 2000;
     float best_ms = 1e30f;
-    for (int v = 0; v < tabu_num_variants(); ++v) {
-        if (!tabu_variant_fits(v, n)) continue;
-        for (int rows = 1; rows <= (st->d.Q2 ? 2 : 1); ++rows) {  // plain rows, then signed rows (if made)
-            float vbest = 1e30f;
-            for (int rep = 0; rep < 2; ++rep) {
-                if ((rc = restore())) return rc;
-                CK(cudaEventRecord(e0, s));
-                CK(launch_tabu(st->d, alpha, p->c, v, s, p->aspiration != 0, st->tune.tabu_wide_keys != 0, rows));
-                CK(cudaEventRecord(e1, s));
-                CK(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < vbest) vbest = ms;
+    // CTAs per replica: one, and the splits that keep every CTA on an SM of its own
+    // (a split needs the compact keys)
+    const bool ck = st->tune.tabu_wide_keys == 0 && tabu_key_shift(n, st->d.gain_bound) > 0;
+    for (int G : {1, 2, 4}) {
+        if (G > 1 && (!ck || (long long)R * G > device_sm_count())) continue;
+        for (int v = 0; v < tabu_num_variants(); ++v) {
+            if (!tabu_variant_fits(v, n, G)) continue;
+            for (int rows = 1; rows <= (st->d.Q2 ? 2 : 1); ++rows) {  // plain rows, then signed rows (if made)
+                float vbest = 1e30f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    if ((rc = restore())) return rc;
+                    CK(cudaEventRecord(e0, s));
+                    CK(launch_tabu(st->d, alpha, p->c, v, s, p->aspiration != 0, st->tune.tabu_wide_keys != 0, rows,
+                                   G));
+                    CK(cudaEventRecord(e1, s));
+                    CK(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, e0, e1));
+                    if (ms < vbest) vbest = ms;
+                }
+                if (vbest < best_ms) {
+                    best_ms = vbest;
+                    best.tabu_variant = v;
+                    best.tabu_rows = rows;
+                    best.tabu_cluster = G;
+                }
             }
-            if (vbest < best_ms) { best_ms = vbest; best.tabu_variant = v; best.tabu_rows = rows; }
         }
     }
     if ((rc = restore())) return rc;
@@ -1355,6 +1408,43 @@ int icd2s_step(icd2s_state* st, const icd2s_params* p, int32_t t, void* stream)
     if (rc) return rc;
     REQ(t >= 0, ICD2S_ERR_ARG, "t < 0");
     return p->use_graph ? graph_step(st, p, t, S(stream)) : step_impl(st, p, t, nullptr, S(stream));
+}
+
+int icd2s_step_shard_begin(icd2s_state* st, const icd2s_params* p, int32_t t, int32_t* counts_dev, void* stream)
+{
+    REQ(st && p && counts_dev, ICD2S_ERR_ARG, "NULL argument");
+    int rc = check_params(st, p);
+    if (rc) return rc;
+    REQ(t >= 0, ICD2S_ERR_ARG, "t < 0");
+    cudaStream_t s = S(stream);
+    if ((rc = step_first(st, p, t, nullptr, s))) return rc;
+    CK(launch_colsum(st->d, counts_dev, s));
+    return ICD2S_OK;
+}
+
+int icd2s_step_shard_finish(icd2s_state* st, const icd2s_params* p, int32_t t, const int32_t* counts_dev,
+                            void* stream)
+{
+    REQ(st && p && counts_dev, ICD2S_ERR_ARG, "NULL argument");
+    int rc = check_params(st, p);
+    if (rc) return rc;
+    REQ(t >= 0, ICD2S_ERR_ARG, "t < 0");
+    return step_second(st, p, t, nullptr, S(stream), false, counts_dev);
+}
+
+int icd2s_get_best_info(icd2s_state* st, int64_t* E_best, int32_t* replica, int32_t* stamp)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    int64_t e = 0;
+    int32_t f[8] = {};
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(&e, st->best_E, 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(f, st->flags, sizeof f, cudaMemcpyDeviceToHost));
+    const bool any = e != INT64_MAX;
+    if (E_best) *E_best = e;
+    if (replica) *replica = any ? st->d.p0 + f[3] : -1;
+    if (stamp) *stamp = any ? f[7] : -1;
+    return ICD2S_OK;
 }
 
 int icd2s_step_host(icd2s_state* st, const icd2s_params* p, int32_t t, const uint8_t* x_in, uint8_t* x_out,

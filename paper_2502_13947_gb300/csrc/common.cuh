@@ -80,13 +80,19 @@ struct Dev {
     int32_t* FL; int32_t* FCNT; unsigned long long* DEACC; unsigned int* DONE;
     uint8_t* best_x; int64_t* best_E; int32_t* flags; // flags[0] improved, [1] stale, [2] error,
                                                        // [3] last best replica, [4] improved in the
-                                                       // finished iteration, [5] its log slot
+                                                       // finished iteration, [5] its log slot,
+                                                       // [6] a Tabu cluster exchange timed out,
+                                                       // [7] stamp of the last best update
     int32_t* H; float* F; float* score;
     int32_t* ACC; unsigned* TT; int apply_splits;     // split write-back: partial sums, tile tickets
     uint32_t k0, k1; // Philox key = seed halves
     long long gain_bound;  // max_j 2 sum_i |Q_ij| >= |g_j| for every x
     const int8_t* Q2;      // [2n][ld] signed rows: row 2i + x = (1 - 2x) Q_i (null unless asked for)
     uint16_t* TL; long long tl_cap;  // Tabu move logs [R][tl_cap] for searches whose log exceeds shared memory
+    // replica sharding: these R replicas are replicas p0 .. p0 + R - 1 of a set of
+    // z_total (every random stream is keyed by the global replica index; gamma is
+    // taken over all z_total replicas)
+    int p0, z_total;
 };
 
 // Counts kernel launches (process-wide, for reporting).
@@ -110,21 +116,32 @@ cudaError_t launch_pad_rows(const uint8_t* src, int n, int rows, uint8_t* dst, i
 // wide_keys: the two-reduction keys even where the compact ones apply;
 // rows: 0 = the default choice of plain or signed rows, 1 = plain rows (the sign
 // applied per variable), 2 = signed rows where d.Q2 exists.
+// cluster: CTAs per replica, 1, 2 or 4 (a thread-block cluster splitting the
+// variables; compact keys only, else one CTA), 0 = tabu_default_cluster.
 cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_t s, bool aspiration = false,
-                        bool wide_keys = false, int rows = 0);
+                        bool wide_keys = false, int rows = 0, int cluster = 1);
 // Shift of the compact Tabu keys for n and the instance's gain bound (0: they do not apply).
 int tabu_key_shift(int n, long long gain_bound);
 size_t tabu_smem_bytes(int n, int alpha);
 constexpr size_t kTabuSmemLimit = 227 * 1024;
 // false: the Tabu move log of alpha moves goes to global memory (Dev::TL, tl_cap >= alpha)
 bool tabu_log_in_smem(int n, int alpha);
-cudaError_t launch_gamma(const Dev& d, cudaStream_t s);
+int tabu_slice(int n, int G);
+int tabu_default_cluster(int n, int R, int sm_count);
+// gamma (Eq. 8) from column counts: counts[j] = sum over all d.z_total replicas of
+// x_pj (null: the counts of this state's own replicas, whose d.R must then be
+// d.z_total)
+cudaError_t launch_gamma(const Dev& d, const int32_t* counts, cudaStream_t s);
+// counts[j] = sum over this state's replicas of x_pj (j < n)
+cudaError_t launch_colsum(const Dev& d, int32_t* counts, cudaStream_t s);
 // Iteration context read by the kernels of a captured outer iteration (a CUDA
 // graph replays the same launches, so the iteration number and the mutation
 // rate come from device memory): iter_dev[0] = t, rates[t] = the rate.  When
 // iter_dev is null the kernels use their `iter` / `rate` arguments.
+// p0: global index of replica 0 (the sizes are drawn per global replica)
 cudaError_t launch_sizes(int R, int K, int m_min, int m_max, uint32_t k0, uint32_t k1, uint32_t iter,
-                         const int32_t* iter_dev, int32_t* off, int32_t* order, int32_t* queue, cudaStream_t s);
+                         const int32_t* iter_dev, int32_t* off, int32_t* order, int32_t* queue, cudaStream_t s,
+                         int p0 = 0);
 // mode: 0 rank S' by A; 1 by d.score; 2 by d.score on even replicas.  Hit
 // counts d.H are incremented for S' when count_hits.
 // ablation 2 (No_SM): A is replaced by the random key Philox(ctr = (j / 4, 7 << 24, p, t)) >> 1.
@@ -153,9 +170,9 @@ struct AnnealArgs {
                                           // by position
 };
 int device_sm_count();
-bool tabu_variant_fits(int variant, int n);
+bool tabu_variant_fits(int variant, int n, int G = 1);
 int tabu_num_variants();
-int tabu_default_variant(int n);
+int tabu_default_variant(int n, int G = 1);
 cudaError_t launch_anneal(const Dev& d, const AnnealArgs& a, cudaStream_t s);
 cudaError_t launch_exact(const Dev& d, const AnnealArgs& a, cudaStream_t s);  // exact IM, m <= 24
 cudaError_t launch_limtab(const uint32_t* beta, int sweeps, const uint32_t* nlog, int* lim, cudaStream_t s);
@@ -164,8 +181,12 @@ cudaError_t launch_apply(const Dev& d, cudaStream_t s);
 int apply_splits_for(int ld, int R);   // CTAs per column tile for long flip lists
 int apply_tiles(int ld);
 // log_ctl (iteration end only, may be null): {entries written, capacity} of the improvement log.
+// stamp: when this update happens (3 t + phase + 1 inside iteration t, 0
+// outside one; with iter_dev the t comes from *iter_dev); flags[7] keeps the
+// stamp of the update that last set the best, which orders equal energies of
+// different replica shards by the time they were reached.
 cudaError_t launch_best(const Dev& d, int64_t* trace_slot, int iter_end, int32_t* iter_dev, cudaStream_t s,
-                        int32_t* log_ctl = nullptr);
+                        int32_t* log_ctl = nullptr, int phase = -1, int t = 0);
 cudaError_t launch_set_iter(int32_t* iter_dev, int t, cudaStream_t s);
 // dense refresh on the tensor cores (kernels_refresh.cu)
 cudaError_t launch_to_bf16(const void* src, bool is_signed, size_t count, void* dst, cudaStream_t s);

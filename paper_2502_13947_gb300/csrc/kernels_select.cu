@@ -81,7 +81,7 @@ __host__ __device__ inline int next_pow2(int v)
 // the persistent anneal kernel, and resets its queue counter.
 __global__ __launch_bounds__(1024) void k_sizes(int R, int K, int m_min, int m_max, uint32_t k0, uint32_t k1,
                                                 uint32_t iter_arg, const int32_t* iter_dev, int32_t* off,
-                                                int32_t* order, int32_t* queue)
+                                                int32_t* order, int32_t* queue, int p0)
 {
     __shared__ int part[1024];
     __shared__ int start[kMaxM + 2];
@@ -93,7 +93,7 @@ __global__ __launch_bounds__(1024) void k_sizes(int R, int K, int m_min, int m_m
     const uint32_t span = (uint32_t)(m_max - m_min + 1);
     auto size_of = [&](int s) -> int {
         if (m_max == m_min) return m_min;
-        const int p = s / K, k = s % K;
+        const int p = p0 + s / K, k = s % K;   // the global replica
         const u32x4 w = philox10((uint32_t)k, kTagSize << 24, (uint32_t)p, iter, k0, k1);
         return m_min + (int)(w.v[0] % span);
     };
@@ -125,9 +125,10 @@ __global__ __launch_bounds__(1024) void k_sizes(int R, int K, int m_min, int m_m
 }
 
 cudaError_t launch_sizes(int R, int K, int m_min, int m_max, uint32_t k0, uint32_t k1, uint32_t iter,
-                         const int32_t* iter_dev, int32_t* off, int32_t* order, int32_t* queue, cudaStream_t s)
+                         const int32_t* iter_dev, int32_t* off, int32_t* order, int32_t* queue, cudaStream_t s,
+                         int p0)
 {
-    k_sizes<<<1, 1024, 0, s>>>(R, K, m_min, m_max, k0, k1, iter, iter_dev, off, order, queue);
+    k_sizes<<<1, 1024, 0, s>>>(R, K, m_min, m_max, k0, k1, iter, iter_dev, off, order, queue, p0);
     note_launch(1);
     return cudaGetLastError();
 }
@@ -161,7 +162,7 @@ __global__ __launch_bounds__(1024) void k_select(Dev d, int64_t w1, int64_t w2, 
             const int dl = mt > 0 ? (int)(((long long)(mt - t) * 65536) / mt) : 0;
             const long long v = w1 * (long long)d.etahat[j] + w2 * (long long)d.gamma[j] - w3 * (long long)dl;
             const int a = ablation == 2   // No_SM: a random ranking key instead of A
-                              ? (int)(philox10((uint32_t)(j >> 2), kTagRank << 24, (uint32_t)p, iter, d.k0,
+                              ? (int)(philox10((uint32_t)(j >> 2), kTagRank << 24, (uint32_t)(d.p0 + p), iter, d.k0,
                                                d.k1).v[j & 3] >> 1)
                               : (int)floor_div_65536(v);
             Arow[j] = a;
@@ -278,7 +279,7 @@ __global__ __launch_bounds__(1024) void k_mutate(Dev d, int K, const int32_t* __
             if (amax == amin || half) P = 2147483648ull;
             else P = ((unsigned long long)((long long)Arow[i] - amin) * 4294967295ull) /
                      (unsigned long long)((long long)amax - amin);
-            const u32x4 w = philox10((uint32_t)(i >> 2), kTagMut << 24, (uint32_t)p, iter, d.k0, d.k1);
+            const u32x4 w = philox10((uint32_t)(i >> 2), kTagMut << 24, (uint32_t)(d.p0 + p), iter, d.k0, d.k1);
             if ((unsigned long long)w.v[i & 3] < P) {
                 const int slot = atomicAdd(&d.FCNT[p], 1);
                 if (slot < ld) d.FL[(size_t)p * ld + slot] = i | (int)((unsigned)xrow[i] << 31);

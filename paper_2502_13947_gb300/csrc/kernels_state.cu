@@ -8,16 +8,17 @@ namespace icd2s {
 
 // ---------------------------------------------------------------------------
 // Generate_Initial_Solution_Set (Algorithm 2): x[p][j] is bit (j mod 32) of
-// word ((j / 32) mod 4) of Philox(ctr = (j / 128, TAG_INIT << 24, p, 0)).
+// word ((j / 32) mod 4) of Philox(ctr = (j / 128, TAG_INIT << 24, p, 0)), p
+// the global replica index (p0 + the local one).
 // One thread per (replica, 128 variables); padding bytes are written as 0.
 // ---------------------------------------------------------------------------
-__global__ void k_init_x(uint8_t* X, int n, int ld, int R, uint32_t k0, uint32_t k1)
+__global__ void k_init_x(uint8_t* X, int n, int ld, int R, int p0, uint32_t k0, uint32_t k1)
 {
     const int blocks = ld / 128;
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= R * blocks) return;
     const int p = gid / blocks, b = gid % blocks;
-    const u32x4 w = philox10((uint32_t)b, kTagInit << 24, (uint32_t)p, 0u, k0, k1);
+    const u32x4 w = philox10((uint32_t)b, kTagInit << 24, (uint32_t)(p0 + p), 0u, k0, k1);
     uint8_t* row = X + (size_t)p * ld + (size_t)b * 128;
 #pragma unroll
     for (int v = 0; v < 8; ++v) {   // 8 x 16 bytes
@@ -41,7 +42,7 @@ __global__ void k_init_x(uint8_t* X, int n, int ld, int R, uint32_t k0, uint32_t
 cudaError_t launch_init_x(const Dev& d, cudaStream_t s)
 {
     const int total = d.R * (d.ld / 128);
-    k_init_x<<<(total + 127) / 128, 128, 0, s>>>(d.X, d.n, d.ld, d.R, d.k0, d.k1);
+    k_init_x<<<(total + 127) / 128, 128, 0, s>>>(d.X, d.n, d.ld, d.R, d.p0, d.k0, d.k1);
     note_launch(1);
     return cudaGetLastError();
 }
@@ -178,22 +179,46 @@ cudaError_t launch_pad_rows(const uint8_t* src, int n, int rows, uint8_t* dst, i
 
 // ---------------------------------------------------------------------------
 // Deviation_Extraction (Eq. 8): gamma_j = 1 - |sum_p x_pj - z/2| / (z/2)
-//                                       = (z - |2 sum_p x_pj - z|) / z, Q16 floor.
+//                                       = (z - |2 sum_p x_pj - z|) / z, Q16 floor,
+// the sum over all z replicas: this state's own (counts == null), or the
+// column counts of every replica shard added up by the caller.
 // ---------------------------------------------------------------------------
-__global__ void k_gamma(const uint8_t* __restrict__ X, int n, int ld, int R, int32_t* __restrict__ gamma)
+__global__ void k_gamma(const uint8_t* __restrict__ X, int n, int ld, int R, const int32_t* __restrict__ counts,
+                        int z, int32_t* __restrict__ gamma)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= ld) return;
     if (j >= n) { gamma[j] = 0; return; }
     int col = 0;
-    for (int p = 0; p < R; ++p) col += X[(size_t)p * ld + j];
-    const int dev = abs(2 * col - R);
-    gamma[j] = (int32_t)(((long long)(R - dev) * 65536) / R);
+    if (counts) {
+        col = counts[j];
+    } else {
+        for (int p = 0; p < R; ++p) col += X[(size_t)p * ld + j];
+    }
+    const int dev = abs(2 * col - z);
+    gamma[j] = (int32_t)(((long long)(z - dev) * 65536) / z);
 }
 
-cudaError_t launch_gamma(const Dev& d, cudaStream_t s)
+cudaError_t launch_gamma(const Dev& d, const int32_t* counts, cudaStream_t s)
 {
-    k_gamma<<<(d.ld + 255) / 256, 256, 0, s>>>(d.X, d.n, d.ld, d.R, d.gamma);
+    k_gamma<<<(d.ld + 255) / 256, 256, 0, s>>>(d.X, d.n, d.ld, d.R, counts, counts ? d.z_total : d.R, d.gamma);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
+// column counts of this state's replicas (the shard's part of Eq. 8's sum)
+__global__ void k_colsum(const uint8_t* __restrict__ X, int n, int ld, int R, int32_t* __restrict__ counts)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int col = 0;
+    for (int p = 0; p < R; ++p) col += X[(size_t)p * ld + j];
+    counts[j] = col;
+}
+
+cudaError_t launch_colsum(const Dev& d, int32_t* counts, cudaStream_t s)
+{
+    k_colsum<<<(d.ld + 255) / 256, 256, 0, s>>>(d.X, d.n, d.ld, d.R, counts);
     note_launch(1);
     return cudaGetLastError();
 }
@@ -210,7 +235,7 @@ cudaError_t launch_gamma(const Dev& d, cudaStream_t s)
 __global__ __launch_bounds__(256) void k_best(const uint8_t* __restrict__ X, int ld, const int64_t* __restrict__ E,
                                               int R, uint8_t* best_x, int64_t* best_E, int32_t* flags,
                                               int64_t* trace_slot, int iter_end, int32_t* iter_dev,
-                                              int32_t* log_ctl)
+                                              int32_t* log_ctl, int phase, int t_arg)
 {
     __shared__ long long sE[8];
     __shared__ int sP[8];
@@ -235,7 +260,10 @@ __global__ __launch_bounds__(256) void k_best(const uint8_t* __restrict__ X, int
             if (sE[w] < me || (sE[w] == me && sP[w] < mp)) { me = sE[w]; mp = sP[w]; }
         const long long cur = *best_E;
         s_win = (me < cur) ? mp : -1;
-        if (s_win >= 0) { *best_E = me; flags[0] = 1; flags[3] = mp; }
+        if (s_win >= 0) {
+            *best_E = me; flags[0] = 1; flags[3] = mp;
+            flags[7] = phase < 0 ? 0 : 3 * (iter_dev ? *iter_dev : t_arg) + phase + 1;
+        }
     }
     __syncthreads();
     const int win = s_win;
@@ -256,10 +284,10 @@ __global__ __launch_bounds__(256) void k_best(const uint8_t* __restrict__ X, int
 }
 
 cudaError_t launch_best(const Dev& d, int64_t* trace_slot, int iter_end, int32_t* iter_dev, cudaStream_t s,
-                        int32_t* log_ctl)
+                        int32_t* log_ctl, int phase, int t)
 {
     k_best<<<1, 256, 0, s>>>(d.X, d.ld, d.E, d.R, d.best_x, d.best_E, d.flags, trace_slot, iter_end, iter_dev,
-                             log_ctl);
+                             log_ctl, phase, t);
     note_launch(1);
     return cudaGetLastError();
 }

@@ -36,7 +36,8 @@ EXPORTS = (
     "icd2s_mlp_score", "icd2s_mlp_grad", "icd2s_mlp_train", "icd2s_state_set_mlp", "icd2s_get_features",
     "icd2s_get_hits", "icd2s_log_enable", "icd2s_log_info", "icd2s_log_copy", "icd2s_get_apply_ms",
     "icd2s_exact_subqubos_batch", "icd2s_tabu_aspiration", "icd2s_state_save", "icd2s_checkpoint_info",
-    "icd2s_state_restore", "icd2s_debug_fail_allocations_after",
+    "icd2s_state_restore", "icd2s_debug_fail_allocations_after", "icd2s_state_create_shard",
+    "icd2s_step_shard_begin", "icd2s_step_shard_finish", "icd2s_get_best_info",
 )
 MLP_PARAMS = 4673
 PHASES = ("tabu", "select", "anneal", "apply_anneal", "mutate", "apply_mutate", "best")
@@ -110,6 +111,10 @@ def lib():
                 "icd2s_qubo_gain_bound": (C.c_int, [vp, P(C.c_int64)]),
                 "icd2s_energy": (C.c_int, [vp, vp, i32, vp, vp]),
                 "icd2s_state_create": (C.c_int, [vp, i32, u64, P(vp)]),
+                "icd2s_state_create_shard": (C.c_int, [vp, i32, i32, i32, u64, P(vp)]),
+                "icd2s_step_shard_begin": (C.c_int, [vp, P(Params), i32, vp, vp]),
+                "icd2s_step_shard_finish": (C.c_int, [vp, P(Params), i32, vp, vp]),
+                "icd2s_get_best_info": (C.c_int, [vp, P(C.c_int64), P(i32), P(i32)]),
                 "icd2s_state_destroy": (C.c_int, [vp]),
                 "icd2s_state_load": (C.c_int, [vp, vp, i32, vp]),
                 "icd2s_get_state": (C.c_int, [vp, vp, vp, vp]),
@@ -239,10 +244,12 @@ def icd2s_state_load(st, x, x_is_device: bool = False, stream=0) -> None:
         _check(lib().icd2s_state_load(st, _np(x), 0, _s(stream)))
 
 
-def icd2s_get_state(st, R: int, n: int):
-    x = np.zeros((R, n), np.uint8)
-    g = np.zeros((R, n), np.int32)
-    E = np.zeros(R, np.int64)
+def icd2s_get_state(st, R: int, n: int, x=None, E=None, want_g: bool = True):
+    """Host copies of the solutions, gains and energies (x / E may be given:
+    uint8 [R][n] / int64 [R] arrays, e.g. pinned; want_g=False skips g)."""
+    x = np.zeros((R, n), np.uint8) if x is None else x
+    g = np.zeros((R, n), np.int32) if want_g else None
+    E = np.zeros(R, np.int64) if E is None else E
     _check(lib().icd2s_get_state(st, _np(x), _np(g), _np(E)))
     return x, g, E
 
@@ -252,6 +259,21 @@ def icd2s_get_best(st, n: int):
     E = np.zeros(1, np.int64)
     _check(lib().icd2s_get_best(st, _np(x), _np(E)))
     return x, int(E[0])
+
+
+def icd2s_get_best_info(st):
+    """(best energy, its global replica index, the stamp of the update that set it)."""
+    E, r, t = C.c_int64(), C.c_int32(), C.c_int32()
+    _check(lib().icd2s_get_best_info(st, C.byref(E), C.byref(r), C.byref(t)))
+    return int(E.value), int(r.value), int(t.value)
+
+
+def icd2s_state_create_shard(q, replicas: int, replica_base: int, replicas_total: int, seed: int) -> C.c_void_p:
+    """Replicas replica_base .. replica_base + replicas - 1 of a set of replicas_total."""
+    h = C.c_void_p()
+    _check(lib().icd2s_state_create_shard(q, replicas, replica_base, replicas_total, C.c_uint64(seed),
+                                          C.byref(h)))
+    return h
 
 
 def icd2s_state_save(st, t_next: int) -> bytes:
@@ -341,6 +363,16 @@ def icd2s_initial_pass(st, p: Params, stream=0) -> None:
 
 def icd2s_step(st, p: Params, t: int, stream=0) -> None:
     _check(lib().icd2s_step(st, C.byref(p), t, _s(stream)))
+
+
+def icd2s_step_shard_begin(st, p: Params, t: int, counts_dev: int, stream=0) -> None:
+    """First half of iteration t on a replica shard; writes its column counts (int32 [n], device)."""
+    _check(lib().icd2s_step_shard_begin(st, C.byref(p), t, C.c_void_p(counts_dev), _s(stream)))
+
+
+def icd2s_step_shard_finish(st, p: Params, t: int, counts_dev: int, stream=0) -> None:
+    """Rest of iteration t, with gamma from the column counts of every shard (int32 [n], device)."""
+    _check(lib().icd2s_step_shard_finish(st, C.byref(p), t, C.c_void_p(counts_dev), _s(stream)))
 
 
 def icd2s_step_host(st, p: Params, t: int, x_in=None, x_out=None, E_out=None, stream=0) -> None:
@@ -503,21 +535,23 @@ def icd2s_apply_flips_static(Q_dev: int, n: int, ld: int, replicas: int, flips_d
 class Tuning(C.Structure):
     _fields_ = [("tabu_variant", C.c_int32), ("anneal_warps_per_cta", C.c_int32), ("refresh_bn", C.c_int32),
                 ("refresh_splits", C.c_int32), ("tabu_wide_keys", C.c_int32),
-                ("tabu_rows", C.c_int32), ("anneal_scheme", C.c_int32), ("refresh_kind", C.c_int32)]
+                ("tabu_rows", C.c_int32), ("anneal_scheme", C.c_int32), ("refresh_kind", C.c_int32),
+                ("tabu_cluster", C.c_int32)]
 
 
 def _tuning_dict(t):
     return dict(tabu_variant=t.tabu_variant, anneal_warps_per_cta=t.anneal_warps_per_cta,
                 refresh_bn=t.refresh_bn, refresh_splits=t.refresh_splits, tabu_wide_keys=t.tabu_wide_keys,
-                tabu_rows=t.tabu_rows, anneal_scheme=t.anneal_scheme, refresh_kind=t.refresh_kind)
+                tabu_rows=t.tabu_rows, anneal_scheme=t.anneal_scheme, refresh_kind=t.refresh_kind,
+                tabu_cluster=t.tabu_cluster)
 
 
 def icd2s_set_tuning(st, tabu_variant: int = -1, anneal_warps_per_cta: int = 0, refresh_bn: int = 0,
                      refresh_splits: int = 0, tabu_wide_keys: int = 0, tabu_rows: int = 0,
-                     anneal_scheme: int = 0, refresh_kind: int = 0) -> None:
+                     anneal_scheme: int = 0, refresh_kind: int = 0, tabu_cluster: int = 0) -> None:
     t = Tuning(tabu_variant=tabu_variant, anneal_warps_per_cta=anneal_warps_per_cta, refresh_bn=refresh_bn,
                refresh_splits=refresh_splits, tabu_wide_keys=tabu_wide_keys, tabu_rows=tabu_rows,
-               anneal_scheme=anneal_scheme, refresh_kind=refresh_kind)
+               anneal_scheme=anneal_scheme, refresh_kind=refresh_kind, tabu_cluster=tabu_cluster)
     _check(lib().icd2s_set_tuning(st, C.byref(t)))
 
 

@@ -228,3 +228,25 @@ def test_run_with_a_move_log_beyond_shared_memory(L, orc):
     lp = lib_params(I, n, z=2, K=1, m_min=32, m_max=32, m_init=32, alpha=400 * n, c=5, sweeps=16,
                     T_max=1500.0, mut_mode=0, patience=0, max_iters=2)
     _compare_runs(orc, Q, lp, 45)
+
+
+@pytest.mark.parametrize("n,K,use_graph,G", [(2400, 4, 1, 2), (4200, 1, 0, 4), (8300, 2, 1, 0)])
+def test_run_with_the_tabu_search_split_over_clusters(L, orc, n, K, use_graph, G):
+    """Few replicas of a large instance with each replica's Tabu search split
+    over a cluster of 2 or 4 CTAs (n = 8300: the default split, 4); the whole
+    run (two of them replayed as a CUDA graph) equals the oracle's."""
+    Q = make_qubo(n, 0.3, 23)
+    lp = lib_params(I, n, z=3, K=K, m_min=16, m_max=64, m_init=64, alpha=n, c=max(2, n // 150), sweeps=16,
+                    T_max=2000.0, mut_mode=0, patience=0, max_iters=3 if n < 8000 else 2, use_graph=use_graph)
+    q = I.icd2s_qubo_create(Q)
+    st = I.icd2s_state_create(q, lp.z, 29)
+    try:
+        I.icd2s_set_tuning(st, tabu_cluster=G)
+        g = I.icd2s_state_run(st, n, lp, trace=True, want_S=True)
+    finally:
+        I.icd2s_state_destroy(st)
+        I.icd2s_qubo_destroy(q)
+    o = orc.run(Q, orc_params(orc, lp), 29)
+    assert g["iters"] == o["iters"] and np.array_equal(g["trace"], o["trace"])
+    assert np.array_equal(g["S"], o["S"])
+    assert g["best_E"] == o["best_E"] and np.array_equal(g["best_x"], o["best_x"])
