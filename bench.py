@@ -10,6 +10,9 @@ step time (sweeps x subQUBO size x subQUBOs per step / step time).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--workload NAME]
   python bench.py --ttt [--ttt-seeds S] [--ttt-budget ITERS] [--ttt-instances a,b]
 
+The line also carries a time-to-target block (`ttt`, the metric's second
+half): learned / batched selection against the plain method on the n = 5000,
+50 % density instance, device-timed, 10 seeds.
 The default workload is the Beasley-shaped instance (n = 2500, 10 % density,
 int8 entries in [-100, 100]) with 128 replicas, subQUBOs of 64, 1024 sweeps,
 alpha = 5n, c = 16 and a 1 % mutation rate.  Inputs are resident in HBM when
@@ -97,9 +100,9 @@ def measured_peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
-def ncu_traffic(kernel_file, kernel):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel's
-    source is unchanged since the capture (else None)."""
+def ncu_traffic(kernel_file, kernel, field="dram_bytes_per_launch"):
+    """A per-launch counter (DRAM bytes by default) from the committed ncu
+    summary, if the kernel's source is unchanged since the capture (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             tab = json.load(f)
@@ -108,7 +111,7 @@ def ncu_traffic(kernel_file, kernel):
             return None
         src = os.path.join(ROOT, "paper_2502_13947_gb300", "csrc", kernel_file)
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        return ent["dram_bytes_per_launch"] if ent.get("source_sha256") == h else None
+        return ent.get(field) if ent.get("source_sha256") == h else None
     except (OSError, KeyError, ValueError):
         return None
 
@@ -249,6 +252,50 @@ def measure_refresh(I, torch, peaks, stream, flush, reps=10):
             "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": 2 * n * ld + 2 * R * ld + 4 * R * ld,
             "launch_ms": ms, "refresh_call_ms": sum(whole) / len(whole), "mismatches": bad,
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst: the kernel is timed alone)"}
+
+
+# The dense-refresh workload as a whole: Ising-machine rounds (selection, one
+# batched anneal launch of R x K uneven subQUBOs, exact write-back) on the dense
+# n = 7000 instance with 256 replicas, and every 64 rounds a tensor-core refresh
+# of all gains and energies that checks the tracked values.
+C4_WORKLOAD = dict(name="dense-n7000-d1.0-R256-K16-m32..256-refresh-every-64-rounds", n=7000, density=1.0, qseed=7,
+                   z=256, K=16, m_min=32, m_max=256, sweeps=256, rounds=64)
+
+
+def measure_c4(I, torch, stream):
+    """Device time of 64 Ising-machine rounds and of the refresh that follows
+    them (CUDA events on the launching stream), the refresh's share, and the
+    anneal's attempt rate over the rounds."""
+    w = C4_WORKLOAD
+    n, R = w["n"], w["z"]
+    q = I.icd2s_qubo_create(make_qubo(n, w["density"], w["qseed"]))
+    st = I.icd2s_state_create(q, R, 5)
+    p = I.icd2s_default_params(n, z=R, K=w["K"], m_min=w["m_min"], m_max=w["m_max"], m_init=64, sweeps=w["sweeps"])
+    sp = stream.cuda_stream
+    try:
+        with torch.cuda.stream(stream):
+            I.icd2s_tabu(st, n, p.c, sp)              # toggle counts for Delta (Eq. 7)
+            I.icd2s_im_round(st, p, 0, sp)             # warm-up (tables, buffers)
+            bad = I.icd2s_refresh(st, False, sp)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            for r in range(w["rounds"]):
+                I.icd2s_im_round(st, p, 1 + r, sp)
+            ev[1].record(stream)
+        bad += I.icd2s_refresh(st, False, sp)         # the drift check (synchronises)
+        with torch.cuda.stream(stream):
+            ev[2].record(stream)
+        ev[2].synchronize()
+    finally:
+        I.icd2s_state_destroy(st)
+        I.icd2s_qubo_destroy(q)
+    rounds_ms, refresh_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    attempts = w["rounds"] * R * w["K"] * w["sweeps"] * (w["m_min"] + w["m_max"]) / 2.0   # mean size
+    return {"workload": w["name"], "rounds": w["rounds"], "rounds_ms": rounds_ms, "round_ms": rounds_ms / w["rounds"],
+            "refresh_call_ms": refresh_ms, "refresh_share": refresh_ms / (rounds_ms + refresh_ms),
+            "anneal_attempts_per_s_expected_sizes": attempts / (rounds_ms / 1000.0), "mismatches": bad,
+            "note": "a round = selection + one batched anneal launch + write-back; the refresh checks all "
+                    "256 x 7000 gains and 256 energies (0 mismatches expected)"}
 
 
 APPLY_WORKLOAD = dict(name="gain-update-n16384-R16-disjoint1024", n=16384, density=1.0, qseed=5, R=16)
@@ -456,6 +503,7 @@ def run_gpu(args, w):
     peaks, peak_src = measured_peaks()
     refresh = None if args.no_refresh else measure_refresh(I, torch, peaks, stream, flush)
     apply_rf = None if args.no_refresh else measure_apply(I, torch, peaks, stream, flush)
+    c4 = None if args.no_refresh else measure_c4(I, torch, stream)
     K = args.steps
     phase_avg = {k: v / K for k, v in phase_tot.items()}
     ld = (n + 127) // 128 * 128
@@ -470,6 +518,29 @@ def run_gpu(args, w):
                 "algorithmic_bytes_per_launch": tabu_bytes, "launch_ms": phase_avg["tabu"],
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src}
     anneal_rate = att / (phase_avg["anneal"] / 1000.0)
+    # The Ising machine's anneal (a7): a sequential Metropolis chain per subQUBO,
+    # bound by integer issue.  Warp instructions per attempt come from the ncu
+    # capture of one launch (profiles/); the peak is every SM sub-partition
+    # issuing one warp instruction per cycle at the sampled SM clock.
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    inst = ncu_traffic("kernels_anneal.cu", "k_anneal", "warp_instructions_per_launch")
+    positions_per_warp = w["sweeps"] * w["m_max"]   # one warp per subQUBO of m_max positions (m_min == m_max)
+    roofline_anneal = {
+        "kernel": "k_anneal", "bound": "alu", "unit": "G warp-instructions/s",
+        "peak": sms * 4 * mhz / 1000.0,
+        "peak_rule": "%d SMs x 4 sub-partitions x 1 warp instruction per cycle x %.0f MHz (sampled SM clock)" % (
+            sms, mhz),
+        "attempts_per_s": anneal_rate,
+        "cycles_per_position": phase_avg["anneal"] / 1000.0 * mhz * 1e6 / positions_per_warp,
+        "warp_instructions_per_attempt": (inst / att) if inst else None,
+        "achieved": (inst / att * anneal_rate / 1e9) if inst else None,
+        "warps": z * w["K"],
+        "note": "one warp per subQUBO: %d warps can use at most %d of the %d sub-partitions" % (
+            z * w["K"], min(z * w["K"], sms * 4), sms * 4),
+    }
+    roofline_anneal["frac"] = (roofline_anneal["achieved"] / roofline_anneal["peak"]
+                               if roofline_anneal["achieved"] else None)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -478,6 +549,7 @@ def run_gpu(args, w):
                "sample": "one whole outer iteration of the workload (all %d replicas), single-threaded C oracle, "
                          "%.1f s" % (z, dt)}
         cpu.update(n_core_ideal(a / dt))
+    ttt = None if (args.no_ttt or world > 1) else ttt_block(I, torch)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -500,6 +572,9 @@ def run_gpu(args, w):
         "clocks": clk,
         "phase_ms": phase_avg,
         "anneal_kernel_attempts_per_s": anneal_rate,
+        "roofline_anneal": roofline_anneal,
+        "c4": c4,
+        "ttt": ttt,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -532,8 +607,12 @@ TTT_METHODS = {  # (K, m_min, m_max, select_mode, ablation, im_order, alpha / n)
                                                   # alpha = 20n the paper gives the Tabu-only solver
 }
 # improvement logs of the plain method for training: shapes of the n = 64
-# dense, n = 2500 sparse and n = 5000 batched workloads, instance seeds 200+
-TTT_LOG_SHAPES = ((64, 1.0, 8, 1, 16, 16, 200), (2500, 0.1, 128, 1, 64, 64, 40), (5000, 0.5, 32, 16, 32, 256, 40))
+# dense, n = 2500 sparse and n = 5000 batched workloads, and the plain method in
+# the time-to-target block's regime (n = 5000, alpha = n); instance seeds 200+,
+# never the measured instance.  Fields: n, density, z, K, m_min, m_max,
+# iterations, alpha / n.
+TTT_LOG_SHAPES = ((64, 1.0, 8, 1, 16, 16, 200, 5), (2500, 0.1, 128, 1, 64, 64, 40, 5),
+                  (5000, 0.5, 32, 16, 32, 256, 40, 5), (5000, 0.5, 32, 1, 64, 64, 40, 1))
 
 
 def ttt_params(I, n, K, m_min, m_max, mode, iters, z=32):
@@ -547,11 +626,12 @@ def ttt_params(I, n, K, m_min, m_max, mode, iters, z=32):
 def ttt_train(I, torch, steps=3000, batch=8192, runs=4):
     """Collects improvement logs of plain runs and trains the network on the GPU."""
     Fs, ys, entries = [], [], 0
-    for (n, rho, z, K, m_min, m_max, iters) in TTT_LOG_SHAPES:
+    for (n, rho, z, K, m_min, m_max, iters, amul) in TTT_LOG_SHAPES:
         for r in range(runs):
             q = I.icd2s_qubo_create(make_qubo(n, rho, 200 + r))
             p = ttt_params(I, n, K, m_min, m_max, 0, iters, z=z)
             p.m_init = min(m_max, 64)
+            p.alpha = amul * n
             st = I.icd2s_state_create(q, z, 200 + r)
             I.icd2s_log_enable(st, 512)
             I.icd2s_state_run(st, n, p)
@@ -579,6 +659,92 @@ def ttt_train(I, torch, steps=3000, batch=8192, runs=4):
     return m, info
 
 
+def ttt_target(I, q, n, budget, alpha_mult=5):
+    """E* of an instance: the best energy of three plain runs ten times as long as
+    the measured ones (run seeds 100-102)."""
+    longs = []
+    for s in (100, 101, 102):
+        p = ttt_params(I, n, 1, 64, 64, 0, 10 * budget)
+        p.alpha = alpha_mult * n
+        longs.append(I.icd2s_run(q, p, s)["best_E"])
+    return min(longs), longs
+
+
+def ttt_methods(I, q, n, mlp, E_star, methods, seeds, budget, alpha_mult=None):
+    """Every method from run seeds 0..seeds-1 until best <= E* or the budget is
+    spent: device time to the target (CUDA events, Call_IM_Solution_Set
+    included), hits, iterations.  alpha_mult overrides each method's alpha / n."""
+    res = {}
+    for meth in methods:
+        K, m_min, m_max, mode, ablation, order, amul = TTT_METHODS[meth]
+        per = []
+        for seed in range(seeds):
+            p = ttt_params(I, n, K, m_min, m_max, mode, budget)
+            p.ablation, p.im_order, p.alpha = ablation, order, (alpha_mult or amul) * n
+            p.stop_at_target, p.target_E = 1, E_star
+            st = I.icd2s_state_create(q, p.z, seed)
+            if mode:
+                I.icd2s_state_set_mlp(st, mlp)
+            r = I.icd2s_state_run(st, n, p)
+            I.icd2s_state_destroy(st)
+            per.append(dict(seed=seed, hit_iter=r["hit_iter"], ttt_ms=round(r["ttt_ms"], 2), best_E=r["best_E"],
+                            ms_per_iter=round(r["device_ms"] / max(r["iters"], 1), 2)))
+        hits = [x["ttt_ms"] for x in per if x["hit_iter"] >= 0]
+        cens = sorted(hits + [float("inf")] * (len(per) - len(hits)))
+        med = cens[len(cens) // 2] if len(cens) % 2 else 0.5 * (cens[len(cens) // 2 - 1] + cens[len(cens) // 2])
+        its = sorted(x["hit_iter"] + 1 if x["hit_iter"] >= 0 else budget + 1 for x in per)
+        res[meth] = dict(median_ttt_ms=None if med == float("inf") else round(med, 2),
+                         success=len(hits), runs=len(per), median_iterations=its[len(its) // 2],
+                         mean_ms_per_iter=round(statistics.mean(x["ms_per_iter"] for x in per), 2),
+                         per_seed=per)
+    return res
+
+
+# the time-to-target block of the default bench line: n = 5000, 50 % density,
+# a Tabu search of alpha = n per iteration, so that the plain method needs
+# several iterations to reach E* (with alpha = 5n every method reaches it in
+# one to four)
+TTT_DEFAULT = dict(instance="n5000-d0.5", methods=("plain", "learned", "batched", "learned+batched", "batched K=4",
+                                                   "learned+batched K=4"), seeds=10, budget=30, alpha_mult=1)
+
+
+def ttt_block(I, torch):
+    """Time to target of learned / batched selection against the plain method
+    (the default bench line's second metric)."""
+    t0 = time.time()
+    mlp, train_info = ttt_train(I, torch)
+    spec = TTT_INSTANCES[TTT_DEFAULT["instance"]]
+    n, am, budget = spec["n"], TTT_DEFAULT["alpha_mult"], TTT_DEFAULT["budget"]
+    q = I.icd2s_qubo_create(make_qubo(n, spec["density"], spec["qseed"]))
+    try:
+        E_star, longs = ttt_target(I, q, n, budget, am)
+        res = ttt_methods(I, q, n, mlp, E_star, TTT_DEFAULT["methods"], TTT_DEFAULT["seeds"], budget, am)
+    finally:
+        I.icd2s_qubo_destroy(q)
+        I.icd2s_mlp_destroy(mlp)
+    summary = {}
+    for m, r in res.items():
+        per = r.pop("per_seed")
+        r["iterations"] = [x["hit_iter"] + 1 if x["hit_iter"] >= 0 else -1 for x in per]  # per seed, -1 = miss
+        summary[m] = r
+    def beats(a, b):   # more runs reach E*, or as many and a lower median device time
+        return bool(a["success"] > b["success"] or
+                    (a["success"] == b["success"] and a["median_ttt_ms"] is not None and
+                     (b["median_ttt_ms"] is None or a["median_ttt_ms"] < b["median_ttt_ms"])))
+    pl = summary["plain"]
+    better = {"K=16": beats(summary["learned+batched"], pl), "K=4": beats(summary["learned+batched K=4"], pl)}
+    network = {"K=1": beats(summary["learned"], pl), "K=16": beats(summary["learned+batched"], summary["batched"]),
+               "K=4": beats(summary["learned+batched K=4"], summary["batched K=4"])}
+    return {"metric": "time-to-target energy", "unit": "ms", "higher_is_better": False,
+            "instance": TTT_DEFAULT["instance"], "target_E": E_star, "target_runs": longs,
+            "target_rule": "best of 3 plain runs of 10x the budget (seeds 100-102)",
+            "params": "z=32, alpha=%dn, c=n/150, 256 sweeps, T 2000->1, Eq. 5 mutation; learned / batched as in "
+                      "--ttt" % am,
+            "seeds": TTT_DEFAULT["seeds"], "budget_iters": budget, "methods": summary,
+            "learned_batched_beats_plain": better, "learned_beats_same_batch_without_network": network,
+            "train": train_info, "wall_s": round(time.time() - t0, 1)}
+
+
 def run_ttt(args):
     import torch
     from paper_2502_13947_gb300 import icd2s as I
@@ -592,32 +758,9 @@ def run_ttt(args):
         spec = TTT_INSTANCES[name]
         n = spec["n"]
         q = I.icd2s_qubo_create(make_qubo(n, spec["density"], spec["qseed"]))
-        longs = []
-        for s in (100, 101, 102):
-            r = I.icd2s_run(q, ttt_params(I, n, 1, 64, 64, 0, 10 * args.ttt_budget), s)
-            longs.append(r["best_E"])
-        E_star = min(longs)
+        E_star, longs = ttt_target(I, q, n, args.ttt_budget)
         res = dict(target_E=E_star, target_runs=longs, budget_iters=args.ttt_budget)
-        for meth, (K, m_min, m_max, mode, ablation, order, amul) in TTT_METHODS.items():
-            per = []
-            for seed in range(args.ttt_seeds):
-                p = ttt_params(I, n, K, m_min, m_max, mode, args.ttt_budget)
-                p.ablation, p.im_order, p.alpha = ablation, order, amul * n
-                p.stop_at_target, p.target_E = 1, E_star
-                st = I.icd2s_state_create(q, p.z, seed)
-                if mode:
-                    I.icd2s_state_set_mlp(st, mlp)
-                r = I.icd2s_state_run(st, n, p)
-                I.icd2s_state_destroy(st)
-                per.append(dict(seed=seed, hit_iter=r["hit_iter"], ttt_ms=round(r["ttt_ms"], 2), best_E=r["best_E"],
-                                ms_per_iter=round(r["device_ms"] / max(r["iters"], 1), 2)))
-            hits = [x["ttt_ms"] for x in per if x["hit_iter"] >= 0]
-            cens = sorted(hits + [float("inf")] * (len(per) - len(hits)))
-            med = cens[len(cens) // 2] if len(cens) % 2 else 0.5 * (cens[len(cens) // 2 - 1] + cens[len(cens) // 2])
-            res[meth] = dict(median_ttt_ms=None if med == float("inf") else round(med, 2),
-                             success=len(hits), runs=len(per),
-                             mean_ms_per_iter=round(statistics.mean(x["ms_per_iter"] for x in per), 2),
-                             per_seed=per)
+        res.update(ttt_methods(I, q, n, mlp, E_star, list(TTT_METHODS), args.ttt_seeds, args.ttt_budget))
         I.icd2s_qubo_destroy(q)
         results[name] = res
     I.icd2s_mlp_destroy(mlp)
@@ -698,6 +841,7 @@ def main():
                     help="skip the tensor-core refresh and the write-back roofline measurements")
     ap.add_argument("--only", choices=["apply", "refresh"], help="run one kernel measurement alone (profiling)")
     ap.add_argument("--ttt", action="store_true", help="time to target: learned / batched vs plain selection")
+    ap.add_argument("--no-ttt", action="store_true", help="leave the time-to-target block out of the bench line")
     ap.add_argument("--ttt-seeds", type=int, default=10)
     ap.add_argument("--ttt-budget", type=int, default=30, help="outer iterations per measured run")
     ap.add_argument("--ttt-instances", default="n5000-d0.5,n10000-d0.5")

@@ -337,8 +337,11 @@ int icd2s_best_update(icd2s_state* st, void* stream);
  * x, since every partial sum is an integer below 2^24), and compares them with
  * the incrementally tracked values.  mismatches (host, may be NULL) receives
  * the number of differing entries and synchronises `stream`; rebuild != 0
- * replaces the tracked values with the recomputed ones.  ICD2S_ERR_TIMEOUT if
- * a bounded device-side wait gave up. */
+ * replaces the tracked values with the recomputed ones (after checking,
+ * synchronously, that the recompute completed).  ICD2S_ERR_TIMEOUT if a
+ * bounded device-side wait of the tensor-core pipeline gave up (reported when
+ * mismatches or rebuild is given); the tracked values are then left alone and
+ * the state stays usable. */
 int icd2s_refresh(icd2s_state* st, int32_t rebuild, int32_t* mismatches, void* stream);
 
 /* Call_IM_Solution_Set (Algorithm 2): for each replica, floor(n / m_init)
@@ -354,6 +357,16 @@ int icd2s_initial_pass(icd2s_state* st, const icd2s_params* p, void* stream);
  * parameters, selection, Ising machine, write-back, mutation, best update.
  * Enqueued on `stream`; no host synchronisation. */
 int icd2s_step(icd2s_state* st, const icd2s_params* p, int32_t t, void* stream);
+
+/* One Ising-machine round (Algorithm 2's IM step alone): control parameters
+ * and selection of the K subQUBOs per replica (Algorithm 3-4, Eq. 6-8, with
+ * Delta from the last Tabu search's toggle counts), the batched anneal of all
+ * replicas * K subQUBOs in one launch (Eq. 4; uneven sizes through the
+ * persistent queue kernel) and the exact write-back of the flips into x, g
+ * and E.  Iteration number t keys the random streams.  Enqueued on `stream`;
+ * no host synchronisation.  A dense workload's drift check alternates rounds
+ * with icd2s_refresh. */
+int icd2s_im_round(icd2s_state* st, const icd2s_params* p, int32_t t, void* stream);
 
 /* Outer iteration t on a replica shard, in two calls enqueued on `stream`.
  * _begin runs the Tabu search (Algorithm 1), the best update after it, the
@@ -492,7 +505,8 @@ typedef struct icd2s_tuning {
     int32_t tabu_variant;
     int32_t anneal_warps_per_cta;
     int32_t refresh_bn;       /* tensor-core refresh: replicas per tile (128 or 256; 0 = default) */
-    int32_t refresh_splits;   /* tensor-core refresh: K splits (0 = about one CTA per SM) */
+    int32_t refresh_splits;   /* tensor-core refresh: kinds 1 and 4, persistent CTAs (0 = one
+                                 per SM); kind 3, K splits (0 = about one CTA per SM) */
     int32_t tabu_wide_keys;   /* 0 = compact Tabu keys where they apply, 1 = never */
     int32_t tabu_rows;        /* 0 = default (plain rows), 1 = plain rows, 2 = signed row pairs */
     int32_t anneal_scheme;    /* sweep of the Ising-machine kernel (every scheme gives the same
@@ -501,8 +515,10 @@ typedef struct icd2s_tuning {
                                  test taken for both outcomes, 4 = per sweep either 1 or by
                                  position (2 up to 64 variables, 3 beyond), whichever the
                                  previous sweep's accepts predict cheaper */
-    int32_t refresh_kind;     /* tensor-core refresh operands: 1 = a BF16 copy of Q (0 =
-                                 default: 1); 2 is not a valid value (ICD2S_ERR_ARG); 3 = int8 Q read as bytes
+    int32_t refresh_kind;     /* tensor-core refresh: 1 = a BF16 copy of Q, persistent over
+                                 the SMs with tiles of 128 rows of Q (0 = default: 1); 4 = the
+                                 same with tiles of 256 rows; 2 is not a valid value
+                                 (ICD2S_ERR_ARG); 3 = int8 Q read as bytes
                                  and converted to BF16 in shared memory (no copy of Q:
                                  2 n ld bytes less device memory, 0.049 against 0.041 ms at
                                  n = 7000, R = 256) */
@@ -533,6 +549,14 @@ int icd2s_kernel_launches(uint64_t* count);
  * buffers that belong together are made all or none, and a later call makes
  * what is missing. */
 int icd2s_debug_fail_allocations_after(int32_t count);
+
+/* Fault injection for tests of the refresh's failure detection: the next
+ * `launches` tensor-core refreshes of this state issue no operand loads and
+ * bound every pipeline wait by wait_us microseconds (1..2000000), so their
+ * waits time out, the kernel raises its error flag, releases its tensor
+ * memory and returns, and icd2s_refresh returns ICD2S_ERR_TIMEOUT.  Later
+ * refreshes run normally (waits bounded by 2 s).  launches = 0 disarms. */
+int icd2s_debug_refresh_stall(icd2s_state* st, int32_t launches, int32_t wait_us);
 
 /* Flip write-back that allocates nothing.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- code

@@ -184,6 +184,8 @@ struct icd2s_state {
     void* Xb = nullptr; int32_t* G2 = nullptr; int64_t* E2 = nullptr; int* rflags = nullptr;  // [0] timeout, [1] mismatches
     cudaEvent_t rev[2] = {};  // around the tensor-core kernel of the last refresh (when timing)
     bool timed_refresh = false;
+    int refresh_stall = 0;                          // fault injection: refreshes left whose loads are skipped
+    unsigned long long refresh_stall_wait_ns = 0;   // and their wait bound
     cudaEvent_t aev[2] = {};  // around the write-back kernel of the last apply_flips_update_gains
     bool timed_apply = false;
     // phase timing of icd2s_step: events [2 * phase] / [2 * phase + 1]
@@ -986,28 +988,33 @@ int icd2s_refresh(icd2s_state* st, int32_t rebuild, int32_t* mismatches, void* s
         if (!st->rev[0]) for (cudaEvent_t& e : st->rev) CK(cudaEventCreate(&e));
         CK(cudaEventRecord(st->rev[0], s));
     }
+    const int stall = st->refresh_stall > 0;
+    const unsigned long long wait_ns = stall ? st->refresh_stall_wait_ns : 2000000000ull;
+    if (stall) --st->refresh_stall;
     if (bytes)
         CK(launch_refresh_i8(q->Q, st->Xb, n, R, ld, st->G2, st->rflags, st->tune.refresh_bn,
-                             st->tune.refresh_splits, s));  // H into G2
+                             st->tune.refresh_splits, wait_ns, stall, s));  // H into G2
     else
         CK(launch_refresh_mma(q->Qb, st->Xb, n, R, ld, st->G2, st->rflags, st->tune.refresh_bn,
-                              st->tune.refresh_splits, s));
+                              st->tune.refresh_splits, st->tune.refresh_kind == 4 ? 256 : 128, wait_ns, stall, s));
     if (st->timing) {
         CK(cudaEventRecord(st->rev[1], s));
         st->timed_refresh = true;
     }
     CK(launch_finish_gains(q->diag, n, ld, st->X, st->G2, st->E2, R, s));     // H -> g, E
     CK(launch_compare(st->G, st->E, st->G2, st->E2, n, ld, R, st->rflags + 1, s));
-    if (rebuild) {
-        CK(cudaMemcpyAsync(st->G, st->G2, RL * 4, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(st->E, st->E2, (size_t)R * 8, cudaMemcpyDeviceToDevice, s));
-    }
-    if (mismatches) {
+    if (mismatches || rebuild) {
+        // a timed-out pipeline leaves an incomplete sum: report it, and never
+        // rebuild the state from it
         int f[2] = {0, 0};
         CK(cudaMemcpyAsync(f, st->rflags, 8, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         REQ(f[0] == 0, ICD2S_ERR_TIMEOUT, "refresh: a tensor-core pipeline wait timed out");
-        *mismatches = f[1];
+        if (mismatches) *mismatches = f[1];
+    }
+    if (rebuild) {
+        CK(cudaMemcpyAsync(st->G, st->G2, RL * 4, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(st->E, st->E2, (size_t)R * 8, cudaMemcpyDeviceToDevice, s));
     }
     return ICD2S_OK;
 }
@@ -1264,8 +1271,8 @@ int icd2s_set_tuning(icd2s_state* st, const icd2s_tuning* t)
         "refresh_bn=%d must be 0, 128 or 256", t->refresh_bn);
     REQ(t->refresh_splits >= 0 && t->refresh_splits <= 256, ICD2S_ERR_ARG, "refresh_splits=%d outside 0..256",
         t->refresh_splits);
-    REQ(t->refresh_kind == 0 || t->refresh_kind == 1 || t->refresh_kind == 3, ICD2S_ERR_ARG,
-        "refresh_kind=%d must be 0, 1 or 3", t->refresh_kind);
+    REQ(t->refresh_kind == 0 || t->refresh_kind == 1 || t->refresh_kind == 3 || t->refresh_kind == 4, ICD2S_ERR_ARG,
+        "refresh_kind=%d must be 0, 1, 3 or 4", t->refresh_kind);
     REQ(t->anneal_warps_per_cta >= 0 && t->anneal_warps_per_cta <= 4, ICD2S_ERR_ARG,
         "anneal_warps_per_cta=%d outside 0..4", t->anneal_warps_per_cta);
     REQ(t->tabu_wide_keys == 0 || t->tabu_wide_keys == 1, ICD2S_ERR_ARG, "tabu_wide_keys=%d must be 0 or 1",
@@ -1395,6 +1402,16 @@ int icd2s_kernel_launches(uint64_t* count)
     return ICD2S_OK;
 }
 
+int icd2s_debug_refresh_stall(icd2s_state* st, int32_t launches, int32_t wait_us)
+{
+    REQ(st, ICD2S_ERR_ARG, "NULL state");
+    REQ(launches >= 0 && wait_us >= 1 && wait_us <= 2000000, ICD2S_ERR_ARG,
+        "launches=%d must be >= 0 and wait_us=%d in 1..2000000", launches, wait_us);
+    st->refresh_stall = launches;
+    st->refresh_stall_wait_ns = (unsigned long long)wait_us * 1000ull;
+    return ICD2S_OK;
+}
+
 int icd2s_debug_fail_allocations_after(int32_t count)
 {
     g_alloc_left.store(count < 0 ? -1 : (long long)count);
@@ -1408,6 +1425,30 @@ int icd2s_step(icd2s_state* st, const icd2s_params* p, int32_t t, void* stream)
     if (rc) return rc;
     REQ(t >= 0, ICD2S_ERR_ARG, "t < 0");
     return p->use_graph ? graph_step(st, p, t, S(stream)) : step_impl(st, p, t, nullptr, S(stream));
+}
+
+int icd2s_im_round(icd2s_state* st, const icd2s_params* p, int32_t t, void* stream)
+{
+    REQ(st && p, ICD2S_ERR_ARG, "NULL argument");
+    int rc = check_params(st, p);
+    if (rc) return rc;
+    REQ(t >= 0, ICD2S_ERR_ARG, "t < 0");
+    REQ(p->ablation == 0, ICD2S_ERR_ARG, "an Ising-machine round has no ablation");
+    cudaStream_t s = S(stream);
+    if ((rc = ensure_beta(st, p->sweeps, p->T_max, p->T_min, s))) return rc;
+    const bool feats = wants_features(st, p);
+    if (feats) {
+        REQ(st->have_scores, ICD2S_ERR_STATE, "the learned selection needs a step that scored the variables");
+    }
+    rc = select_impl(st, p->w1, p->w2, p->w3, p->K, p->m_min, p->m_max, (uint32_t)t, s, nullptr, p->select_mode,
+                     true, 0);                                                              // Eq. 6-8, Alg. 3-4
+    if (rc) return rc;
+    const bool queued = p->K > 1 || p->m_min != p->m_max;
+    rc = anneal_impl(st, st->idx, st->off, st->R * p->K, p->K, p->m_max, 0, 0, p->sweeps, p->T_max, p->T_min,
+                     (uint32_t)t, nullptr, 0, nullptr, s, queued, nullptr, p->im_mode);  // Eq. 4, Algorithm 4
+    if (rc) return rc;
+    CK(launch_apply(st->d, s));
+    return ICD2S_OK;
 }
 
 int icd2s_step_shard_begin(icd2s_state* st, const icd2s_params* p, int32_t t, int32_t* counts_dev, void* stream)

@@ -190,11 +190,16 @@ cudaError_t launch_best(const Dev& d, int64_t* trace_slot, int iter_end, int32_t
 cudaError_t launch_set_iter(int32_t* iter_dev, int t, cudaStream_t s);
 // dense refresh on the tensor cores (kernels_refresh.cu)
 cudaError_t launch_to_bf16(const void* src, bool is_signed, size_t count, void* dst, cudaStream_t s);
+// H[R][ld] += Q X^T (BF16 copies of Q and X), persistent over the SMs: bn
+// replicas and rows (128 / 256) of Q per tile, ctas persistent CTAs (0: one
+// per SM); every pipeline wait bounded by wait_ns, after which err is raised;
+// skip_loads: fault injection for tests (the producer issues no loads)
 cudaError_t launch_refresh_mma(const void* Qb, const void* Xb, int n, int R, int ld, int32_t* H, int* err, int bn,
-                               int splits, cudaStream_t s);
+                               int ctas, int rows, unsigned long long wait_ns, int skip_loads, cudaStream_t s);
 // the same with Q read as int8 bytes and converted to BF16 in shared memory
+// (one tile and K split per CTA: splits K splits, 0 = a single wave)
 cudaError_t launch_refresh_i8(const void* Q8, const void* Xb, int n, int R, int ld, int32_t* H, int* err, int bn,
-                              int splits, cudaStream_t s);
+                              int splits, unsigned long long wait_ns, int skip_loads, cudaStream_t s);
 cudaError_t launch_finish_gains(const int32_t* diag, int n, int ld, const uint8_t* X, int32_t* G, int64_t* E, int R,
                                 cudaStream_t s);
 // learned selection (kernels_mlp.cu)

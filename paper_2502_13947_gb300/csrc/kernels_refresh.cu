@@ -31,6 +31,7 @@ namespace icd2s {
 namespace {
 
 constexpr int kBM = 128, kBK = 64;
+constexpr uint32_t kStgBytes = 2 * 32 * kBM * 4;  // the persistent refresh's two epilogue tiles
 constexpr int kWaitLimit = 1 << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -63,14 +64,15 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// bounded wait (iterations and about 2 s of wall time); false, with the error
-// flag raised, if the phase never completes
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err)
+// bounded wait (iterations and wait_ns of wall time, 2 s unless a test asks
+// for less); false, with the error flag raised, if the phase never completes
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, uint64_t wait_ns = 2000000000ull)
 {
+    if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (int i = 0; i < kWaitLimit; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 255) == 255 && global_ns() - t0 > 2000000000ull) break;
+        if ((i & 255) == 255 && global_ns() - t0 > wait_ns) break;
     }
     atomicExch(err, 1);
     return false;
@@ -120,6 +122,41 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
         : "memory");
 }
 
+// element-wise add of a shared-memory tile into global memory by the TMA
+// (the tensor map's type and box; elements outside the tensor are skipped)
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, int x, int y, uint32_t src)
+{
+    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];"
+                 ::"l"(map), "r"(x), "r"(y), "r"(src)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int threads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// named barrier that also returns whether `pred` holds in any of its threads
+__device__ __forceinline__ bool named_bar_or(int id, int threads, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(threads)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -128,114 +165,193 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
 
 }  // namespace
 
-template <int BN, int STAGES>
-__global__ __launch_bounds__(128, 1) void k_refresh_mma(const __grid_constant__ CUtensorMap tA,
-                                                       const __grid_constant__ CUtensorMap tB, int n, int R,
-                                                       int kc_total, int kc_per_split, int32_t* __restrict__ H,
-                                                       int ldh, int* err)
+// ---------------------------------------------------------------------------
+// Persistent form: one CTA per SM walks a contiguous range of the work units
+// (tile, K chunk), tiles of MS x 128 rows of Q by BN replicas taken in order
+// and each tile's K chunks in order, so a CTA's range covers the end of one
+// tile, whole tiles and the start of another ("stream-K"): every SM gets the
+// same number of chunks, whatever the tile count.  Each run of chunks of one
+// tile (a segment) accumulates in tensor memory and is added to H by the
+// epilogue warps (exact int32 atomics: the segments of a tile may come from
+// several CTAs).  With NACC = 2 accumulators the epilogue of one segment
+// overlaps the MMAs of the next.  Warps: 0 = TMA producer (lane 0), 1 = MMA
+// issuer (lane 0), 2..5 = epilogue (warp w reads accumulator lanes
+// 32 (w mod 4) .. + 31).  Barriers: full/empty per stage, full/empty per
+// accumulator, and `done` for the issuer's last MMAs.  Every wait is bounded
+// by wait_ns; a timed-out wait raises the error flag and its role stops, so
+// the others time out as well and the kernel ends with the flag set.
+// skip_loads (fault injection for tests): the producer issues nothing.
+// ---------------------------------------------------------------------------
+template <int BN, int MS, int STAGES, int NACC>
+__global__ __launch_bounds__(192, 1) void k_refresh_mma(const __grid_constant__ CUtensorMap tA,
+                                                       const __grid_constant__ CUtensorMap tB,
+                                                       const __grid_constant__ CUtensorMap tH, int n, int R,
+                                                       int kc_total, int tiles_n, long long units, int* err,
+                                                       unsigned long long wait_ns, int skip_loads)
 {
+    static_assert(MS * BN * NACC <= 512, "tensor memory holds 512 columns");
     constexpr uint32_t kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
+    constexpr uint32_t kStage = MS * kABytes + kBBytes;
     constexpr uint32_t kIdesc = idesc_bf16_f32(kBM, BN);
+    constexpr uint32_t kCols = MS * BN * NACC;  // a power of two >= 32
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* sA = smem;
-    unsigned char* sB = smem + STAGES * kABytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * kBBytes);  // full[S], empty[S], done
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+    int32_t* stg = reinterpret_cast<int32_t*>(smem + STAGES * kStage);   // epilogue tiles [2][32][128]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * kStage + kStgBytes);
+    // full[S], empty[S], afull[NACC], aempty[NACC], done
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2 * NACC + 1);
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * STAGES, afull0 = empty0 + 8 * STAGES,
+                   aempty0 = afull0 + 8 * NACC, done = aempty0 + 8 * NACC;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-    const int kc0 = blockIdx.z * kc_per_split;
-    const int kc1 = min(kc0 + kc_per_split, kc_total);
-    const int nk = kc1 > kc0 ? kc1 - kc0 : 0;
+    const long long u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
+        for (int a = 0; a < NACC; ++a) {
+            mbar_init(afull0 + 8 * a, 1);
+            mbar_init(aempty0 + 8 * a, 128);   // every epilogue thread
+        }
         mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(BN)
+                     "r"(kCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    bool ok = true;
 
-    if (warp == 0 && lane == 0 && nk > 0) {
-        // producer: TMA loads of A = Q[m0 .. m0+127][k] and B = X[n0 .. n0+BN-1][k]
-        int issued = 0;
-        for (int i = 0; i < nk && ok; ++i) {
-            const int s = i % STAGES, u = i / STAGES;
-            if (u > 0) ok = mbar_wait(empty0 + 8 * s, (uint32_t)((u - 1) & 1), err);
-            if (!ok) break;
-            const uint32_t fb = full0 + 8 * s;
-            mbar_expect_tx(fb, kABytes + kBBytes);
-            const int kx = (kc0 + i) * kBK;  // element column, a multiple of 64
-            tma_load_2d(smem_u32(sA + s * kABytes), &tA, kx, m0, fb);
-            tma_load_2d(smem_u32(sB + s * kBBytes), &tB, kx, n0, fb);
-            ++issued;
-        }
-        // every load this thread issued has landed before the CTA can leave
-        for (int i = issued - STAGES > 0 ? issued - STAGES : 0; i < issued; ++i)
-            mbar_wait(full0 + 8 * (i % STAGES), (uint32_t)((i / STAGES) & 1), err);
-    } else if (warp == 1 && lane == 0 && nk > 0) {
-        // MMA issuer
-        for (int i = 0; i < nk && ok; ++i) {
-            const int s = i % STAGES, u = i / STAGES;
-            ok = mbar_wait(full0 + 8 * s, (uint32_t)(u & 1), err);
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a = smem_u32(sA + s * kABytes), b = smem_u32(sB + s * kBBytes);
+    if (warp == 0) {
+        if (lane == 0 && !skip_loads) {
+            // producer: A = Q[rows of the tile][chunk] (MS boxes of 128 rows), B = X[replicas of the tile][chunk]
+            bool ok = true;
+            long long issued = 0;
+            for (long long u = u0; u < u1 && ok; ++u, ++issued) {
+                const int s = (int)(issued % STAGES);
+                const long long use = issued / STAGES;
+                if (use > 0) ok = mbar_wait(empty0 + 8 * s, (uint32_t)((use - 1) & 1), err, wait_ns);
+                if (!ok) break;
+                const int tile = (int)(u / kc_total), kc = (int)(u % kc_total);
+                const int tm = tile / tiles_n, tn = tile % tiles_n;
+                const uint32_t fb = full0 + 8 * s;
+                unsigned char* st = smem + (size_t)s * kStage;
+                mbar_expect_tx(fb, kStage);
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk)  // K = 16 per instruction: 32 bytes along the row
-                mma_bf16(tmem, smem_desc_sw128(a + 32 * kk), smem_desc_sw128(b + 32 * kk), kIdesc,
-                         (i > 0 || kk > 0) ? 1u : 0u);
-            mma_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
+                for (int ms = 0; ms < MS; ++ms)
+                    tma_load_2d(smem_u32(st + ms * kABytes), &tA, kc * kBK, (tm * MS + ms) * kBM, fb);
+                tma_load_2d(smem_u32(st + MS * kABytes), &tB, kc * kBK, tn * BN, fb);
+            }
+            // every load issued has landed before the CTA can leave
+            for (long long i = issued - STAGES > 0 ? issued - STAGES : 0; i < issued; ++i)
+                mbar_wait(full0 + 8 * (int)(i % STAGES), (uint32_t)((i / STAGES) & 1), err, wait_ns);
         }
-        mma_commit(done);
-    }
-    __syncwarp();
-
-    // epilogue: warp w owns accumulator lanes (rows) 32 w .. 32 w + 31
-    if (nk > 0 && mbar_wait(done, 0u, err)) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-        for (int c = 0; c < BN; c += 16) {
-            uint32_t v[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15])
-                : "r"(tw + (uint32_t)c));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < n) {
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: per segment, accumulator a = segment mod NACC, freed by the epilogue
+            bool ok = true;
+            long long i = 0;
+            int seg = 0;
+            for (long long u = u0; u < u1 && ok; ++u, ++i) {
+                const int kc = (int)(u % kc_total);
+                const bool first = u == u0 || kc == 0, last = u + 1 == u1 || kc + 1 == kc_total;
+                const int a = seg % NACC, ause = seg / NACC;
+                if (first && ause > 0) {
+                    ok = mbar_wait(aempty0 + 8 * a, (uint32_t)((ause - 1) & 1), err, wait_ns);
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                }
+                const int s = (int)(i % STAGES);
+                ok = mbar_wait(full0 + 8 * s, (uint32_t)((i / STAGES) & 1), err, wait_ns);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t st = smem_u32(smem + (size_t)s * kStage);
+                const uint32_t b = st + MS * kABytes;
 #pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    const int p = n0 + c + t;
-                    if (p < R) {
-                        const int h = __float2int_rn(__uint_as_float(v[t]));
-                        if (h != 0) atomicAdd(H + (size_t)p * ldh + row, h);
-                    }
+                for (int ms = 0; ms < MS; ++ms) {
+                    const uint32_t d = tmem + (uint32_t)((a * MS + ms) * BN);
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk)  // K = 16 per instruction: 32 bytes along the row
+                        mma_bf16(d, smem_desc_sw128(st + ms * kABytes + 32 * kk), smem_desc_sw128(b + 32 * kk),
+                                 kIdesc, (!first || kk > 0) ? 1u : 0u);
+                }
+                mma_commit(empty0 + 8 * s);              // the stage is free once these MMAs have read it
+                if (last) {
+                    mma_commit(afull0 + 8 * a);          // the segment's sums are complete
+                    ++seg;
                 }
             }
+            mma_commit(done);                            // tracks every MMA issued above
+            mbar_wait(done, 0u, err, wait_ns);
         }
+    } else {
+        // epilogue: warp w owns accumulator lanes (rows) 32 (w mod 4) .. + 31.  Per
+        // 32 replicas the 128 threads write the sums as int32 into a staging tile
+        // [32 replicas][128 rows] (two tiles, alternating) and one thread adds the
+        // tile into H with a TMA reduction; the tile is reused once that
+        // reduction has read it.
+        const int et = threadIdx.x - 64, quad = warp & 3;
+        int seg = 0, chunk = 0;
+        for (long long u = u0; u < u1;) {
+            const int tile = (int)(u / kc_total), kc = (int)(u % kc_total);
+            long long send = u + (kc_total - kc);        // the segment: to the tile's end or the range's
+            if (send > u1) send = u1;
+            const int tm = tile / tiles_n, tn = tile % tiles_n;
+            const int a = seg % NACC, ause = seg / NACC;
+            const bool got = mbar_wait(afull0 + 8 * a, (uint32_t)(ause & 1), err, wait_ns);
+            // all 128 threads go on together (the loads below are warp-collective and
+            // the tiles are shared), or all stop
+            if (named_bar_or(1, 128, !got)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+            for (int ms = 0; ms < MS; ++ms) {
+                const uint32_t tw = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)((a * MS + ms) * BN);
+#pragma unroll 1
+                for (int c = 0; c < BN; c += 32, ++chunk) {
+                    uint32_t v[32];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                        : "r"(tw + (uint32_t)c));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    const int b = chunk & 1;
+                    if (chunk >= 2) {   // the reduction issued from this tile two chunks ago has read it
+                        if (et == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                        named_bar_sync(1, 128);
+                    }
+                    int32_t* dst = stg + b * (32 * kBM) + quad * 32 + lane;
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) dst[t * kBM] = __float2int_rn(__uint_as_float(v[t]));
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the TMA
+                    named_bar_sync(1, 128);
+                    if (et == 0)
+                        tma_reduce_add_2d(&tH, (tm * MS + ms) * kBM, tn * BN + c, smem_u32(stg + b * (32 * kBM)));
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(aempty0 + 8 * a);                // the accumulator may be overwritten
+            ++seg;
+            u = send;
+        }
+        if (et == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // every reduction is done
     }
+    __syncwarp();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -265,18 +381,13 @@ __device__ __forceinline__ uint4 bf16x8_from_s8(uint2 w)
                       __byte_perm(h[4], h[5], 0x7632u), __byte_perm(h[6], h[7], 0x7632u));
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
 }  // namespace
 
 template <int BN, int SI, int SC>
 __global__ __launch_bounds__(192, 1) void k_refresh_i8(const __grid_constant__ CUtensorMap tA8,
                                                       const __grid_constant__ CUtensorMap tB, int n, int R,
                                                       int kc_total, int kc_per_split, int32_t* __restrict__ H,
-                                                      int ldh, int* err)
+                                                      int ldh, int* err, unsigned long long wait_ns, int skip_loads)
 {
     constexpr uint32_t kA8 = kBM * kBK, kA16 = kBM * kBK * 2, kB16 = BN * kBK * 2;
     constexpr uint32_t kIdesc = idesc_bf16_f32(kBM, BN);
@@ -320,12 +431,12 @@ __global__ __launch_bounds__(192, 1) void k_refresh_i8(const __grid_constant__ C
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
 
-    if (warp == 0 && lane == 0 && nk > 0) {
+    if (warp == 0 && lane == 0 && nk > 0 && !skip_loads) {
         // producer: byte tiles of Q[m0 ..][k], BF16 tiles of X[n0 ..][k]
         int issued = 0;
         for (int i = 0; i < nk && ok; ++i) {
             const int s = i % SI, u = i / SI;
-            if (u > 0) ok = mbar_wait(iempty0 + 8 * s, (uint32_t)((u - 1) & 1), err);
+            if (u > 0) ok = mbar_wait(iempty0 + 8 * s, (uint32_t)((u - 1) & 1), err, wait_ns);
             if (!ok) break;
             const uint32_t fb = ifull0 + 8 * s;
             mbar_expect_tx(fb, kA8 + kB16);
@@ -335,14 +446,14 @@ __global__ __launch_bounds__(192, 1) void k_refresh_i8(const __grid_constant__ C
             ++issued;
         }
         for (int i = issued - SI > 0 ? issued - SI : 0; i < issued; ++i)
-            mbar_wait(ifull0 + 8 * (i % SI), (uint32_t)((i / SI) & 1), err);
+            mbar_wait(ifull0 + 8 * (i % SI), (uint32_t)((i / SI) & 1), err, wait_ns);
     } else if (warp == 1 && lane == 0 && nk > 0) {
         // MMA issuer: converted Q from buffer i mod SC (its stage's X tile has landed
         // before the converters released the buffer), X from TMA stage i mod SI
         for (int i = 0; i < nk && ok; ++i) {
             const int sc = i % SC, si = i % SI;
-            ok = mbar_wait(cfull0 + 8 * sc, (uint32_t)((i / SC) & 1), err) &&
-                 mbar_wait(ifull0 + 8 * si, (uint32_t)((i / SI) & 1), err);  // the X tile, observed directly
+            ok = mbar_wait(cfull0 + 8 * sc, (uint32_t)((i / SC) & 1), err, wait_ns) &&
+                 mbar_wait(ifull0 + 8 * si, (uint32_t)((i / SI) & 1), err, wait_ns);  // the X tile, observed directly
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a = smem_u32(cA + sc * kA16), b = smem_u32(tB16 + si * kB16);
@@ -360,8 +471,8 @@ __global__ __launch_bounds__(192, 1) void k_refresh_i8(const __grid_constant__ C
         const int c = threadIdx.x - 64;
         for (int i = 0; i < nk && ok; ++i) {
             const int si = i % SI, sc = i % SC, uc = i / SC;
-            ok = mbar_wait(ifull0 + 8 * si, (uint32_t)((i / SI) & 1), err);
-            if (ok && uc > 0) ok = mbar_wait(cempty0 + 8 * sc, (uint32_t)((uc - 1) & 1), err);
+            ok = mbar_wait(ifull0 + 8 * si, (uint32_t)((i / SI) & 1), err, wait_ns);
+            if (ok && uc > 0) ok = mbar_wait(cempty0 + 8 * sc, (uint32_t)((uc - 1) & 1), err, wait_ns);
             if (!ok) break;
             const unsigned char* a8 = tA8b + si * kA8;
             unsigned char* a16 = cA + sc * kA16;
@@ -379,7 +490,10 @@ __global__ __launch_bounds__(192, 1) void k_refresh_i8(const __grid_constant__ C
     __syncwarp();
 
     // epilogue: warps 2..5; warp w owns accumulator lanes (rows) 32 (w mod 4) ..
-    if (warp >= 2 && nk > 0 && mbar_wait(done, 0u, err)) {
+    // (a warp reads tensor memory only if every lane saw the sums complete)
+    bool got = false;
+    if (warp >= 2 && nk > 0) got = __all_sync(0xffffffffu, mbar_wait(done, 0u, err, wait_ns));
+    if (got) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int quad = warp & 3;
         const int row = m0 + quad * 32 + lane;
@@ -499,7 +613,7 @@ bool make_map_u8(CUtensorMap* m, const void* base, int rows, int ld, int box_row
 
 template <int BN, int SI, int SC>
 cudaError_t launch_i8(const CUtensorMap& tA, const CUtensorMap& tB, int n, int R, int ld, int splits, int32_t* H,
-                      int* err, cudaStream_t s)
+                      int* err, unsigned long long wait_ns, int skip_loads, cudaStream_t s)
 {
     const size_t sm = 1024 + (size_t)SI * (kBM + 2 * BN) * kBK + (size_t)SC * kBM * kBK * 2 +
                       (2 * SI + 2 * SC + 1) * 8 + 16;
@@ -509,23 +623,40 @@ cudaError_t launch_i8(const CUtensorMap& tA, const CUtensorMap& tB, int n, int R
     const int kc_total = ld / kBK;
     const int kcps = (kc_total + splits - 1) / splits;
     dim3 grid((n + kBM - 1) / kBM, (R + BN - 1) / BN, (kc_total + kcps - 1) / kcps);
-    kern<<<grid, 192, sm, s>>>(tA, tB, n, R, kc_total, kcps, H, ld, err);
+    kern<<<grid, 192, sm, s>>>(tA, tB, n, R, kc_total, kcps, H, ld, err, wait_ns, skip_loads);
     note_launch(1);
     return cudaGetLastError();
 }
 
-template <int BN, int STAGES>
-cudaError_t launch_mma(const CUtensorMap& tA, const CUtensorMap& tB, int n, int R, int ld, int splits, int32_t* H,
-                       int* err, cudaStream_t s)
+// 2-D int32 tensor [rows][ld] for the epilogue's TMA reductions, box = 128 x 32, no swizzle
+bool make_map_h(CUtensorMap* m, const void* base, int rows, int ld)
 {
-    const size_t sm = 1024 + (size_t)STAGES * (kBM + BN) * kBK * 2 + (2 * STAGES + 1) * 8 + 16;
-    auto kern = k_refresh_mma<BN, STAGES>;
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)kBM, 32u};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int MS, int STAGES, int NACC>
+cudaError_t launch_mma(const CUtensorMap& tA, const CUtensorMap& tB, const CUtensorMap& tH, int n, int R, int ld,
+                       int ctas, int* err, unsigned long long wait_ns, int skip_loads, cudaStream_t s)
+{
+    constexpr size_t kStage = (size_t)(MS * kBM + BN) * kBK * 2;
+    const size_t sm = 1024 + STAGES * kStage + kStgBytes + (2 * STAGES + 2 * NACC + 1) * 8 + 16;
+    auto kern = k_refresh_mma<BN, MS, STAGES, NACC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int kc_total = ld / kBK;
-    const int kcps = (kc_total + splits - 1) / splits;
-    dim3 grid((n + kBM - 1) / kBM, (R + BN - 1) / BN, (kc_total + kcps - 1) / kcps);
-    kern<<<grid, 128, sm, s>>>(tA, tB, n, R, kc_total, kcps, H, ld, err);
+    const int tiles_m = (n + MS * kBM - 1) / (MS * kBM), tiles_n = (R + BN - 1) / BN;
+    const long long units = (long long)tiles_m * tiles_n * kc_total;
+    int grid = ctas > 0 ? ctas : device_sm_count();   // persistent: one CTA per SM
+    if (grid > units) grid = (int)units;
+    kern<<<grid, 192, sm, s>>>(tA, tB, tH, n, R, kc_total, tiles_n, units, err, wait_ns, skip_loads);
     note_launch(1);
     return cudaGetLastError();
 }
@@ -534,27 +665,28 @@ cudaError_t launch_mma(const CUtensorMap& tA, const CUtensorMap& tB, int n, int 
 
 // H[R][ld] (int32, zeroed by the caller) += Q X^T on the tensor cores.  Qb: bf16 [n][ld];
 // Xb: bf16 [R][ld]; ld a multiple of 128.  err: device flag raised on a
-// timed-out wait.  bn: replicas per tile (128 / 256; 0 picks by R);
-// splits: K splits (0: as many as keep every tile's CTAs in one wave).
+// timed-out wait.  bn: replicas per tile (128 / 256; 0 picks by R); rows: 128
+// or 256 rows of Q per tile (0 = 128); ctas: persistent CTAs (0 = one per SM).
+// wait_ns: bound of every pipeline wait; skip_loads: fault injection (no loads).
 cudaError_t launch_refresh_mma(const void* Qb, const void* Xb, int n, int R, int ld, int32_t* H, int* err, int bn,
-                               int splits, cudaStream_t s)
+                               int ctas, int rows, unsigned long long wait_ns, int skip_loads, cudaStream_t s)
 {
-    CUtensorMap tA, tB;
+    CUtensorMap tA, tB, tH;
     const int BN = bn == 128 || bn == 256 ? bn : (R > 128 ? 256 : 128);
-    if (!make_map(&tA, Qb, n, ld, kBM) || !make_map(&tB, Xb, R, ld, BN)) return cudaErrorInvalidValue;
-    const int tiles = ((n + kBM - 1) / kBM) * ((R + BN - 1) / BN);
-    const int kc_total = ld / kBK;
-    if (splits <= 0) splits = device_sm_count() / tiles;  // one CTA per SM, a single wave
-    if (splits < 1) splits = 1;
-    if (splits > kc_total) splits = kc_total;
-    if (BN == 256) return launch_mma<256, 4>(tA, tB, n, R, ld, splits, H, err, s);
-    return launch_mma<128, 6>(tA, tB, n, R, ld, splits, H, err, s);
+    if (!make_map(&tA, Qb, n, ld, kBM) || !make_map(&tB, Xb, R, ld, BN) || !make_map_h(&tH, H, R, ld))
+        return cudaErrorInvalidValue;
+    if (rows == 256) {  // two 128-row halves share each replica tile; one accumulator
+        if (BN == 256) return launch_mma<256, 2, 3, 1>(tA, tB, tH, n, R, ld, ctas, err, wait_ns, skip_loads, s);
+        return launch_mma<128, 2, 4, 2>(tA, tB, tH, n, R, ld, ctas, err, wait_ns, skip_loads, s);
+    }
+    if (BN == 256) return launch_mma<256, 1, 4, 2>(tA, tB, tH, n, R, ld, ctas, err, wait_ns, skip_loads, s);
+    return launch_mma<128, 1, 6, 2>(tA, tB, tH, n, R, ld, ctas, err, wait_ns, skip_loads, s);
 }
 
 // H[R][ld] (int32, zeroed by the caller) += Q X^T with Q read as bytes:
 // Q8 int8 [n][ld], Xb bf16 [R][ld]; ld a multiple of 128.
 cudaError_t launch_refresh_i8(const void* Q8, const void* Xb, int n, int R, int ld, int32_t* H, int* err, int bn,
-                              int splits, cudaStream_t s)
+                              int splits, unsigned long long wait_ns, int skip_loads, cudaStream_t s)
 {
     CUtensorMap tA, tB;
     const int BN = bn == 128 || bn == 256 ? bn : (R > 128 ? 256 : 128);
@@ -564,8 +696,8 @@ cudaError_t launch_refresh_i8(const void* Q8, const void* Xb, int n, int R, int 
     if (splits <= 0) splits = device_sm_count() / tiles;
     if (splits < 1) splits = 1;
     if (splits > kc_total) splits = kc_total;
-    if (BN == 256) return launch_i8<256, 4, 3>(tA, tB, n, R, ld, splits, H, err, s);
-    return launch_i8<128, 6, 3>(tA, tB, n, R, ld, splits, H, err, s);
+    if (BN == 256) return launch_i8<256, 4, 3>(tA, tB, n, R, ld, splits, H, err, wait_ns, skip_loads, s);
+    return launch_i8<128, 6, 3>(tA, tB, n, R, ld, splits, H, err, wait_ns, skip_loads, s);
 }
 
 // Counts entries where two gain/energy sets differ (the drift check).

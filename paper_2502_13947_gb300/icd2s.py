@@ -37,7 +37,8 @@ EXPORTS = (
     "icd2s_get_hits", "icd2s_log_enable", "icd2s_log_info", "icd2s_log_copy", "icd2s_get_apply_ms",
     "icd2s_exact_subqubos_batch", "icd2s_tabu_aspiration", "icd2s_state_save", "icd2s_checkpoint_info",
     "icd2s_state_restore", "icd2s_debug_fail_allocations_after", "icd2s_state_create_shard",
-    "icd2s_step_shard_begin", "icd2s_step_shard_finish", "icd2s_get_best_info",
+    "icd2s_step_shard_begin", "icd2s_step_shard_finish", "icd2s_get_best_info", "icd2s_debug_refresh_stall",
+    "icd2s_im_round",
 )
 MLP_PARAMS = 4673
 PHASES = ("tabu", "select", "anneal", "apply_anneal", "mutate", "apply_mutate", "best")
@@ -115,6 +116,8 @@ def lib():
                 "icd2s_step_shard_begin": (C.c_int, [vp, P(Params), i32, vp, vp]),
                 "icd2s_step_shard_finish": (C.c_int, [vp, P(Params), i32, vp, vp]),
                 "icd2s_get_best_info": (C.c_int, [vp, P(C.c_int64), P(i32), P(i32)]),
+                "icd2s_debug_refresh_stall": (C.c_int, [vp, i32, i32]),
+                "icd2s_im_round": (C.c_int, [vp, P(Params), i32, vp]),
                 "icd2s_state_destroy": (C.c_int, [vp]),
                 "icd2s_state_load": (C.c_int, [vp, vp, i32, vp]),
                 "icd2s_get_state": (C.c_int, [vp, vp, vp, vp]),
@@ -365,6 +368,11 @@ def icd2s_step(st, p: Params, t: int, stream=0) -> None:
     _check(lib().icd2s_step(st, C.byref(p), t, _s(stream)))
 
 
+def icd2s_im_round(st, p: Params, t: int, stream=0) -> None:
+    """One Ising-machine round: selection, batched anneal, write-back (no Tabu, no mutation)."""
+    _check(lib().icd2s_im_round(st, C.byref(p), t, _s(stream)))
+
+
 def icd2s_step_shard_begin(st, p: Params, t: int, counts_dev: int, stream=0) -> None:
     """First half of iteration t on a replica shard; writes its column counts (int32 [n], device)."""
     _check(lib().icd2s_step_shard_begin(st, C.byref(p), t, C.c_void_p(counts_dev), _s(stream)))
@@ -585,3 +593,9 @@ def icd2s_autotune(st, p: Params, stream=0) -> dict:
     t = Tuning()
     _check(lib().icd2s_autotune(st, C.byref(p), C.byref(t), _s(stream)))
     return _tuning_dict(t)
+
+
+def icd2s_debug_refresh_stall(st, launches: int, wait_us: int) -> None:
+    """Fault injection: the next `launches` refreshes skip their operand loads
+    and time out after wait_us (see include/icd2s.h)."""
+    _check(lib().icd2s_debug_refresh_stall(st, launches, wait_us))

@@ -21,12 +21,13 @@ def L():
     return I.lib()
 
 
-@pytest.mark.parametrize("kind", [1, 3])
+@pytest.mark.parametrize("kind", [1, 3, 4])
 @pytest.mark.parametrize("n,R,density", [(1, 1, 1.0), (64, 8, 1.0), (200, 16, 0.5), (300, 5, 0.3),
                                          (1000, 33, 1.0), (2500, 130, 0.1), (4097, 3, 1.0)])
 def test_refresh_equals_the_definition(L, orc, n, R, density, kind):
-    """Both operand paths: BF16 copies of Q and X loaded by TMA, and Q's
-    bytes converted to BF16 in shared memory."""
+    """Every operand path: BF16 copies of Q and X loaded by TMA (tiles of 128
+    or 256 rows of Q, persistent over the SMs), and Q's bytes converted to BF16
+    in shared memory."""
     Q = make_qubo(n, density, n + R)
     X = random_solutions(n, R, 4)
     q = I.icd2s_qubo_create(Q)
@@ -59,8 +60,8 @@ def test_refresh_after_steps_dense_n7000_R256(L, orc):
     try:
         for t in range(2):
             I.icd2s_step(st, lp, t)
-        for kind in (1, 3):
-            for bn, splits in ((256, 0), (128, 1), (256, 3)):
+        for kind in (1, 3, 4):
+            for bn, splits in ((256, 0), (128, 1), (256, 3), (128, 0), (256, 151)):
                 I.icd2s_set_tuning(st, refresh_bn=bn, refresh_splits=splits, refresh_kind=kind)
                 assert I.icd2s_refresh(st) == 0, (kind, bn, splits)
         x, g, E = I.icd2s_get_state(st, R, n)
@@ -84,3 +85,33 @@ def test_run_with_periodic_refresh_matches_the_oracle(L, orc):
         I.icd2s_qubo_destroy(q)
     o = orc.run(Q, orc_params(orc, lp), 9)
     assert np.array_equal(g["trace"], o["trace"]) and np.array_equal(g["S"], o["S"])
+
+
+@pytest.mark.parametrize("kind", [1, 3, 4])
+def test_refresh_wait_timeout_is_reported_and_the_state_stays_usable(L, orc, kind):
+    """Failure detection on the device: a refresh whose producer issues no
+    loads (fault injection) has every tensor-core pipeline wait run out after
+    2 ms; the kernel raises its flag, frees its tensor memory and returns,
+    icd2s_refresh returns ICD2S_ERR_TIMEOUT without rebuilding from the
+    incomplete sums, and the next refresh on the same state is exact."""
+    n, R = 1000, 33
+    Q = make_qubo(n, 1.0, 12)
+    X = random_solutions(n, R, 13)
+    q = I.icd2s_qubo_create(Q)
+    st = I.icd2s_state_create(q, R, 1)
+    try:
+        I.icd2s_set_tuning(st, refresh_kind=kind)
+        I.icd2s_state_load(st, X)
+        assert I.icd2s_refresh(st) == 0
+        I.icd2s_debug_refresh_stall(st, 1, 2000)
+        with pytest.raises(I.ICD2SError) as e:
+            I.icd2s_refresh(st, rebuild=True)
+        assert e.value.code == I.ERR_TIMEOUT
+        x, g, E = I.icd2s_get_state(st, R, n)       # the tracked values were not replaced
+        assert np.array_equal(E, orc.energy_batch(Q, X))
+        assert np.array_equal(g[5], orc.gains(Q, X[5]))
+        assert I.icd2s_refresh(st) == 0             # the next refresh runs normally
+        assert I.icd2s_refresh(st, rebuild=True) == 0
+    finally:
+        I.icd2s_state_destroy(st)
+        I.icd2s_qubo_destroy(q)

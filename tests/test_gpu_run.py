@@ -250,3 +250,45 @@ def test_run_with_the_tabu_search_split_over_clusters(L, orc, n, K, use_graph, G
     assert g["iters"] == o["iters"] and np.array_equal(g["trace"], o["trace"])
     assert np.array_equal(g["S"], o["S"])
     assert g["best_E"] == o["best_E"] and np.array_equal(g["best_x"], o["best_x"])
+
+
+@pytest.mark.parametrize("K,m_min,m_max", [(1, 32, 32), (3, 10, 60)])
+def test_im_round_equals_its_pieces(L, orc, K, m_min, m_max):
+    """icd2s_im_round (selection, one batched anneal launch, write-back, all
+    on the device) equals the same round made of the separately
+    oracle-checked calls: icd2s_select_subqubos, icd2s_anneal_subqubos_batch
+    and icd2s_apply_flips_update_gains; and the tracked gains stay exact (a
+    tensor-core refresh finds no difference)."""
+    torch = torch_cuda()
+    n, R, t = 600, 4, 3
+    Q = make_qubo(n, 0.5, 5)
+    X0 = random_solutions(n, R, 6)
+    lp = lib_params(I, n, z=R, K=K, m_min=m_min, m_max=m_max, m_init=m_max, alpha=n, c=4, sweeps=32,
+                    T_max=2000.0)
+    q = I.icd2s_qubo_create(Q)
+    a = I.icd2s_state_create(q, R, 8)
+    b = I.icd2s_state_create(q, R, 8)
+    try:
+        for st in (a, b):
+            I.icd2s_state_load(st, X0)
+            I.icd2s_tabu(st, lp.alpha, lp.c)
+        I.icd2s_im_round(a, lp, t)
+        idx = torch.zeros(R * K * m_max + 1, dtype=torch.int32, device="cuda")
+        off = torch.zeros(R * K * m_max + 1, dtype=torch.int32, device="cuda")
+        mask = torch.zeros((R, n), dtype=torch.uint8, device="cuda")
+        I.icd2s_select_subqubos(b, I.SelectParams(w1=lp.w1, w2=lp.w2, w3=lp.w3, K=K, m_min=m_min, m_max=m_max,
+                                                  iter=t), idx.data_ptr(), off.data_ptr())
+        I.icd2s_anneal_subqubos_batch(b, idx.data_ptr(), off.data_ptr(), R * K,
+                                      I.AnnealParams(sweeps=lp.sweeps, T_max=lp.T_max, T_min=lp.T_min, iter=t,
+                                                     per_replica=K), mask.data_ptr())
+        I.icd2s_apply_flips_update_gains(b, mask.data_ptr())
+        sa, sb = I.icd2s_get_state(a, R, n), I.icd2s_get_state(b, R, n)
+        for u, v in zip(sa, sb):
+            assert np.array_equal(u, v)
+        assert not np.array_equal(sa[0], X0)          # the round changed the solutions
+        assert I.icd2s_refresh(a) == 0
+        assert np.array_equal(sa[2], orc.energy_batch(Q, sa[0]))
+    finally:
+        I.icd2s_state_destroy(a)
+        I.icd2s_state_destroy(b)
+        I.icd2s_qubo_destroy(q)
