@@ -298,6 +298,46 @@ def measure_c4(I, torch, stream):
                     "256 x 7000 gains and 256 energies (0 mismatches expected)"}
 
 
+# The proposal network at the learned-selection workload's size: scores of
+# every variable of 32 replicas of n = 10 000 (320 000 rows), and training
+# steps on 8192-row batches, with the gradient on the CUDA cores (FP32) and on
+# the tensor cores (BF16 operands, FP32 accumulation).
+MLP_WORKLOAD = dict(name="learned-n10000-z32", rows=320000, batch=8192, steps=50)
+
+
+def measure_mlp(I, torch, stream, reps=10):
+    w = MLP_WORKLOAD
+    g = torch.Generator(device="cpu").manual_seed(3)
+    F = torch.rand((w["rows"], 6), generator=g).cuda()
+    y = (torch.rand(w["rows"], generator=g) < 0.1).to(torch.uint8).cuda()
+    out = torch.empty(w["rows"], dtype=torch.float32, device="cuda")
+    m = I.icd2s_mlp_create(1)
+    sp = stream.cuda_stream
+    res = {"workload": w["name"], "score_rows": w["rows"], "train_batch": w["batch"]}
+    try:
+        def timed(fn):
+            with torch.cuda.stream(stream):
+                fn()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    fn()
+                e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / reps
+        res["score_ms"] = timed(lambda: I.icd2s_mlp_score(m, F.data_ptr(), w["rows"], out.data_ptr(), sp))
+        for tc in (False, True):
+            I.icd2s_mlp_set_tensor_cores(m, tc)
+            ms = timed(lambda: I.icd2s_mlp_train(m, F.data_ptr(), y.data_ptr(), w["rows"], steps=w["steps"],
+                                                 batch=w["batch"], lr=1e-3, stream=sp))
+            res["train_step_ms_" + ("tensor_cores" if tc else "fp32")] = ms / w["steps"]
+    finally:
+        I.icd2s_mlp_destroy(m)
+    flops = 2 * 8960
+    res["score_gflops"] = flops * w["rows"] / (res["score_ms"] / 1000) / 1e9
+    return res
+
+
 APPLY_WORKLOAD = dict(name="gain-update-n16384-R16-disjoint1024", n=16384, density=1.0, qseed=5, R=16)
 
 
@@ -504,6 +544,7 @@ def run_gpu(args, w):
     refresh = None if args.no_refresh else measure_refresh(I, torch, peaks, stream, flush)
     apply_rf = None if args.no_refresh else measure_apply(I, torch, peaks, stream, flush)
     c4 = None if args.no_refresh else measure_c4(I, torch, stream)
+    mlp = None if args.no_refresh else measure_mlp(I, torch, stream)
     K = args.steps
     phase_avg = {k: v / K for k, v in phase_tot.items()}
     ld = (n + 127) // 128 * 128
@@ -574,6 +615,7 @@ def run_gpu(args, w):
         "anneal_kernel_attempts_per_s": anneal_rate,
         "roofline_anneal": roofline_anneal,
         "c4": c4,
+        "mlp": mlp,
         "ttt": ttt,
     }
     print(json.dumps(line), flush=True)

@@ -446,6 +446,15 @@ int icd2s_mlp_grad(icd2s_mlp* m, const float* F_dev, const uint8_t* y_dev, int64
 int icd2s_mlp_train(icd2s_mlp* m, const float* F_dev, const uint8_t* y_dev, int64_t rows,
                     const icd2s_train_params* tp, float* loss_host, void* stream);
 
+/* Where the network's gradient (icd2s_mlp_grad, icd2s_mlp_train) runs: 0 =
+ * the CUDA cores in FP32 (the default), 1 = its three 64-wide contractions
+ * (the layer-2 forward, the W2 gradient and the backward through W2) on the
+ * tensor cores, mma.sync BF16 x BF16 -> FP32, with the activations rounded
+ * to BF16 for the products; layer 1, the loss and the bias and W1 sums stay
+ * FP32.  Both are deterministic.  Scores (icd2s_mlp_score, the learned
+ * selection) are always FP32. */
+int icd2s_mlp_set_tensor_cores(icd2s_mlp* m, int32_t enable);
+
 /* Attaches a network to a state for select_mode 1/2 (NULL detaches).  The
  * state borrows it: it must outlive the state's use of it. */
 int icd2s_state_set_mlp(icd2s_state* st, icd2s_mlp* m);

@@ -145,6 +145,7 @@ struct icd2s_mlp {
     float* partial = nullptr; size_t partial_cap = 0;
     float* losses = nullptr; int loss_cap = 0;
     int64_t adam_t = 0;                       // Adam steps taken
+    bool tensor_cores = false;                // gradient contractions on the tensor cores (BF16 activations)
 };
 
 struct icd2s_state {
@@ -1743,7 +1744,7 @@ int icd2s_mlp_grad(icd2s_mlp* m, const float* F_dev, const uint8_t* y_dev, int64
     int rc = ensure_partial(m, rows, s);
     if (rc) return rc;
     CK(launch_mlp_grad(F_dev, y_dev, rows, rows, 0u, 0u, 0u, m->Wb, pos_weight, m->partial, grad_dev, loss_dev,
-                       nullptr, nullptr, nullptr, nullptr, 0, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f, s));
+                       nullptr, nullptr, nullptr, nullptr, 0, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f, s, m->tensor_cores));
     return ICD2S_OK;
 }
 
@@ -1776,13 +1777,21 @@ int icd2s_mlp_train(icd2s_mlp* m, const float* F_dev, const uint8_t* y_dev, int6
         const float bc2 = (float)(1.0 - std::pow((double)tp->beta2, (double)t));
         CK(launch_mlp_grad(F_dev, y_dev, rows, tp->batch, (uint32_t)m->adam_t, k0, k1, m->Wb, tp->pos_weight,
                            m->partial, nullptr, m->losses + i, m->master, m->mom, m->vel, m->Wb, 1, tp->lr,
-                           tp->beta1, tp->beta2, tp->eps, bc1, bc2, s));
+                           tp->beta1, tp->beta2, tp->eps, bc1, bc2, s, m->tensor_cores));
         m->adam_t = t;
     }
     if (loss_host) {
         CK(cudaMemcpyAsync(loss_host, m->losses, sizeof(float) * tp->steps, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
     }
+    return ICD2S_OK;
+}
+
+int icd2s_mlp_set_tensor_cores(icd2s_mlp* m, int32_t enable)
+{
+    REQ(m, ICD2S_ERR_ARG, "NULL network");
+    REQ(enable == 0 || enable == 1, ICD2S_ERR_ARG, "enable must be 0 or 1");
+    m->tensor_cores = enable != 0;
     return ICD2S_OK;
 }
 

@@ -210,7 +210,8 @@ size_t mlp_partial_floats(long long batch);
 cudaError_t launch_mlp_grad(const float* F, const uint8_t* y, long long rows, long long batch, uint32_t step,
                             uint32_t k0, uint32_t k1, const void* Wb, float pos_weight, float* partial,
                             float* grad_out, float* loss_out, float* master, float* mom, float* vel, void* Wb_out,
-                            int adam, float lr, float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
+                            int adam, float lr, float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s,
+                            bool tensor_cores = false);
 cudaError_t launch_round_bf16(const float* master, void* Wb, cudaStream_t s);
 cudaError_t launch_log(const Dev& d, uint8_t* prev_x, float* LF, uint8_t* LY, int32_t* lrep, cudaStream_t s);
 cudaError_t launch_compare(const int32_t* G1, const int64_t* E1, const int32_t* G2, const int64_t* E2, int n, int ld,

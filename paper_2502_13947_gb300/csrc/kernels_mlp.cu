@@ -268,6 +268,243 @@ __global__ __launch_bounds__(kRowsPerCta) void k_mlp_grad(const float* __restric
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same partial gradient with its three 64-wide contractions on the tensor
+// cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation): the layer-2
+// forward A2 = H1 W2^T, the weight gradient dW2 = dA2^T H1 and the backward
+// dA1 = dA2 W2, per CTA of 128 rows (warp w: rows 32 w .. 32 w + 31, or
+// output rows 16 w .. of dW2).  The activations h1 and dA2 are rounded to
+// BF16 for the products (the weights already are BF16); layer 1, the losses
+// and the column sums (b1, b2, w3, b3, W1) stay in FP32 on the CUDA cores,
+// summed over the rows in order.  Deterministic: the summation order of every
+// output is fixed.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kTS = 72;    // row stride (bf16) of the 64-wide operand tiles
+constexpr int kTT = 136;   // row stride (bf16) of the transposed 128-wide tiles
+
+// D += A B: A 16 x 16 (row-major), B 16 x 8 (column-major), BF16 -> FP32
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// acc[mt][nt] += A[r0 + 16 mt ..][k] B[k][16 nt ..] over k < K: A row-major with
+// stride lda, B stored by columns (column n contiguous in k) with stride ldb
+template <int MT, int K>
+__device__ __forceinline__ void warp_gemm_n64(float (&acc)[MT][8][4], const __nv_bfloat16* A, int lda, int r0,
+                                              const __nv_bfloat16* Bc, int ldb)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        uint32_t a[MT][4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            const __nv_bfloat16* ar = A + (size_t)(r0 + 16 * mt + g) * lda + k0 + 2 * t;
+            a[mt][0] = ld_pair(ar);
+            a[mt][1] = ld_pair(ar + 8 * lda);
+            a[mt][2] = ld_pair(ar + 8);
+            a[mt][3] = ld_pair(ar + 8 * lda + 8);
+        }
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const __nv_bfloat16* br = Bc + (size_t)(8 * nt + g) * ldb + k0 + 2 * t;
+            const uint32_t b0 = ld_pair(br), b1 = ld_pair(br + 8);
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) mma_bf16_16816(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+        }
+    }
+}
+
+}  // namespace
+
+__global__ __launch_bounds__(kRowsPerCta) void k_mlp_grad_tc(const float* __restrict__ F,
+                                                             const uint8_t* __restrict__ y, long long rows,
+                                                             long long batch, uint32_t step, uint32_t k0, uint32_t k1,
+                                                             const __nv_bfloat16* __restrict__ Wb, float pos_weight,
+                                                             float* __restrict__ partial)
+{
+    extern __shared__ __align__(16) float sm[];
+    float* w = sm;                                          // [kNParPad] FP32 copy of the BF16 weights
+    float* Fs = w + kNParPad;                               // [128][kFS]
+    float* DS = Fs + kRowsPerCta * kFS;                     // [128] dL/ds
+    float* LS = DS + kRowsPerCta;                           // [128] loss terms
+    float* X2 = LS + kRowsPerCta;                           // [128][kHS] h2, later dL/da1 (FP32)
+    __nv_bfloat16* H1b = reinterpret_cast<__nv_bfloat16*>(X2 + kRowsPerCta * kHS);  // [128][kTS] h1
+    __nv_bfloat16* H1t = H1b + kRowsPerCta * kTS;           // [64][kTT] h1^T
+    __nv_bfloat16* W2b = H1t + 64 * kTT;                    // [64][kTS] W2 (row o: weights into unit o)
+    __nv_bfloat16* W2t = W2b + 64 * kTS;                    // [64][kTS] W2^T
+    __nv_bfloat16* D2b = W2t + 64 * kTS;                    // [128][kTS] dL/da2
+    __nv_bfloat16* D2t = D2b + kRowsPerCta * kTS;           // [64][kTT] dL/da2^T
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    const long long nb = batch < rows ? batch : rows;
+    const long long r0 = (long long)blockIdx.x * kRowsPerCta;
+    load_weights(Wb, w);
+    for (int q = tid; q < 64 * 64; q += kRowsPerCta) {
+        const int o = q >> 6, k = q & 63;
+        W2b[o * kTS + k] = Wb[kOffW2 + q];
+        W2t[k * kTS + o] = Wb[kOffW2 + q];
+    }
+    __syncthreads();
+
+    // layer 1 (FP32), one row per thread
+    float yv = 0.f;
+    const bool valid = r0 + tid < nb;
+    {
+        float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (valid) {
+            const long long row = batch_row(r0 + tid, rows, batch, step, k0, k1);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) f[k] = F[row * 6 + k];
+            yv = y[row] ? 1.f : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Fs[tid * kFS + k] = f[k];
+#pragma unroll 8
+        for (int o = 0; o < 64; ++o) {
+            float a = w[kOffB1 + o];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) a = __fmaf_rn(w[kOffW1 + o * 6 + k], f[k], a);
+            const __nv_bfloat16 h = __float2bfloat16_rn(a > 0.f ? a : 0.f);
+            H1b[tid * kTS + o] = h;
+            H1t[o * kTT + tid] = h;
+        }
+    }
+    __syncthreads();
+
+    // layer 2 forward on the tensor cores: rows 32 warp .. + 31, all 64 units
+    {
+        float acc[2][8][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+        warp_gemm_n64<2, 64>(acc, H1b, kTS, 32 * warp, W2b, kTS);
+        // h2 = relu(a2 + b2) into X2; the row's score s = b3 + sum_o w3_o h2_o
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {           // rows g and g + 8 of the tile
+                const int r = 32 * warp + 16 * mt + g + 8 * hf;
+                float part = 0.f;
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int o = 8 * nt + 2 * t + e;
+                        const float a = acc[mt][nt][2 * hf + e] + w[kOffB2 + o];
+                        const float h2 = a > 0.f ? a : 0.f;
+                        X2[r * kHS + o] = h2;
+                        part = __fmaf_rn(w[kOffW3 + o], h2, part);
+                    }
+                // the row's 64 products: 4 threads x 16, added in a fixed tree
+                part += __shfl_xor_sync(0xffffffffu, part, 1);
+                part += __shfl_xor_sync(0xffffffffu, part, 2);
+                if (t == 0) DS[r] = part;   // the score without b3, for the owner thread below
+            }
+    }
+    __syncthreads();
+    {
+        const float s = w[kOffB3] + DS[tid];
+        const float sg = sigmoid(s);
+        DS[tid] = valid ? (pos_weight * yv * (sg - 1.f) + (1.f - yv) * sg) / (float)nb : 0.f;
+        LS[tid] = valid ? pos_weight * yv * softplus(-s) + (1.f - yv) * softplus(s) : 0.f;
+    }
+    __syncthreads();
+    float* out = partial + (size_t)blockIdx.x * kPartStride;
+    // w3, b2, b3 (FP32, rows in order); dL/da2 = ds w3 [h2 > 0] as BF16 tiles
+    if (tid < 64) {
+        float gsum = 0.f, bsum = 0.f;
+        const float w3 = w[kOffW3 + tid];
+        for (int r = 0; r < kRowsPerCta; ++r) {
+            const float h2 = X2[r * kHS + tid];
+            gsum = __fmaf_rn(DS[r], h2, gsum);
+            bsum += h2 > 0.f ? DS[r] * w3 : 0.f;
+        }
+        out[kOffW3 + tid] = gsum;
+        out[kOffB2 + tid] = bsum;
+    } else if (tid == 64) {
+        float gsum = 0.f, l = 0.f;
+        for (int r = 0; r < kRowsPerCta; ++r) { gsum += DS[r]; l += LS[r]; }
+        out[kOffB3] = gsum;
+        out[kNPar] = l / (float)nb;
+    }
+    {
+        const float ds = DS[tid];
+#pragma unroll 8
+        for (int o = 0; o < 64; ++o) {
+            const float d2 = X2[tid * kHS + o] > 0.f ? ds * w[kOffW3 + o] : 0.f;
+            const __nv_bfloat16 b = __float2bfloat16_rn(d2);
+            D2b[tid * kTS + o] = b;
+            D2t[o * kTT + tid] = b;
+        }
+    }
+    __syncthreads();
+    // dW2 = dA2^T H1 on the tensor cores: output rows 16 warp .. + 15
+    {
+        float acc[1][8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[0][nt][e] = 0.f;
+        warp_gemm_n64<1, kRowsPerCta>(acc, D2t, kTT, 16 * warp, H1t, kTT);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int o0 = 16 * warp + g, k = 8 * nt + 2 * t;
+            out[kOffW2 + o0 * 64 + k] = acc[0][nt][0];
+            out[kOffW2 + o0 * 64 + k + 1] = acc[0][nt][1];
+            out[kOffW2 + (o0 + 8) * 64 + k] = acc[0][nt][2];
+            out[kOffW2 + (o0 + 8) * 64 + k + 1] = acc[0][nt][3];
+        }
+    }
+    // dA1 = dA2 W2 on the tensor cores, masked by h1 > 0, into X2 (FP32)
+    {
+        float acc[2][8][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+        warp_gemm_n64<2, 64>(acc, D2b, kTS, 32 * warp, W2t, kTS);
+        __syncthreads();   // every thread has read X2 (the h2 values) above
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int r = 32 * warp + 16 * mt + g + 8 * (e >> 1), k = 8 * nt + 2 * t + (e & 1);
+                    X2[r * kHS + k] = __bfloat162float(H1b[r * kTS + k]) > 0.f ? acc[mt][nt][e] : 0.f;
+                }
+    }
+    __syncthreads();
+    // W1 (384) and b1 (64), FP32, rows in order
+    for (int q = tid; q < 64 * 6 + 64; q += kRowsPerCta) {
+        float gsum = 0.f;
+        if (q < 384) {
+            const int o = q / 6, k = q % 6;
+            for (int r = 0; r < kRowsPerCta; ++r) gsum = __fmaf_rn(X2[r * kHS + o], Fs[r * kFS + k], gsum);
+            out[kOffW1 + q] = gsum;
+        } else {
+            const int o = q - 384;
+            for (int r = 0; r < kRowsPerCta; ++r) gsum += X2[r * kHS + o];
+            out[kOffB1 + o] = gsum;
+        }
+    }
+}
+
 // Sums the partial gradients (and losses) of `blocks` CTAs in CTA order; then
 // optionally Adam: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
 // w -= lr (m / bc1) / (sqrt(v / bc2) + eps), with bc1/bc2 the bias corrections.
@@ -348,15 +585,28 @@ size_t mlp_partial_floats(long long batch) { return (size_t)((batch + kRowsPerCt
 cudaError_t launch_mlp_grad(const float* F, const uint8_t* y, long long rows, long long batch, uint32_t step,
                             uint32_t k0, uint32_t k1, const void* Wb, float pos_weight, float* partial,
                             float* grad_out, float* loss_out, float* master, float* mom, float* vel, void* Wb_out,
-                            int adam, float lr, float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s)
+                            int adam, float lr, float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s,
+                            bool tensor_cores)
 {
     const long long nb = batch < rows ? batch : rows;
     const int blocks = (int)((nb + kRowsPerCta - 1) / kRowsPerCta);
-    const size_t smem = sizeof(float) * ((size_t)kNParPad + 2 * kRowsPerCta * kHS + kRowsPerCta * kFS + 2 * kRowsPerCta);
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_mlp_grad<<<blocks, kRowsPerCta, smem, s>>>(F, y, rows, batch, step, k0, k1,
-                                                 reinterpret_cast<const __nv_bfloat16*>(Wb), pos_weight, partial);
+    if (tensor_cores) {
+        const size_t smem = sizeof(float) * ((size_t)kNParPad + kRowsPerCta * kFS + 2 * kRowsPerCta +
+                                             kRowsPerCta * kHS) +
+                            sizeof(__nv_bfloat16) * (2 * (size_t)kRowsPerCta * kTS + 2 * 64 * kTT + 2 * 64 * kTS);
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_mlp_grad_tc<<<blocks, kRowsPerCta, smem, s>>>(F, y, rows, batch, step, k0, k1,
+                                                        reinterpret_cast<const __nv_bfloat16*>(Wb), pos_weight,
+                                                        partial);
+    } else {
+        const size_t smem =
+            sizeof(float) * ((size_t)kNParPad + 2 * kRowsPerCta * kHS + kRowsPerCta * kFS + 2 * kRowsPerCta);
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_mlp_grad<<<blocks, kRowsPerCta, smem, s>>>(F, y, rows, batch, step, k0, k1,
+                                                     reinterpret_cast<const __nv_bfloat16*>(Wb), pos_weight, partial);
+    }
     k_mlp_reduce<<<(kNPar + 1 + 255) / 256, 256, 0, s>>>(partial, blocks, grad_out, loss_out, master, mom, vel,
                                                         reinterpret_cast<__nv_bfloat16*>(Wb_out), adam, lr, b1, b2,
                                                         eps, bc1, bc2);

@@ -38,7 +38,7 @@ EXPORTS = (
     "icd2s_exact_subqubos_batch", "icd2s_tabu_aspiration", "icd2s_state_save", "icd2s_checkpoint_info",
     "icd2s_state_restore", "icd2s_debug_fail_allocations_after", "icd2s_state_create_shard",
     "icd2s_step_shard_begin", "icd2s_step_shard_finish", "icd2s_get_best_info", "icd2s_debug_refresh_stall",
-    "icd2s_im_round",
+    "icd2s_im_round", "icd2s_mlp_set_tensor_cores",
 )
 MLP_PARAMS = 4673
 PHASES = ("tabu", "select", "anneal", "apply_anneal", "mutate", "apply_mutate", "best")
@@ -118,6 +118,7 @@ def lib():
                 "icd2s_get_best_info": (C.c_int, [vp, P(C.c_int64), P(i32), P(i32)]),
                 "icd2s_debug_refresh_stall": (C.c_int, [vp, i32, i32]),
                 "icd2s_im_round": (C.c_int, [vp, P(Params), i32, vp]),
+                "icd2s_mlp_set_tensor_cores": (C.c_int, [vp, i32]),
                 "icd2s_state_destroy": (C.c_int, [vp]),
                 "icd2s_state_load": (C.c_int, [vp, vp, i32, vp]),
                 "icd2s_get_state": (C.c_int, [vp, vp, vp, vp]),
@@ -599,3 +600,8 @@ def icd2s_debug_refresh_stall(st, launches: int, wait_us: int) -> None:
     """Fault injection: the next `launches` refreshes skip their operand loads
     and time out after wait_us (see include/icd2s.h)."""
     _check(lib().icd2s_debug_refresh_stall(st, launches, wait_us))
+
+
+def icd2s_mlp_set_tensor_cores(m, enable: bool = True) -> None:
+    """The network's gradient on the tensor cores (BF16 operands, FP32 accumulation) or in FP32."""
+    _check(lib().icd2s_mlp_set_tensor_cores(m, 1 if enable else 0))

@@ -222,3 +222,48 @@ def test_training_lowers_the_loss(L):
     assert np.all(np.isfinite(losses))
     assert l1 < 0.5 * l0 and l1 < 0.5 * base
     assert losses[-20:].mean() < 0.5 * losses[:20].mean()
+
+
+@pytest.mark.parametrize("rows", [905, 128, 5000])
+def test_tensor_core_gradient_matches_reference(L, rows):
+    """The gradient with its 64-wide contractions on the tensor cores (BF16
+    operands, FP32 accumulation) agrees with the double-precision reference
+    within 1e-3 absolute or 1e-2 relative, its loss within 2e-3 relative, and
+    two evaluations are bit-identical (fixed summation order)."""
+    F = _features(4 + rows, rows)
+    yv = (np.random.default_rng(5).uniform(size=rows) < 0.25).astype(np.uint8)
+    m, Wb = _net(_weights(6))
+    I.icd2s_mlp_set_tensor_cores(m, True)
+    torch = torch_cuda()
+    out = []
+    Fd, yd = dev(F), dev(yv)
+    for _ in range(2):
+        grad = torch.zeros(M.NPAR, dtype=torch.float32, device="cuda")
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        I.icd2s_mlp_grad(m, Fd.data_ptr(), yd.data_ptr(), rows, 3.0, grad.data_ptr(), loss.data_ptr())
+        out.append((grad.cpu().numpy(), float(loss.cpu()[0])))
+    I.icd2s_mlp_destroy(m)
+    (g, lval), (g2, lval2) = out
+    assert np.array_equal(g.view(np.uint32), g2.view(np.uint32)) and lval == lval2
+    L_ref, g_ref = M.loss_and_grad(Wb, F, yv, 3.0)
+    assert abs(lval - L_ref) <= 2e-3 * (1 + abs(L_ref))
+    err = np.abs(g - g_ref)
+    assert np.all((err <= 1e-3) | (err <= 1e-2 * np.abs(g_ref)))
+
+
+def test_tensor_core_training_lowers_the_loss(L):
+    """The training test of the FP32 path, with the gradient on the tensor cores."""
+    rows = 20000
+    F = _features(10, rows)
+    yv = (F[:, 1] < -0.3).astype(np.uint8)
+    m, Wb0 = _net(_weights(11, 0.2))
+    I.icd2s_mlp_set_tensor_cores(m, True)
+    Fd, yd = dev(F), dev(yv)
+    losses = I.icd2s_mlp_train(m, Fd.data_ptr(), yd.data_ptr(), rows, steps=400, batch=256, lr=3e-3)
+    _, Wb1 = I.icd2s_mlp_get_weights(m)
+    I.icd2s_mlp_destroy(m)
+    l0, l1 = M.loss(Wb0, F, yv), M.loss(Wb1, F, yv)
+    p = yv.mean()
+    base = -(p * np.log(p) + (1 - p) * np.log(1 - p))
+    assert np.all(np.isfinite(losses))
+    assert l1 < 0.5 * l0 and l1 < 0.5 * base
