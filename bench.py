@@ -202,7 +202,10 @@ def run_reference(args, w):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": dict(workload=args.workload, **{k: w[k] for k in ("n", "density", "z", "K", "m_min", "m_max",
                                                                           "sweeps", "alpha", "c", "mut_rate")},
-                           replicas_per_sample_step=z_s, l2="n/a (CPU)"),
+                           replicas_per_sample_step=z_s, l2="n/a (CPU)",
+                           differs_from_gpu_line="only in the replicas sampled per step (%d of %d); every replica "
+                                                 "of a phase does the same work, so attempts/s is comparable"
+                                                 % (z_s, w["z"])),
             "cpu_baseline": dict({"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
                                  **n_core_ideal(value)),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
