@@ -63,13 +63,13 @@ def broadcast_x(dist, torch, x_or_none, n, owner, device, group=None):
 class ShardedState:
     """This rank's shard of a solution set of z_total replicas on the current GPU."""
 
-    def __init__(self, I, torch, dist, q, n: int, z_total: int, seed: int, group=None):
-        self.I, self.torch, self.dist, self.group = I, torch, dist, group
+    def __init__(self, I, torch, dist, q, n: int, z_total: int, seed: int, group=None, device="cuda"):
+        self.I, self.torch, self.dist, self.group, self.device = I, torch, dist, group, device
         self.n, self.z_total = n, z_total
         rank, world = dist.get_rank(group), dist.get_world_size(group)
         self.base, self.count = shard_range(z_total, rank, world)
         self.st = I.icd2s_state_create_shard(q, self.count, self.base, z_total, seed)
-        self.counts = torch.zeros(n, dtype=torch.int32, device="cuda")
+        self.counts = torch.zeros(n, dtype=torch.int32, device=device)
 
     def close(self):
         if self.st is not None:
@@ -77,7 +77,7 @@ class ShardedState:
             self.st = None
 
     def _stream(self):
-        return self.torch.cuda.current_stream().cuda_stream
+        return self.torch.cuda.current_stream().cuda_stream if self.device == "cuda" else 0
 
     def initial_pass(self, p):
         """Call_IM_Solution_Set (each replica on its own) and the first best update."""
@@ -96,7 +96,7 @@ class ShardedState:
         """(energy, global replica, x) of the method's best over every shard."""
         E, r, stamp = self.I.icd2s_get_best_info(self.st)
         x = self.I.icd2s_get_best(self.st, self.n)[0] if r >= 0 else None
-        owner, E, r, _ = best_owner(self.dist, self.torch, (E, r, stamp), "cuda", self.group)
+        owner, E, r, _ = best_owner(self.dist, self.torch, (E, r, stamp), self.device, self.group)
         if owner < 0:
             return None, -1, None
-        return E, r, broadcast_x(self.dist, self.torch, x, self.n, owner, "cuda", self.group)
+        return E, r, broadcast_x(self.dist, self.torch, x, self.n, owner, self.device, self.group)
