@@ -803,15 +803,18 @@ def run_ttt(args):
         spec = TTT_INSTANCES[name]
         n = spec["n"]
         q = I.icd2s_qubo_create(make_qubo(n, spec["density"], spec["qseed"]))
-        E_star, longs = ttt_target(I, q, n, args.ttt_budget)
-        res = dict(target_E=E_star, target_runs=longs, budget_iters=args.ttt_budget)
-        res.update(ttt_methods(I, q, n, mlp, E_star, list(TTT_METHODS), args.ttt_seeds, args.ttt_budget))
+        am = args.ttt_alpha
+        E_star, longs = ttt_target(I, q, n, args.ttt_budget, am)
+        res = dict(target_E=E_star, target_runs=longs, budget_iters=args.ttt_budget, alpha="%dn" % am)
+        res.update(ttt_methods(I, q, n, mlp, E_star, list(TTT_METHODS), args.ttt_seeds, args.ttt_budget,
+                               None if am == 5 else am))
         I.icd2s_qubo_destroy(q)
         results[name] = res
     I.icd2s_mlp_destroy(mlp)
     line = {"metric": "time-to-target energy", "unit": "ms", "higher_is_better": False, "n_gpus": 1,
             "data": "synthetic", "dtype": "int32/int64 (network: bf16 weights, f32)",
-            "config": {"workload": "time-to-target, z=32, alpha=5n, c=n/150, 256 sweeps, T 2000->1, Eq. 5 mutation",
+            "config": {"workload": "time-to-target, z=32, alpha=%dn, c=n/150, 256 sweeps, T 2000->1, Eq. 5 mutation"
+                                   % args.ttt_alpha,
                        "methods": {k: dict(K=v[0], m_min=v[1], m_max=v[2], select_mode=v[3], ablation=v[4],
                                            im_order=v[5], alpha=f"{v[6]}n")
                                    for k, v in TTT_METHODS.items()}},
@@ -890,6 +893,7 @@ def main():
     ap.add_argument("--ttt-seeds", type=int, default=10)
     ap.add_argument("--ttt-budget", type=int, default=30, help="outer iterations per measured run")
     ap.add_argument("--ttt-instances", default="n5000-d0.5,n10000-d0.5")
+    ap.add_argument("--ttt-alpha", type=int, default=5, help="Tabu search length alpha / n of every method")
     ap.add_argument("--sweep", action="store_true", help="time to target as z, alpha and c vary (n = 5000)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
