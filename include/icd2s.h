@@ -172,10 +172,12 @@ int icd2s_default_params(int32_t n, icd2s_params* out);
 int icd2s_qubo_create(const int8_t* Q_host, int32_t n, icd2s_qubo** out);
 int icd2s_qubo_destroy(icd2s_qubo* q);
 int icd2s_qubo_size(const icd2s_qubo* q, int32_t* n_out);
-/* 2 max_j sum_i |Q_ij|, computed once at creation: no gain
- * g_j = (1 - 2x_j)(Q_jj + 2 sum_{i != j} Q_ij x_i) of any x exceeds it in
- * magnitude (Section 2.4).  The Tabu search uses it to decide whether a move
- * fits a 32-bit key. */
+/* The largest gain magnitude of the instance over every x, computed once at
+ * creation: max_j max(|Q_jj - 2 N_j|, |Q_jj + 2 P_j|), with P_j and N_j the
+ * sums of the positive and of the negative off-diagonal entries of column j
+ * in magnitude (g_j = (1 - 2x_j)(Q_jj + 2 sum_{i != j} Q_ij x_i), Section 2.4;
+ * the bound is attained by some x).  The Tabu search uses it to decide
+ * whether a move fits a 32-bit key. */
 int icd2s_qubo_gain_bound(const icd2s_qubo* q, int64_t* bound_out);
 
 /* Eq. 1 for `count` binary rows x_dev[count][n] (dense, row stride n, values

@@ -126,9 +126,14 @@ struct icd2s_qubo {
     int32_t* diag = nullptr;
     int32_t* eta = nullptr;
     int32_t* etahat = nullptr;
-    long long gain_bound = 0;  // 2 max_j sum_i |Q_ij|: bounds every gain of every solution
+    long long gain_bound = 0;  // max over j and x of |g_j|: bounds every gain of every solution (attained)
     int8_t* Q2 = nullptr;      // signed row pairs for the Tabu search (made when a state asks for them)
     bool has_m128 = false;     // an entry is -128: no signed rows (its negation is not an int8)
+    // Q on parity labels (even Q_jj first), made at creation when the gain bound
+    // is too wide for the compact Tabu keys on indices but fits them on labels
+    int8_t* Qpk = nullptr;
+    int32_t* pk_perm = nullptr;
+    int pk_n0 = 0;
     // scratch of icd2s_energy (grown on demand)
     int cap = 0;
     uint8_t* xpad = nullptr;
@@ -374,6 +379,8 @@ int icd2s_qubo_create(const int8_t* Q_host, int32_t n, icd2s_qubo** out)
         if (q->Q) cudaFree(q->Q);
         if (q->diag) cudaFree(q->diag);
         if (q->Q2) cudaFree(q->Q2);
+        if (q->Qpk) cudaFree(q->Qpk);
+        if (q->pk_perm) cudaFree(q->pk_perm);
         if (q->eta) cudaFree(q->eta);
         if (q->etahat) cudaFree(q->etahat);
         delete q;
@@ -383,20 +390,37 @@ int icd2s_qubo_create(const int8_t* Q_host, int32_t n, icd2s_qubo** out)
     cudaError_t e;
     if ((e = dalloc(&q->Q, (size_t)n * q->ld)) != cudaSuccess || (e = dalloc(&q->diag, q->ld)) != cudaSuccess ||
         (e = dalloc(&q->eta, q->ld)) != cudaSuccess || (e = dalloc(&q->etahat, q->ld)) != cudaSuccess ||
-        (e = dalloc(&mism, 3)) != cudaSuccess)
+        (e = dalloc(&mism, 4)) != cudaSuccess)
         return bail(fail(ICD2S_ERR_OOM, "device allocation failed: %s", cudaGetErrorString(e)));
-    int got[3] = {0, 0, 0};  // symmetry mismatches, max_j eta_j, entries equal to -128
+    int got[4] = {0, 0, 0, 0};  // symmetry mismatches, max_j eta_j, entries equal to -128, max |g|
     if ((e = cudaMemset(q->Q, 0, (size_t)n * q->ld)) == cudaSuccess &&
         (e = cudaMemcpy2D(q->Q, q->ld, Q_host, n, n, n, cudaMemcpyHostToDevice)) == cudaSuccess &&
-        (e = cudaMemset(mism, 0, 3 * sizeof(int))) == cudaSuccess &&
-        (e = launch_prepare(q->Q, n, q->ld, q->eta, q->etahat, q->diag, mism, mism + 1, 0)) == cudaSuccess &&
-        (e = cudaMemcpy(got, mism, 3 * sizeof(int), cudaMemcpyDeviceToHost)) == cudaSuccess) {
+        (e = cudaMemset(mism, 0, 4 * sizeof(int))) == cudaSuccess &&
+        (e = launch_prepare(q->Q, n, q->ld, q->eta, q->etahat, q->diag, mism, mism + 1, mism + 3, 0)) ==
+            cudaSuccess &&
+        (e = cudaMemcpy(got, mism, 4 * sizeof(int), cudaMemcpyDeviceToHost)) == cudaSuccess) {
         cudaFree(mism);
         mism = nullptr;
         const int bad = got[0];
-        q->gain_bound = 2LL * got[1];
+        q->gain_bound = got[3];
         q->has_m128 = got[2] != 0;
         if (bad) return bail(fail(ICD2S_ERR_ASYMMETRIC, "Q is not symmetric (%d mismatched entries)", bad));
+        // parity labels: the variables with an even diagonal, then the odd ones
+        std::vector<int32_t> perm(n);
+        int n0 = 0;
+        for (int j = 0; j < n; ++j)
+            if ((Q_host[(size_t)j * n + j] & 1) == 0) perm[n0++] = j;
+        for (int j = 0, k = n0; j < n; ++j)
+            if ((Q_host[(size_t)j * n + j] & 1) != 0) perm[k++] = j;
+        if (tabu_key_shift(n, q->gain_bound) == 0 && tabu_key_shift_pk(n0, n - n0, q->gain_bound) > 0) {
+            if ((e = dalloc(&q->Qpk, (size_t)n * q->ld)) != cudaSuccess || (e = dalloc(&q->pk_perm, n)) != cudaSuccess)
+                return bail(fail(ICD2S_ERR_OOM, "device allocation failed: %s", cudaGetErrorString(e)));
+            q->pk_n0 = n0;
+            if ((e = cudaMemcpy(q->pk_perm, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = launch_relabel(q->Q, q->pk_perm, n, q->ld, q->Qpk, 0)) != cudaSuccess ||
+                (e = cudaDeviceSynchronize()) != cudaSuccess)
+                return bail(fail(ICD2S_ERR_CUDA, "qubo_create: %s", cudaGetErrorString(e)));
+        }
         *out = q;
         return ICD2S_OK;
     }
@@ -407,7 +431,7 @@ int icd2s_qubo_create(const int8_t* Q_host, int32_t n, icd2s_qubo** out)
 int icd2s_qubo_destroy(icd2s_qubo* q)
 {
     if (!q) return ICD2S_OK;
-    void* ptrs[] = {q->Q, q->Q2, q->diag, q->eta, q->etahat, q->xpad, q->hpad, q->Qb};
+    void* ptrs[] = {q->Q, q->Q2, q->Qpk, q->pk_perm, q->diag, q->eta, q->etahat, q->xpad, q->hpad, q->Qb};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete q;
@@ -487,6 +511,7 @@ int icd2s_state_create_shard(icd2s_qubo* q, int32_t replicas, int32_t replica_ba
     d.Q = q->Q; d.diag = q->diag; d.etahat = q->etahat; d.n = q->n; d.ld = q->ld; d.R = replicas;
     d.gain_bound = q->gain_bound;
     d.Q2 = nullptr;  // signed rows only once the state asks for them
+    d.Qpk = q->Qpk; d.pk_perm = q->pk_perm; d.pk_n0 = q->pk_n0;
     d.X = st->X; d.G = st->G; d.E = st->E; d.T = st->T; d.C = st->C; d.gamma = st->gamma; d.A = st->A;
     d.delta = st->delta; d.order = st->order; d.sel = st->sel; d.FL = st->FL; d.FCNT = st->FCNT;
     d.DEACC = st->DEACC; d.DONE = st->DONE; d.best_x = st->best_x; d.best_E = st->best_E; d.flags = st->flags;

@@ -86,8 +86,12 @@ struct Dev {
     int32_t* H; float* F; float* score;
     int32_t* ACC; unsigned* TT; int apply_splits;     // split write-back: partial sums, tile tickets
     uint32_t k0, k1; // Philox key = seed halves
-    long long gain_bound;  // max_j 2 sum_i |Q_ij| >= |g_j| for every x
+    long long gain_bound;  // max over j and x of |g_j| (the Tabu keys' width depends on it)
     const int8_t* Q2;      // [2n][ld] signed rows: row 2i + x = (1 - 2x) Q_i (null unless asked for)
+    // Q on parity labels for the Tabu keys (null unless the instance needs them):
+    // Qpk[L][M] = Q[pk_perm[L]][pk_perm[M]], the pk_n0 variables with an even Q_jj
+    // first, each class in index order
+    const int8_t* Qpk; const int32_t* pk_perm; int pk_n0;
     uint16_t* TL; long long tl_cap;  // Tabu move logs [R][tl_cap] for searches whose log exceeds shared memory
     // replica sharding: these R replicas are replicas p0 .. p0 + R - 1 of a set of
     // z_total (every random stream is keyed by the global replica index; gamma is
@@ -103,9 +107,12 @@ void set_error_message(const char* msg);
 
 // ---- launchers (each returns cudaGetLastError() of its launch) ----
 // eta_max[0] receives max_j eta_j (eta_j = sum_i |Q_ij|), eta_max[1] the
-// number of entries equal to -128.
+// number of entries equal to -128; gain_max (zeroed by the caller) the largest
+// |g_j| over all j and x.
 cudaError_t launch_prepare(const int8_t* Q, int n, int ld, int32_t* eta, int32_t* etahat, int32_t* diag,
-                           int* mismatches, int* eta_max, cudaStream_t s);
+                           int* mismatches, int* eta_max, int* gain_max, cudaStream_t s);
+// Qpk[L][M] = Q[perm[L]][perm[M]] for L, M < n; padding columns 0.
+cudaError_t launch_relabel(const int8_t* Q, const int32_t* perm, int n, int ld, int8_t* Qpk, cudaStream_t s);
 // Q2[2i + x][j] = (1 - 2x) Q[i][j] (Q without -128 entries; padding columns 0).
 cudaError_t launch_signed_rows(const int8_t* Q, int n, int ld, int8_t* Q2, cudaStream_t s);
 cudaError_t launch_init_x(const Dev& d, cudaStream_t s);
@@ -122,6 +129,8 @@ cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_
                         bool wide_keys = false, int rows = 0, int cluster = 1);
 // Shift of the compact Tabu keys for n and the instance's gain bound (0: they do not apply).
 int tabu_key_shift(int n, long long gain_bound);
+// The shift of the compact keys on parity labels (0: they do not apply either).
+int tabu_key_shift_pk(int n_even, int n_odd, long long gain_bound);
 size_t tabu_smem_bytes(int n, int alpha);
 constexpr size_t kTabuSmemLimit = 227 * 1024;
 // false: the Tabu move log of alpha moves goes to global memory (Dev::TL, tl_cap >= alpha)

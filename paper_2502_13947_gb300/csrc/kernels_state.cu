@@ -317,8 +317,11 @@ int device_sm_count()
 // ---------------------------------------------------------------------------
 // Per-instance preparation.  k_symcheck compares 32 x 32 tiles of Q with the
 // transposed tiles (counts mismatches); k_eta forms eta_j = sum_i |Q_ij|
-// (Eq. 6) and the diagonal, one thread per column (coalesced across j);
-// k_etahat normalises by the maximum (Q16, floor).
+// (Eq. 6), the diagonal and the column's largest gain over all x (one thread
+// per column, coalesced across j): with P_j / N_j the sums of the positive /
+// negative off-diagonal entries' magnitudes, Q_jj + 2 sum_{i != j} Q_ij x_i
+// ranges over [Q_jj - 2 N_j, Q_jj + 2 P_j], so max |g_j| = max(|Q_jj - 2 N_j|,
+// |Q_jj + 2 P_j|), attained; k_etahat normalises eta by its maximum (Q16, floor).
 // ---------------------------------------------------------------------------
 __global__ void k_symcheck(const int8_t* __restrict__ Q, int n, int ld, int* mismatches)
 {
@@ -337,20 +340,27 @@ __global__ void k_symcheck(const int8_t* __restrict__ Q, int n, int ld, int* mis
     if (threadIdx.x == 0 && bad) atomicAdd(mismatches, bad);
 }
 
-__global__ void k_eta(const int8_t* __restrict__ Q, int n, int ld, int32_t* eta, int32_t* diag, int* n128)
+__global__ void k_eta(const int8_t* __restrict__ Q, int n, int ld, int32_t* eta, int32_t* diag, int* n128,
+                      int* gmax)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= ld) return;
     if (j >= n) { eta[j] = 0; diag[j] = 0; return; }
-    int s = 0, m = 0;
+    int s = 0, m = 0, pos = 0, neg = 0;
     for (int i = 0; i < n; ++i) {
         const int v = Q[(size_t)i * ld + j];
         s += abs(v);
         m += v == -128;
+        if (i != j) {
+            pos += v > 0 ? v : 0;
+            neg += v < 0 ? -v : 0;
+        }
     }
     eta[j] = s;
-    diag[j] = Q[(size_t)j * ld + j];
+    const int qjj = Q[(size_t)j * ld + j];
+    diag[j] = qjj;
     if (m) atomicAdd(n128, m);
+    atomicMax(gmax, max(abs(qjj - 2 * neg), abs(qjj + 2 * pos)));
 }
 
 __global__ __launch_bounds__(1024) void k_etahat(const int32_t* __restrict__ eta, int n, int ld, int32_t* etahat,
@@ -390,6 +400,23 @@ __global__ void k_signed_rows(const int8_t* __restrict__ Q, int n, int ld, int8_
     *reinterpret_cast<uint4*>(Q2 + (2 * i + 1) * ld + 16 * c) = make_uint4(m[0], m[1], m[2], m[3]);
 }
 
+// One CTA per row of the relabeled matrix; the label table is read through L1.
+__global__ void k_relabel(const int8_t* __restrict__ Q, const int32_t* __restrict__ perm, int n, int ld,
+                          int8_t* __restrict__ Qpk)
+{
+    const int L = blockIdx.x;
+    const int8_t* src = Q + (size_t)perm[L] * ld;
+    int8_t* dst = Qpk + (size_t)L * ld;
+    for (int M = threadIdx.x; M < ld; M += blockDim.x) dst[M] = M < n ? src[perm[M]] : (int8_t)0;
+}
+
+cudaError_t launch_relabel(const int8_t* Q, const int32_t* perm, int n, int ld, int8_t* Qpk, cudaStream_t s)
+{
+    k_relabel<<<n, 256, 0, s>>>(Q, perm, n, ld, Qpk);
+    note_launch(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_signed_rows(const int8_t* Q, int n, int ld, int8_t* Q2, cudaStream_t s)
 {
     const size_t chunks = (size_t)n * (ld / 16);
@@ -399,14 +426,14 @@ cudaError_t launch_signed_rows(const int8_t* Q, int n, int ld, int8_t* Q2, cudaS
 }
 
 cudaError_t launch_prepare(const int8_t* Q, int n, int ld, int32_t* eta, int32_t* etahat, int32_t* diag,
-                           int* mismatches, int* eta_max, cudaStream_t s)
+                           int* mismatches, int* eta_max, int* gain_max, cudaStream_t s)
 {
     const int tiles = (n + 31) / 32;
     k_symcheck<<<dim3(tiles, tiles), dim3(32, 8), 0, s>>>(Q, n, ld, mismatches);
     note_launch(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_eta<<<(ld + 255) / 256, 256, 0, s>>>(Q, n, ld, eta, diag, eta_max + 1);
+    k_eta<<<(ld + 255) / 256, 256, 0, s>>>(Q, n, ld, eta, diag, eta_max + 1, gain_max);
     note_launch(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_etahat<<<1, 1024, 0, s>>>(eta, n, ld, etahat, eta_max);

@@ -28,8 +28,18 @@
 // |g| < 2^(31 - sh) - 1 with sh = 1 + (bits of n), the whole move fits one
 // 32-bit key (g + 2^(31 - sh)) << sh | j << 1 | x_j, so the warp and the block
 // each take their arg-min with a single redux.sync and the key carries x_i.
-// The bound |g_j| <= |Q_jj| + 2 sum_{i != j} |Q_ij| <= 2 sum_i |Q_ij| holds for
-// every x, so it is computed once per instance.
+// The bound max_j max(|Q_jj - 2 N_j|, |Q_jj + 2 P_j|) (P_j, N_j: the positive
+// and negative off-diagonal sums of column j in magnitude) holds for every x
+// and is attained, so it is computed once per instance.
+// Parity labels (PK), where that bound is one bit too wide: g_j is congruent
+// to Q_jj mod 2 for every x, so the gain field's lowest bit already names the
+// parity class of the variable, and within a class the rank r of j (in index
+// order) identifies it.  The search then runs on Q relabeled with the n0
+// even-diagonal variables first (label L = r, or n0 + r for the odd class) and
+// the key (g + 2^(31 - sh)) << sh | r << 1 | x_j needs sh - 1 = bits of the
+// larger class instead of bits of n.  Key order is still (g, j): equal gains
+// share a class, where ranks follow j.  The state is gathered through the
+// labels at the start and scattered back at the end.
 // Each variable's update is one dp4a of the row word with the byte
 // 2 (1 - 2 x_i) in the variable's lane.  Signed rows (SR, on request; not for
 // Q with an entry -128): the rows (1 - 2x) Q_i interleaved, row 2i + x, so the
@@ -169,10 +179,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 // g < OVmin - OV, which in key units is (key >> shift) < OVmin - OV + bias.
 // G: CTAs per replica (a thread-block cluster of G; 1 = no cluster); each owns
 // `slice` variables (a multiple of 128; G slice >= ld).
-template <int W, int MAXT, bool ASP, bool CK, bool SR, int G>
+template <int W, int MAXT, bool ASP, bool CK, bool SR, int G, bool PK = false>
 __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh, int slice)
 {
     static_assert(4 * W <= (1 << kKeyShift), "the local index must fit the key");
+    static_assert(!PK || (CK && G == 1 && !SR), "parity labels: compact keys, one CTA per replica, plain rows");
     extern __shared__ __align__(16) unsigned char smem[];
     // warp keys of the arg-min: wide keys [2][32] (+0), and with the cluster split
     // and aspiration the unmasked ones [2][32] (+512); compact keys [2][32] (+0)
@@ -201,7 +212,9 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh, 
     const int n = d.n, ld = d.ld;
     const int lo = G > 1 ? rank * slice : 0;                 // owned variables [lo, hi)
     const int hi = G > 1 ? min(lo + slice, ld) : ld;
-    const int8_t* __restrict__ Q = d.Q;
+    const int8_t* __restrict__ Q = PK ? d.Qpk : d.Q;   // PK: rows and columns in label order
+    const int32_t* __restrict__ lab = d.pk_perm;        // PK: label -> variable
+    const unsigned n0 = PK ? (unsigned)d.pk_n0 : 0u;
     const int8_t* __restrict__ Q2 = d.Q2;  // SR: row 2i + x = (1 - 2x) Q_i
     uint8_t* xrow = d.X + (size_t)p * ld;
     int32_t* grow = d.G + (size_t)p * ld;
@@ -221,10 +234,11 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh, 
     int gf[W][4], fa[W][4];
     // 2^shift (1 - 2 x_j) mod 2^32: the key is gf * s32 + kc, one multiply-add
     unsigned s32[W][4];
-    // CK: kc = bias << sh | j << 1 | x_j; otherwise the constant bias << 5 | local index
+    // CK: kc = bias << sh | j << 1 | x_j (PK: the rank r in place of j); otherwise
+    // the constant bias << 5 | local index
     unsigned kc[W][4];
     const unsigned cbias = CK ? 1u << (31 - sh) : kKeyBias;
-    const unsigned imask = CK ? (1u << (sh - 1)) - 1u : 0u;  // CK: the index field (2^(sh-1) > n)
+    const unsigned imask = CK ? (1u << (sh - 1)) - 1u : 0u;  // CK: the index field (2^(sh-1) > n; PK: > each class)
     unsigned xb = 0;  // bit 4w+b = x of the owned variable
 #pragma unroll
     for (int w = 0; w < W; ++w) {
@@ -232,9 +246,19 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh, 
         int gv[4] = {0, 0, 0, 0};
         uint32_t xv = 0;
         if (j0 < hi) {
-            const int4 g4 = *reinterpret_cast<const int4*>(grow + j0);
-            xv = *reinterpret_cast<const uint32_t*>(xrow + j0);
-            gv[0] = g4.x; gv[1] = g4.y; gv[2] = g4.z; gv[3] = g4.w;
+            if constexpr (PK) {  // gathered through the labels (padding: 0)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (j0 + b < n) {
+                        const int v = lab[j0 + b];
+                        gv[b] = grow[v];
+                        xv |= (uint32_t)(xrow[v] & 1u) << (8 * b);
+                    }
+            } else {
+                const int4 g4 = *reinterpret_cast<const int4*>(grow + j0);
+                xv = *reinterpret_cast<const uint32_t*>(xrow + j0);
+                gv[0] = g4.x; gv[1] = g4.y; gv[2] = g4.z; gv[3] = g4.w;
+            }
         }
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
@@ -243,8 +267,9 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh, 
             gf[w][b] = xj ? -gv[b] : gv[b];
             const unsigned one = CK ? 1u << sh : 1u << kKeyShift;
             s32[w][b] = xj ? 0u - one : one;
-            kc[w][b] = CK ? (cbias << sh) | ((unsigned)(j0 + b) << 1) | xj
-                          : (kKeyBias << kKeyShift) | (unsigned)(4 * w + b);
+            unsigned jk = (unsigned)(j0 + b);  // the key's index: j, or (PK) the rank in the class
+            if constexpr (PK) jk = jk >= (unsigned)n ? imask : (jk >= n0 ? jk - n0 : jk);
+            kc[w][b] = CK ? (cbias << sh) | (jk << 1) | xj : (kKeyBias << kKeyShift) | (unsigned)(4 * w + b);
             fa[w][b] = (j0 + b < n && j0 < hi) ? 0 : INT_MAX;  // padding never becomes free
         }
     }
@@ -369,6 +394,12 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh, 
         // the chosen move: index and value (CK: no candidate is the key ~0,
         // whose index field 2^(sh-1) - 1 >= n; otherwise its index half is ~0)
         unsigned jx = CK ? (unsigned)key & (2u * imask + 1u) : (unsigned)key;
+        if constexpr (PK) {
+            // the label: the rank, plus n0 for the odd class (the gain's parity,
+            // bit sh of the key); no candidate (all ones) gives imask + n0 >= n
+            const unsigned L = (((unsigned)key >> 1) & imask) + (((unsigned)key >> sh) & 1u) * n0;
+            jx = (L << 1) | ((unsigned)key & 1u);
+        }
         // Without aspiration at most c - 1 <= n - 1 variables are tabu, so a
         // move always exists; the clamp only keeps the row read in bounds.
         // (With the cluster split the fallback key always names a variable.)
@@ -495,7 +526,7 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh, 
         __syncthreads();
     }
     int32_t* Tout = d.T + (size_t)p * ld;
-    for (int j = lo + tid; j < hi; j += NT) Tout[j] = Ts[j];
+    for (int j = lo + tid; j < hi; j += NT) Tout[PK && j < n ? lab[j] : j] = Ts[j];
     __syncthreads();  // T has been read out before the flip list reuses it
     int32_t* flist = Ts;
     if constexpr (G > 1) {
@@ -552,7 +583,7 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh, 
             int xj = (int)((xb >> (4 * w + b)) & 1u);
             int gj = 0, cj = 0;
             if (j < n) {
-                const int dj = d.diag[j];
+                const int dj = d.diag[PK ? lab[j] : j];
                 const int h = (gf[w][b] - dj) / 2 + acc[w][b];   // (1 - 2x) g = Q_jj + 2 h
                 xj ^= (int)((undo[j >> 5] >> (j & 31)) & 1u);
                 gj = (1 - 2 * xj) * (dj + 2 * h);
@@ -564,9 +595,19 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh, 
             cv[b] = cj;
             xv |= (uint32_t)xj << (8 * b);
         }
-        *reinterpret_cast<int4*>(grow + j0) = make_int4(gv[0], gv[1], gv[2], gv[3]);
-        *reinterpret_cast<int4*>(Cout + j0) = make_int4(cv[0], cv[1], cv[2], cv[3]);
-        *reinterpret_cast<uint32_t*>(xrow + j0) = xv;
+        if constexpr (PK) {  // scattered back through the labels
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int v = j0 + b < n ? lab[j0 + b] : j0 + b;
+                grow[v] = gv[b];
+                Cout[v] = cv[b];
+                xrow[v] = (uint8_t)(xv >> (8 * b));
+            }
+        } else {
+            *reinterpret_cast<int4*>(grow + j0) = make_int4(gv[0], gv[1], gv[2], gv[3]);
+            *reinterpret_cast<int4*>(Cout + j0) = make_int4(cv[0], cv[1], cv[2], cv[3]);
+            *reinterpret_cast<uint32_t*>(xrow + j0) = xv;
+        }
     }
     if (tid == 0 && rank == 0) d.E[p] = OVmin;
 }
@@ -587,7 +628,7 @@ int tabu_slice(int n, int G)
     return G <= 1 ? round_up(n, kLdAlign) : round_up((n + G - 1) / G, kLdAlign);
 }
 
-template <int W, int MAXT, bool ASP, bool CK, bool SR, int G>
+template <int W, int MAXT, bool ASP, bool CK, bool SR, int G, bool PK = false>
 static cudaError_t launch_tabu_w(const Dev& d, int alpha, int c, int sh, cudaStream_t s)
 {
     const int slice = tabu_slice(d.n, G);
@@ -597,7 +638,7 @@ static cudaError_t launch_tabu_w(const Dev& d, int alpha, int c, int sh, cudaStr
     const bool in_smem = tabu_log_in_smem(d.n, alpha);
     if (!in_smem && (!d.TL || d.tl_cap < alpha)) return cudaErrorInvalidValue;
     const size_t sm = tabu_smem_bytes(d.n, in_smem ? alpha : 0);
-    auto kern = k_tabu<W, MAXT, ASP, CK, SR, G>;
+    auto kern = k_tabu<W, MAXT, ASP, CK, SR, G, PK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     // as little shared memory as the block needs: the rest of the SM's 256 KB
@@ -632,10 +673,18 @@ static cudaError_t launch_tabu_w(const Dev& d, int alpha, int c, int sh, cudaStr
 }
 
 // One kernel shape: picks the build for aspiration, compact keys (sh > 0; only
-// where CKOK) and signed rows; G CTAs per replica.
+// where CKOK; sh < 0: compact keys on parity labels, shift -sh, one CTA per
+// replica, plain rows) and signed rows; G CTAs per replica.
 template <int W, int MAXT, bool CKOK, int G>
 static cudaError_t launch_shape(const Dev& d, int alpha, int c, int sh, bool asp, bool sr, cudaStream_t s)
 {
+    if constexpr (CKOK && G == 1) {
+        if (sh < 0) {
+            if (asp) return launch_tabu_w<W, MAXT, true, true, false, 1, true>(d, alpha, c, -sh, s);
+            return launch_tabu_w<W, MAXT, false, true, false, 1, true>(d, alpha, c, -sh, s);
+        }
+    }
+    if (sh < 0) sh = 0;   // (other shapes: the wide keys)
     if constexpr (CKOK) {
         if (sh) {
             if (asp) return sr ? launch_tabu_w<W, MAXT, true, true, true, G>(d, alpha, c, sh, s)
@@ -686,6 +735,17 @@ int tabu_key_shift(int n, long long gain_bound)
     return sh <= 30 && gain_bound + 1 < (1LL << (31 - sh)) ? sh : 0;
 }
 
+// The same for the keys on parity labels: the index field holds the rank in
+// the larger parity class.
+int tabu_key_shift_pk(int n_even, int n_odd, long long gain_bound)
+{
+    const int m = n_even > n_odd ? n_even : n_odd;
+    int ib = 0;
+    while ((1 << ib) <= m) ++ib;
+    const int sh = ib + 1;
+    return sh <= 30 && gain_bound + 1 < (1LL << (31 - sh)) ? sh : 0;
+}
+
 // CTAs per replica when the caller leaves it open.  The exchange through
 // distributed shared memory costs about as much per move as the work a split
 // saves up to n of several thousand (GB300, z = 32: n = 2500 one CTA 3.6 ms, two
@@ -706,13 +766,16 @@ int tabu_default_cluster(int n, int R, int sm_count)
 cudaError_t launch_tabu(const Dev& d, int alpha, int c, int variant, cudaStream_t s, bool aspiration, bool wide_keys,
                         int rows, int cluster)
 {
-    const int sh = wide_keys ? 0 : tabu_key_shift(d.n, d.gain_bound);
+    int sh = wide_keys ? 0 : tabu_key_shift(d.n, d.gain_bound);
     int G = cluster == 0 ? tabu_default_cluster(d.n, d.R, device_sm_count()) : cluster;
     if (G != 1 && G != 2 && G != 4) return cudaErrorInvalidValue;
     // a default split gives way to a kernel shape chosen for one CTA per replica
     if (cluster == 0 && variant >= 0 && !tabu_variant_fits(variant, d.n, G)) G = 1;
     if (variant < 0) variant = tabu_default_variant(d.n, G);
     if (!tabu_variant_fits(variant, d.n, G)) return cudaErrorInvalidConfiguration;
+    // a gain bound one bit too wide for the compact keys: the parity labels, where the
+    // instance has them (one CTA per replica)
+    if (!wide_keys && sh == 0 && G == 1 && d.Qpk) sh = -tabu_key_shift_pk(d.pk_n0, d.n - d.pk_n0, d.gain_bound);
     const bool sr = d.Q2 != nullptr && rows == 2;
     // the 1024-thread shapes with 12 and 16 variables per thread would spill the
     // per-variable key constants: they keep the wide keys (and one CTA per replica)

@@ -167,7 +167,30 @@ def _compact_shift(n, bound):
     return sh if bound + 1 < (1 << (31 - sh)) else 0
 
 
-def _tabu_both_keys(P, X0, alpha, c, asp, variant=-1):
+def _pk_shift(Q, bound):
+    """The same for the keys on parity labels (one CTA per replica): the index
+    field holds the rank of a variable within its class of Q_jj mod 2."""
+    odd = int((np.diag(Q).astype(np.int64) & 1).sum())
+    sh = max(odd, Q.shape[0] - odd).bit_length() + 1
+    return sh if bound + 1 < (1 << (31 - sh)) else 0
+
+
+def _attained_bound(Q):
+    """max_j max(|Q_jj - 2 N_j|, |Q_jj + 2 P_j|), P_j / N_j the positive /
+    negative off-diagonal sums of column j in magnitude, and an x attaining
+    it: column j's couplings of the sign that widens it on, x_j = 0."""
+    Qi = Q.astype(np.int64)
+    d = np.diag(Qi).copy()
+    off = Qi - np.diag(d)
+    P, N = np.clip(off, 0, None).sum(axis=0), np.clip(-off, 0, None).sum(axis=0)
+    hi, lo = np.abs(d + 2 * P), np.abs(d - 2 * N)
+    j = int(np.maximum(hi, lo).argmax())
+    x = ((off[:, j] > 0) if hi[j] >= lo[j] else (off[:, j] < 0)).astype(np.uint8)
+    x[j] = 0
+    return int(max(hi[j], lo[j])), x
+
+
+def _tabu_both_keys(P, X0, alpha, c, asp, variant=-1, cluster=0):
     """Runs the search with the compact keys (where the instance allows them)
     and with the wide keys, each with the signed row pairs (where the
     instance has them) and with the plain rows, from the same start; returns
@@ -176,7 +199,8 @@ def _tabu_both_keys(P, X0, alpha, c, asp, variant=-1):
     for wide in (0, 1):
         for rows in (1, 2):
             P.load(X0)
-            I.icd2s_set_tuning(P.st, tabu_variant=variant, tabu_wide_keys=wide, tabu_rows=rows)
+            I.icd2s_set_tuning(P.st, tabu_variant=variant, tabu_wide_keys=wide, tabu_rows=rows,
+                               tabu_cluster=cluster)
             (I.icd2s_tabu_aspiration if asp else I.icd2s_tabu)(P.st, alpha, c)
             out.append(P.state() + I.icd2s_get_tabu(P.st, P.R, P.n))
     return out
@@ -193,19 +217,18 @@ def _check_tabu(orc, Q, X0, alpha, c, asp, res):
 
 @pytest.mark.parametrize("n,density,seed", [(40, 1.0, 2), (2500, 0.1, 3), (5000, 0.5, 4), (700, 1.0, 5)])
 def test_gain_bound(L, orc, n, density, seed):
-    """icd2s_qubo_gain_bound = 2 max_j sum_i |Q_ij|, and no gain of the
-    sampled solutions (nor of the worst-case solution of the heaviest column)
-    exceeds it."""
+    """icd2s_qubo_gain_bound is the largest gain magnitude over every x: the
+    oracle's gains of an x built to attain it reach it exactly, no gain of
+    sampled solutions exceeds it, and it lies within 2 max_j sum_i |Q_ij|."""
     Q = make_qubo(n, density, seed)
     q = I.icd2s_qubo_create(Q)
     bound = I.icd2s_qubo_gain_bound(q)
     I.icd2s_qubo_destroy(q)
-    colsum = np.abs(Q.astype(np.int64)).sum(axis=0)
-    assert bound == 2 * int(colsum.max())
-    j = int(colsum.argmax())
-    worst = (Q[:, j] > 0).astype(np.uint8)   # every positive coupling of j on, j off
-    worst[j] = 0
-    for x in list(random_solutions(n, 4, seed)) + [worst]:
+    want, worst = _attained_bound(Q)
+    assert bound == want
+    assert int(np.abs(orc.gains(Q, worst).astype(np.int64)).max()) == bound
+    assert bound <= 2 * int(np.abs(Q.astype(np.int64)).sum(axis=0).max())
+    for x in list(random_solutions(n, 4, seed)):
         assert int(np.abs(orc.gains(Q, x).astype(np.int64)).max()) <= bound
 
 
@@ -237,7 +260,7 @@ def test_tabu_with_entries_of_minus_128(L, orc, n, asp):
     R, alpha, c = 3, 3 * n, max(2, n // 50)
     q = I.icd2s_qubo_create(Q)
     st = I.icd2s_state_create(q, R, 5)
-    assert I.icd2s_qubo_gain_bound(q) == 2 * int(np.abs(Q.astype(np.int64)).sum(axis=0).max())
+    assert I.icd2s_qubo_gain_bound(q) == _attained_bound(Q)[0]
     X0 = random_solutions(n, R, 52)
     try:
         I.icd2s_set_tuning(st, tabu_rows=2)
@@ -250,28 +273,58 @@ def test_tabu_with_entries_of_minus_128(L, orc, n, asp):
         I.icd2s_qubo_destroy(q)
 
 
+@pytest.mark.parametrize("n,density,variant,asp", [(5000, 0.5, -1, 0), (5000, 0.5, -1, 1), (5000, 0.5, 5, 0),
+                                                   (5000, 0.5, 1, 1), (4800, 0.6, 5, 1), (4800, 0.6, 1, 0)])
+def test_tabu_parity_label_keys(L, orc, n, density, variant, asp):
+    """Instances whose gain bound is too wide for the compact keys on indices
+    but fits them on parity labels (Q relabeled with the even-diagonal
+    variables first): that search and the wide keys' give the oracle's, with
+    and without aspiration."""
+    R, alpha, c = 3, n, max(2, n // 50)
+    P = Problem(n, density, 7 * n + 1, R=R)
+    bound = I.icd2s_qubo_gain_bound(P.q)
+    assert _compact_shift(n, bound) == 0 and _pk_shift(P.Q, bound) > 0
+    X0 = random_solutions(n, R, n + 19)
+    for res in _tabu_both_keys(P, X0, alpha, c, asp, variant, cluster=1):
+        _check_tabu(orc, P.Q, X0, alpha, c, asp, res)
+    P.close()
+
+
+@pytest.mark.parametrize("mode", ["ck", "pk"])
 @pytest.mark.parametrize("extra", [0, 1])
-def test_tabu_compact_keys_at_the_gain_bound(L, orc, extra):
-    """n = 8192 (index field of 14 bits, key shift 15): the heaviest column
-    sums to 32767 (gain bound 65534, the largest the compact keys take) or,
-    with one more unit entry, 32768 (the wide keys only).  The start puts
-    the heavy variable at its extreme gains +-(127 + 2 * 32640) so the keys
-    span their whole range."""
+def test_tabu_keys_at_the_gain_bound(L, orc, mode, extra):
+    """n = 8192: a heavy variable h whose gain bound is the largest a 32-bit
+    key takes -- 65534 on indices (14-bit index field, shift 15), 2^(31 - s)
+    - 2 on parity labels (shift s from the larger class) -- or, with Q_hh one
+    larger, one more (the next wider keys).  Q_hh = 126 + extra and positive
+    couplings (entries of 127, the rest of 1) summing to (target - 126) / 2;
+    the start puts h at its extreme gains +-(Q_hh + 2 P_h), so the keys span
+    their whole range."""
     n, R, alpha, c, h = 8192, 2, 1500, 54, 5000
     Q = make_qubo(n, 0.0005, 91).astype(np.int16)
-    rng = np.random.Generator(np.random.PCG64(92))
-    nb = np.sort(rng.choice(np.setdiff1d(np.arange(n), [h]), 258 + extra, replace=False))
     Q[h, :] = 0
     Q[:, h] = 0
-    Q[h, h] = 127
-    Q[h, nb[:257]] = 127
-    Q[h, nb[257:]] = 1
+    Q[h, h] = 126 + extra
+    if mode == "ck":
+        target = 65534
+    else:
+        odd = int((np.diag(Q) & 1).sum())
+        target = (1 << (31 - (max(odd, n - odd).bit_length() + 1))) - 2
+    half = (target - 126) // 2
+    k127, k1 = half // 127, half % 127
+    rng = np.random.Generator(np.random.PCG64(92))
+    nb = np.sort(rng.choice(np.setdiff1d(np.arange(n), [h]), k127 + k1, replace=False))
+    Q[h, nb[:k127]] = 127
+    Q[h, nb[k127:]] = 1
     Q[nb, h] = Q[h, nb]
     Q = Q.astype(np.int8)
     q = I.icd2s_qubo_create(Q)
     bound = I.icd2s_qubo_gain_bound(q)
-    assert bound == 65534 + 2 * extra
-    assert (_compact_shift(n, bound) == 15) == (extra == 0)
+    assert bound == target + extra == _attained_bound(Q)[0]
+    if mode == "ck":
+        assert (_compact_shift(n, bound) == 15) == (extra == 0) and _pk_shift(Q, bound) > 0
+    else:
+        assert _compact_shift(n, bound) == 0 and (_pk_shift(Q, bound) > 0) == (extra == 0)
     st = I.icd2s_state_create(q, R, 3)
 
     class _P:
@@ -281,15 +334,14 @@ def test_tabu_compact_keys_at_the_gain_bound(L, orc, extra):
     P.load = lambda X: I.icd2s_state_load(st, X)
     P.state = lambda: I.icd2s_get_state(st, R, n)
     X0 = random_solutions(n, R, 93)
-    X0[:, nb[:257]] = 1
-    X0[:, nb[257:]] = 1
+    X0[:, nb] = 1
     X0[0, h], X0[1, h] = 0, 1          # the heavy variable's largest gain, and its negative
-    g0 = orc.gains(Q, X0[1])
-    assert int(g0[h]) == -(127 + 2 * (257 * 127 + 1 + extra))
+    assert int(orc.gains(Q, X0[0])[h]) == bound and int(orc.gains(Q, X0[1])[h]) == -bound
     try:
         for asp in (0, 1):
-            for res in _tabu_both_keys(P, X0, alpha, c, asp):
-                _check_tabu(orc, Q, X0, alpha, c, asp, res)
+            for cluster in (1, 0):     # one CTA per replica, and the default split (n >= 8192, R = 2)
+                for res in _tabu_both_keys(P, X0, alpha, c, asp, cluster=cluster):
+                    _check_tabu(orc, Q, X0, alpha, c, asp, res)
     finally:
         I.icd2s_state_destroy(st)
         I.icd2s_qubo_destroy(q)
