@@ -240,11 +240,13 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh, 
     const unsigned cbias = CK ? 1u << (31 - sh) : kKeyBias;
     const unsigned imask = CK ? (1u << (sh - 1)) - 1u : 0u;  // CK: the index field (2^(sh-1) > n; PK: > each class)
     unsigned xb = 0;  // bit 4w+b = x of the owned variable
+    uint32_t dq[W];   // byte b of dq[w] = Q_jj of the owned variable 4w+b (the moved variable's own term)
 #pragma unroll
     for (int w = 0; w < W; ++w) {
         const int j0 = lo + 4 * (tid + w * NT);
         int gv[4] = {0, 0, 0, 0};
         uint32_t xv = 0;
+        dq[w] = 0u;
         if (j0 < hi) {
             if constexpr (PK) {  // gathered through the labels (padding: 0)
 #pragma unroll
@@ -271,6 +273,7 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh, 
             if constexpr (PK) jk = jk >= (unsigned)n ? imask : (jk >= n0 ? jk - n0 : jk);
             kc[w][b] = CK ? (cbias << sh) | (jk << 1) | xj : (kKeyBias << kKeyShift) | (unsigned)(4 * w + b);
             fa[w][b] = (j0 + b < n && j0 < hi) ? 0 : INT_MAX;  // padding never becomes free
+            if (j0 + b < n && j0 < hi) dq[w] |= (uint32_t)(uint8_t)(int8_t)d.diag[PK ? lab[j0 + b] : j0 + b] << (8 * b);
         }
     }
 
@@ -421,18 +424,10 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh, 
             const int j0 = lo + 4 * (tid + w * NT);
             rv[w] = j0 < hi ? __ldg(reinterpret_cast<const int*>(row + j0)) : 0;
         }
-        // + 2 (1 - 2 x_i) Q_ij: one dp4a per variable with the byte 2 (1 - 2 x_i)
-        // in the variable's lane (the masks depend on the move only, so they are
-        // warp-uniform; signed rows already carry the sign)
-        unsigned msk[4];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) msk[b] = (SR || !(jx & 1u) ? 0x02u : 0xFEu) << (8 * b);
-#pragma unroll
-        for (int w = 0; w < W; ++w)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) gf[w][b] = __dp4a(rv[w], (int)msk[b], gf[w][b]);
-        // the moved variable keeps its folded gain, flips, and becomes tabu
-        // (owned by this CTA only if it lies in the slice)
+        // the moved variable keeps its folded gain (the update below adds
+        // 2 (1 - 2 x_i) Q_ii to it, taken off here from the diagonal held in a
+        // register, so that this runs while the row is in flight), flips, and
+        // becomes tabu (owned by this CTA only if it lies in the slice)
         const int rel = (G == 1 || (i >= lo && i < hi)) ? ((i - lo) >> 2) - tid : -1;
         const int bi = i & 3;
 #pragma unroll
@@ -441,7 +436,7 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh, 
 #pragma unroll
                 for (int b = 0; b < 4; ++b)
                     if (b == bi) {
-                        gf[w][b] -= (int)(int8_t)(rv[w] >> (8 * b)) * (SR ? 2 : si2);
+                        gf[w][b] -= (int)(int8_t)(dq[w] >> (8 * b)) * si2;
                         xb ^= 1u << (4 * w + b);
                         s32[w][b] = 0u - s32[w][b];
                         if (CK) kc[w][b] ^= 1u;
@@ -464,6 +459,16 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh, 
             objective();
             if (log_writer) mlog[it] = (uint16_t)i;
         }
+        // + 2 (1 - 2 x_i) Q_ij: one dp4a per variable with the byte 2 (1 - 2 x_i)
+        // in the variable's lane (the masks depend on the move only, so they are
+        // warp-uniform; signed rows already carry the sign)
+        unsigned msk[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) msk[b] = (SR || !(jx & 1u) ? 0x02u : 0xFEu) << (8 * b);
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) gf[w][b] = __dp4a(rv[w], (int)msk[b], gf[w][b]);
         warp_argmin(it + 1, slot, ASP ? asp_limit() : 0u);
         if constexpr (G > 1) {
             // one barrier per move, which also makes an exchange time-out end the
