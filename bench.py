@@ -561,6 +561,23 @@ def run_gpu(args, w):
                 "traffic": ncu_traffic("kernels_tabu.cu", "k_tabu"),
                 "algorithmic_bytes_per_launch": tabu_bytes, "launch_ms": phase_avg["tabu"],
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src}
+    # The Tabu kernel's own limit: one CTA per replica runs a dependent chain per
+    # move, and its SMs issue at a fraction of one warp instruction per cycle per
+    # sub-partition (warp instructions per launch from the ncu capture of one
+    # launch, profiles/; the same peak rule as the anneal's below).
+    sms_t = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz_t = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    inst_t = ncu_traffic("kernels_tabu.cu", "k_tabu", "warp_instructions_per_launch")
+    used_t = min(z, sms_t)
+    roofline["issue"] = {
+        "warp_instructions_per_launch": inst_t,
+        "achieved": (inst_t / tabu_s / 1e9) if inst_t else None,
+        "peak": sms_t * 4 * mhz_t / 1000.0, "unit": "G warp-instructions/s",
+        "frac": (inst_t / tabu_s / 1e9) / (sms_t * 4 * mhz_t / 1000.0) if inst_t else None,
+        "frac_of_sms_used": (inst_t / tabu_s / 1e9) / (used_t * 4 * mhz_t / 1000.0) if inst_t else None,
+        "sms_used": used_t,
+        "cycles_per_move": tabu_s * mhz_t * 1e6 / w["alpha"],
+    }
     anneal_rate = att / (phase_avg["anneal"] / 1000.0)
     # The Ising machine's anneal (a7): a sequential Metropolis chain per subQUBO,
     # bound by integer issue.  Warp instructions per attempt come from the ncu

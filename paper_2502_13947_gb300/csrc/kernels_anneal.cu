@@ -238,9 +238,13 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
                     const int f = acc ? fx : 0;
 #pragma unroll
                     for (int q2 = 0; q2 < P; ++q2) h[q2] += f * (int)(int8_t)(uint8_t)(rb >> (8 * q2));
+                    // up to 32 positions the next test goes before position L's own
+                    // sign change (lane L's test is not read again in this block;
+                    // measured faster for m <= 32, slower for m = 64)
+                    if constexpr (P == 1) t = sg[q] * h[q] <= lim[q];
                     if (acc && lane == L) { dE += sg[q] * h[q]; sg[q] = -sg[q]; }
                     fl |= (unsigned)acc << L;
-                    t = sg[q] * h[q] <= lim[q];
+                    if constexpr (P != 1) t = sg[q] * h[q] <= lim[q];
                 } else {
                     // fields if b flips, and the next position's test for either outcome
                     int hp[P];

@@ -16,7 +16,10 @@
 //      block-wide arg-min;
 //   2. it streams its 4W bytes of row i of Q (coalesced 4-byte loads; the row
 //      index is only known after the arg-min, so there is nothing to
-//      prefetch -- rows stay hot in L1/L2) and applies the update;
+//      prefetch -- rows stay hot in L1/L2) and applies the update; while the
+//      row is in flight, the owner of i flips it and takes the update's term
+//      2 (1 - 2 x_i) Q_ii off its gain in advance (Q_jj of the owned variables
+//      is held in a register), and thread 0 logs the move;
 //   3. it takes the arg-min over its free variables as the minimum of 32-bit
 //      keys (g + 2^26) << 5 | local index (the local index orders a thread's
 //      variables by j), the warp takes the arg-min with two redux.sync (gain,
