@@ -12,8 +12,10 @@ solution is the rank best with the smallest (energy, stamp, replica): one
 all_gather of three int64 per rank, then a broadcast of the winner's x.
 
 torch.distributed carries the collectives: NCCL on device tensors between
-GPUs, gloo on host tensors in the CPU tests.  Library calls are enqueued on
-torch's current stream, which NCCL's collectives are ordered after.
+GPUs, or gloo on host tensors (``exchange="cpu"``: the counts are copied to
+the host, added and copied back, and the best is chosen on host tensors).
+Library calls are enqueued on torch's current stream, which NCCL's
+collectives are ordered after; the host copies synchronise with it.
 """
 from __future__ import annotations
 
@@ -63,8 +65,10 @@ def broadcast_x(dist, torch, x_or_none, n, owner, device, group=None):
 class ShardedState:
     """This rank's shard of a solution set of z_total replicas on the current GPU."""
 
-    def __init__(self, I, torch, dist, q, n: int, z_total: int, seed: int, group=None, device="cuda"):
+    def __init__(self, I, torch, dist, q, n: int, z_total: int, seed: int, group=None, device="cuda",
+                 exchange=None):
         self.I, self.torch, self.dist, self.group, self.device = I, torch, dist, group, device
+        self.exchange = exchange or device   # where the collectives' tensors live
         self.n, self.z_total = n, z_total
         rank, world = dist.get_rank(group), dist.get_world_size(group)
         self.base, self.count = shard_range(z_total, rank, world)
@@ -89,14 +93,19 @@ class ShardedState:
         """Outer iteration t: Tabu, one allreduce of the column counts, the rest."""
         s = self._stream()
         self.I.icd2s_step_shard_begin(self.st, p, t, self.counts.data_ptr(), s)
-        add_counts(self.dist, self.counts, self.group)
+        if self.exchange == self.device:
+            add_counts(self.dist, self.counts, self.group)
+        else:
+            host = self.counts.to(self.exchange)       # waits for the shard's kernels
+            add_counts(self.dist, host, self.group)
+            self.counts.copy_(host)
         self.I.icd2s_step_shard_finish(self.st, p, t, self.counts.data_ptr(), s)
 
     def best(self):
         """(energy, global replica, x) of the method's best over every shard."""
         E, r, stamp = self.I.icd2s_get_best_info(self.st)
         x = self.I.icd2s_get_best(self.st, self.n)[0] if r >= 0 else None
-        owner, E, r, _ = best_owner(self.dist, self.torch, (E, r, stamp), self.device, self.group)
+        owner, E, r, _ = best_owner(self.dist, self.torch, (E, r, stamp), self.exchange, self.group)
         if owner < 0:
             return None, -1, None
-        return E, r, broadcast_x(self.dist, self.torch, x, self.n, owner, self.device, self.group)
+        return E, r, broadcast_x(self.dist, self.torch, x, self.n, owner, self.exchange, self.group)
