@@ -465,13 +465,30 @@ __global__ __launch_bounds__(MAXT) void k_tabu(Dev d, int alpha, int c, int sh, 
         // + 2 (1 - 2 x_i) Q_ij: one dp4a per variable with the byte 2 (1 - 2 x_i)
         // in the variable's lane (the masks depend on the move only, so they are
         // warp-uniform; signed rows already carry the sign)
-        unsigned msk[4];
+        if constexpr (!CK || ASP) {
+            // a warp-uniform branch on the move's sign, so the byte masks are
+            // immediates (measured faster for the wide keys and with aspiration,
+            // slower for the compact keys without it)
+            if (SR || !(jx & 1u)) {
 #pragma unroll
-        for (int b = 0; b < 4; ++b) msk[b] = (SR || !(jx & 1u) ? 0x02u : 0xFEu) << (8 * b);
+                for (int w = 0; w < W; ++w)
 #pragma unroll
-        for (int w = 0; w < W; ++w)
+                    for (int b = 0; b < 4; ++b) gf[w][b] = __dp4a(rv[w], (int)(0x02u << (8 * b)), gf[w][b]);
+            } else {
 #pragma unroll
-            for (int b = 0; b < 4; ++b) gf[w][b] = __dp4a(rv[w], (int)msk[b], gf[w][b]);
+                for (int w = 0; w < W; ++w)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) gf[w][b] = __dp4a(rv[w], (int)(0xFEu << (8 * b)), gf[w][b]);
+            }
+        } else {
+            unsigned msk[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) msk[b] = (SR || !(jx & 1u) ? 0x02u : 0xFEu) << (8 * b);
+#pragma unroll
+            for (int w = 0; w < W; ++w)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) gf[w][b] = __dp4a(rv[w], (int)msk[b], gf[w][b]);
+        }
         warp_argmin(it + 1, slot, ASP ? asp_limit() : 0u);
         if constexpr (G > 1) {
             // one barrier per move, which also makes an exchange time-out end the
