@@ -523,9 +523,8 @@ typedef struct icd2s_tuning {
     int32_t anneal_scheme;    /* sweep of the Ising-machine kernel (every scheme gives the same
                                  trajectory): 0 = default (4), 1 = rounds of decisions, 2 =
                                  position by position, 3 = position by position with the next
-                                 test taken for both outcomes, 4 = per sweep either 1 or by
-                                 position (2 up to 64 variables, 3 beyond), whichever the
-                                 previous sweep's accepts predict cheaper */
+                                 test taken for both outcomes, 4 = per sweep either 1 or 3,
+                                 whichever the previous sweep's accepts predict cheaper */
     int32_t refresh_kind;     /* tensor-core refresh: 1 = a BF16 copy of Q, persistent over
                                  the SMs with tiles of 128 rows of Q (0 = default: 1); 4 = the
                                  same with tiles of 256 rows; 2 is not a valid value

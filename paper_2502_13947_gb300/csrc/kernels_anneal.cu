@@ -71,7 +71,7 @@ __device__ __forceinline__ int accept_limit(uint32_t thr, uint32_t beta)
 // SEQ: 0 = rounds (multi-accept for P <= 4, first accept for P = 8);
 // 1 = position by position; 2 = position by position with the next
 // position's decision taken for both outcomes of the current one; 3 = per
-// sweep, rounds or by position (1 for P <= 2, 2 beyond), whichever the
+// sweep, rounds or by position (as 2), whichever the
 // previous sweep's accepts predict cheaper.
 template <int P, int SEQ>
 __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, int s, int lane, int8_t* Qs)
@@ -162,7 +162,13 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
         x0 |= (unsigned)xv << q;
         X[q] = __ballot_sync(0xffffffffu, xv != 0);
     }
-    int dE = 0;  // |f_sub| <= 256 m n - 128 m^2 < 2^30 (int8 Q), so the running change fits int32
+    // The anneal's energy change comes at the end from the gains alone: for the
+    // set F of positions whose value changed, E(x') - E(x) = (1/2) sum_{i in F}
+    // (g_i(x) - g_i(x')) (flip them one after the other), so no step of a sweep
+    // tracks it.  g0 = the gains at the start.
+    int g0[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) g0[q] = sg[q] * h[q];
 
     // acceptance limits of 4 consecutive sweeps: Philox block k4/4 of every owned
     // position, looked up in the schedule's table (issued one block ahead, so
@@ -203,7 +209,6 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             const bool f = (A[q] >> lane) & 1u;
-            dE += f ? sg[q] * h[q] : 0;
             sg[q] = f ? -sg[q] : sg[q];
             X[q] ^= A[q];
         }
@@ -232,33 +237,35 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
                 const Seg rb = rn;
                 if (L < 31) rn = *reinterpret_cast<const Seg*>(base + (size_t)(L + 1) * MC);
                 const int fx = ((xs >> L) & 1u) ? -2 : 2;  // 2 (1 - 2 x_b)
-                // the simple form for up to 64 positions, both outcomes beyond (measured)
-                if constexpr (SEQ == 1 || (SEQ == 3 && P <= 2)) {
+                // the simple form on request, otherwise both outcomes (measured faster
+                // at every size once a step no longer tracks the energy)
+                if constexpr (SEQ == 1) {
                     const bool acc = (__ballot_sync(0xffffffffu, t) >> L) & 1u;
                     const int f = acc ? fx : 0;
 #pragma unroll
                     for (int q2 = 0; q2 < P; ++q2) h[q2] += f * (int)(int8_t)(uint8_t)(rb >> (8 * q2));
-                    // up to 32 positions the next test goes before position L's own
-                    // sign change (lane L's test is not read again in this block;
-                    // measured faster for m <= 32, slower for m = 64)
-                    if constexpr (P == 1) t = sg[q] * h[q] <= lim[q];
-                    if (acc && lane == L) { dE += sg[q] * h[q]; sg[q] = -sg[q]; }
+                    // a flipped position's sign changes at the end of the block: its
+                    // test is not read again in this block
                     fl |= (unsigned)acc << L;
-                    if constexpr (P != 1) t = sg[q] * h[q] <= lim[q];
+                    t = sg[q] * h[q] <= lim[q];
                 } else {
                     // fields if b flips, and the next position's test for either outcome
                     int hp[P];
 #pragma unroll
                     for (int q2 = 0; q2 < P; ++q2) hp[q2] = h[q2] + fx * (int)(int8_t)(uint8_t)(rb >> (8 * q2));
-                    const bool tA = sg[q] * hp[q] <= lim[q], tR = sg[q] * h[q] <= lim[q];
+                    // (rejected, the state and so every lane's test stay as they are:
+                    // up to 64 positions the test is kept, beyond it is taken again --
+                    // each measured the faster there)
+                    const bool tA = sg[q] * hp[q] <= lim[q];
+                    const bool tR = P <= 2 ? t : sg[q] * h[q] <= lim[q];
                     const bool acc = (__ballot_sync(0xffffffffu, t) >> L) & 1u;
 #pragma unroll
                     for (int q2 = 0; q2 < P; ++q2) h[q2] = acc ? hp[q2] : h[q2];
-                    if (acc && lane == L) { dE += sg[q] * h[q]; sg[q] = -sg[q]; }
                     fl |= (unsigned)acc << L;
                     t = acc ? tA : tR;
                 }
             }
+            sg[q] = ((fl >> lane) & 1u) ? -sg[q] : sg[q];
             X[q] ^= fl;
         }
     };
@@ -439,11 +446,14 @@ __device__ __forceinline__ void anneal_one(const Dev& d, const AnnealArgs& a, in
                 ++pos;
             }
     }
-    long long dEl = dE;
+    long long dEl = 0;  // twice the energy change
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+        if ((changed >> q) & 1u) dEl += (long long)g0[q] - (long long)(sg[q] * h[q]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dEl += __shfl_xor_sync(0xffffffffu, dEl, o);
     if (lane == 0) {
-        if (a.dE) a.dE[s] = dEl;
+        if (a.dE) a.dE[s] = dEl / 2;
         if (a.attempts_acc) atomicAdd(reinterpret_cast<unsigned long long*>(a.attempts_acc),
                                       (unsigned long long)a.sweeps * (unsigned long long)m);
     }
