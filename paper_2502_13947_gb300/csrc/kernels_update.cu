@@ -16,7 +16,7 @@
 // caller's buffers are only 4-byte aligned).  The replica's flip list is staged in
 // shared memory in chunks; for every listed row i the thread streams the 16
 // bytes Q[i][j..j+15] (coalesced 2 KiB per CTA per row -- Q is symmetric, so
-// the row is the column), eight rows in flight per thread.  Long lists are
+// the row is the column), sixteen rows in flight per thread.  Long lists are
 // split over up to S CTAs per column tile (at least kMinRows rows each, so
 // the HBM stream has enough loads in flight): CTA z stores its partial sums
 // to the plane ACC[z][p][j], and the last of them (a per-tile ticket) adds
@@ -53,7 +53,7 @@ template <> struct RowLoad<4> {
     }
 };
 
-// acc[c] += d_i Q[i][j0 + c] over the staged rows, 8 rows in flight per
+// acc[c] += d_i Q[i][j0 + c] over the staged rows, 16 rows in flight per
 // thread; the diagonal term Q_jj d_j that a flipped j adds to its own sum is
 // taken out when the tile is finished.
 template <int COLS>
@@ -61,17 +61,17 @@ __device__ __forceinline__ void accumulate_rows(const Dev& d, const int32_t* sl,
 {
     const int ld = d.ld;
     int e = 0;
-    for (; e + 8 <= cn; e += 8) {
-        unsigned rv[8][COLS / 4];
-        int di[8];
+    for (; e + 16 <= cn; e += 16) {
+        unsigned rv[16][COLS / 4];
+        int di[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 16; ++u) {
             const int v = sl[e + u];
             di[u] = v < 0 ? -1 : 1;
             RowLoad<COLS>::get(d.Q + (size_t)(v & 0x7fffffff) * ld + j0, rv[u]);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < 16; ++u)
 #pragma unroll
             for (int c = 0; c < COLS; ++c) acc[c] += di[u] * (int)(int8_t)(rv[u][c >> 2] >> (8 * (c & 3)));
     }
