@@ -50,7 +50,9 @@ cudaError_t launch_init_x(const Dev& d, cudaStream_t s)
 // ---------------------------------------------------------------------------
 // H[p][j] = sum_k Q[j][k] x[p][k]  (int8 x {0,1}, exact int32) with dp4a on
 // 64 x 64 output tiles; the k loop walks 64-byte chunks staged in shared
-// memory.  Rows are padded with zeros to ld, so no tail handling in k.
+// memory.  Rows are padded with zeros to ld, so no tail handling in k.  With
+// few tiles the k range is split over gridDim.z CTAs whose partial sums are
+// added into H (zeroed first) with integer atomics: exact in any order.
 // ---------------------------------------------------------------------------
 constexpr int kGT = 64;          // tile edge (rows j and replicas p)
 constexpr int kGK = 64;          // bytes of k per stage
@@ -71,7 +73,9 @@ __global__ __launch_bounds__(256) void k_hgemm(const int8_t* __restrict__ Q, int
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0;
     const int lr = t / 4, lseg = (t % 4) * 16;  // loader: row, byte offset within the chunk
-    for (int k0 = 0; k0 < ld; k0 += kGK) {
+    const int chunks = ld / kGK, ks = (int)gridDim.z;
+    const int kb = (int)((long long)chunks * blockIdx.z / ks) * kGK, ke = (int)((long long)chunks * (blockIdx.z + 1) / ks) * kGK;
+    for (int k0 = kb; k0 < ke; k0 += kGK) {
         uint4 qv = make_uint4(0, 0, 0, 0), xv = make_uint4(0, 0, 0, 0);
         if (j0 + lr < n) qv = __ldg(reinterpret_cast<const uint4*>(Q + (size_t)(j0 + lr) * ld + k0 + lseg));
         if (p0 + lr < R) xv = *reinterpret_cast<const uint4*>(X + (size_t)(p0 + lr) * ldx + k0 + lseg);
@@ -101,7 +105,10 @@ __global__ __launch_bounds__(256) void k_hgemm(const int8_t* __restrict__ Q, int
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const int j = j0 + tj * 4 + a;
-            if (j < n) H[(size_t)p * ldh + j] = acc[a][b];
+            if (j < n) {
+                if (ks == 1) H[(size_t)p * ldh + j] = acc[a][b];
+                else atomicAdd(&H[(size_t)p * ldh + j], acc[a][b]);
+            }
         }
     }
 }
@@ -139,9 +146,17 @@ cudaError_t launch_recompute(const Dev& d, const uint8_t* X, int ldx, int R, int
                              cudaStream_t s)
 {
     dim3 grid((d.n + kGT - 1) / kGT, (R + kGT - 1) / kGT);
+    // k splits so that about two CTAs per SM run, each over at least 4 chunks of k
+    const int tiles = (int)(grid.x * grid.y), chunks = d.ld / kGK;
+    int ks = (2 * device_sm_count() + tiles - 1) / tiles;
+    if (ks > chunks / 4) ks = chunks / 4;
+    if (ks < 1) ks = 1;
+    grid.z = (unsigned)ks;
+    cudaError_t e;
+    if (ks > 1 && (e = cudaMemsetAsync(G, 0, sizeof(int32_t) * (size_t)R * d.ld, s)) != cudaSuccess) return e;
     k_hgemm<<<grid, 256, 0, s>>>(d.Q, d.n, d.ld, X, ldx, R, G, d.ld);
     note_launch(1);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_finish_gains<<<R, 256, 0, s>>>(d.diag, d.n, d.ld, X, ldx, G, E);
     note_launch(1);
