@@ -882,7 +882,7 @@ def run_sweep(args):
             med = cens[len(cens) // 2] if len(cens) % 2 else 0.5 * (cens[len(cens) // 2 - 1] + cens[len(cens) // 2])
             results["%s=%s" % (name, v)] = dict(success=len(hits), runs=len(per),
                                                 median_ttt_ms=None if med == float("inf") else round(med, 2),
-                                                iterations=[h for h, _, _ in per],
+                                                iterations=[h + 1 if h >= 0 else -1 for h, _, _ in per],
                                                 mean_ms_per_iter=round(statistics.mean(m for _, _, m in per), 2))
     I.icd2s_qubo_destroy(q)
     line = {"metric": "time-to-target energy, parameter sweep", "unit": "ms", "higher_is_better": False,
