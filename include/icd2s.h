@@ -506,7 +506,10 @@ int icd2s_get_apply_ms(icd2s_state* st, double* ms);
  * anneal_warps_per_cta = subQUBOs per CTA of the Ising-machine kernel,
  * 0 = default.  The Tabu search packs a move into one 32-bit key (one
  * reduction per warp and per block) when every gain of the instance fits
- * beside the index: 2 max_j sum_i |Q_ij| + 1 < 2^(30 - b), b = bits of n;
+ * beside the index: gain bound + 1 < 2^(30 - b), b = bits of n (see
+ * icd2s_qubo_gain_bound); with one CTA per replica, where that fails by one
+ * bit, on Q relabeled with the even-diagonal variables first, b = bits of the
+ * larger class (made once at icd2s_qubo_create, n ld bytes beside Q);
  * tabu_wide_keys = 1 keeps the two-reduction 64-bit keys anyway.  tabu_rows
  * = 2 makes (once per instance, 2 n ld bytes beside Q) and uses the rows of Q
  * negated as well, so a move reads its row already multiplied by (1 - 2x_i);
