@@ -168,7 +168,10 @@ int icd2s_default_params(int32_t n, icd2s_params* out);
 /* --- Problem ---------------------------------------------------------------
  * Copies the row-major n x n int8 matrix Q_host (Eq. 1) to the device.
  * Q must be symmetric (ICD2S_ERR_ASYMMETRIC otherwise).  Also computes the
- * diagonal and the normalised weight effect eta_j = sum_i |Q_ij| (Eq. 6). */
+ * diagonal, the normalised weight effect eta_j = sum_i |Q_ij| (Eq. 6) and the
+ * gain bound, and, for an instance whose gain bound needs the Tabu keys on
+ * parity labels, Q relabeled with the even-diagonal variables first (n x ld
+ * more bytes of device memory; ICD2S_ERR_OOM if they cannot be had). */
 int icd2s_qubo_create(const int8_t* Q_host, int32_t n, icd2s_qubo** out);
 int icd2s_qubo_destroy(icd2s_qubo* q);
 int icd2s_qubo_size(const icd2s_qubo* q, int32_t* n_out);
