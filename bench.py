@@ -397,9 +397,49 @@ def measure_apply(I, torch, peaks, stream, flush, reps=10):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst: the call is timed alone)"}
 
 
+TABU_WORKLOAD = dict(name="tabu-n5000-d0.5-z32-alpha5n", n=5000, density=0.5, qseed=1, z=32, alpha_per_n=5,
+                     c_div=150)
+
+
+def measure_tabu(I, torch, peaks, stream, flush, reps=3):
+    """One Tabu search (Algorithm 1) of every replica at the time-to-target
+    shape: n = 5000, rho = 0.5 (gain bound too wide for the compact keys on
+    indices: the keys on parity labels), 32 replicas, alpha = 5n.  Library
+    events around the call on the launching stream, L2 flushed before each."""
+    w = TABU_WORKLOAD
+    n, z = w["n"], w["z"]
+    alpha, c = w["alpha_per_n"] * n, max(2, n // w["c_div"])
+    Q = make_qubo(n, w["density"], w["qseed"])
+    q = I.icd2s_qubo_create(Q)
+    bound = I.icd2s_qubo_gain_bound(q)
+    st = I.icd2s_state_create(q, z, 5)
+    X0 = random_solutions(n, z, 3)
+    sp = stream.cuda_stream
+    ms = []
+    try:
+        for r in range(reps + 1):
+            with torch.cuda.stream(stream):
+                I.icd2s_state_load(st, X0, stream=sp)
+                flush()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                I.icd2s_tabu(st, alpha, c, sp)
+                e1.record(stream)
+            e1.synchronize()
+            if r > 0:   # the first call is the warm-up
+                ms.append(e0.elapsed_time(e1))
+    finally:
+        I.icd2s_state_destroy(st)
+        I.icd2s_qubo_destroy(q)
+    t = sum(ms) / len(ms)
+    return {"kernel": "k_tabu", "workload": w["name"], "gain_bound": bound, "alpha": alpha, "c": c, "launch_ms": t,
+            "moves_per_s": z * alpha / (t / 1000.0), "us_per_move": t * 1000.0 / alpha}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_only(args):
-    """One measurement alone (for profiling commands): --only apply|refresh."""
+    """One measurement alone (for profiling commands): --only apply|refresh|tabu."""
     import torch
 
     from paper_2502_13947_gb300 import build as B
@@ -410,7 +450,7 @@ def run_only(args):
     peaks, _ = measured_peaks()
     stream = torch.cuda.Stream()
     flush = L2Flush(torch)
-    fn = measure_apply if args.only == "apply" else measure_refresh
+    fn = {"apply": measure_apply, "refresh": measure_refresh, "tabu": measure_tabu}[args.only]
     print(json.dumps(fn(I, torch, peaks, stream, flush, reps=args.steps)), flush=True)
 
 
@@ -904,7 +944,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-refresh", action="store_true",
                     help="skip the tensor-core refresh and the write-back roofline measurements")
-    ap.add_argument("--only", choices=["apply", "refresh"], help="run one kernel measurement alone (profiling)")
+    ap.add_argument("--only", choices=["apply", "refresh", "tabu"], help="run one kernel measurement alone (profiling)")
     ap.add_argument("--ttt", action="store_true", help="time to target: learned / batched vs plain selection")
     ap.add_argument("--no-ttt", action="store_true", help="leave the time-to-target block out of the bench line")
     ap.add_argument("--ttt-seeds", type=int, default=10)
